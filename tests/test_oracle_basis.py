@@ -1,0 +1,164 @@
+"""Pins of the oracle's radial part against facts the paper and the mathematics fix.
+
+B-splines (Sec. 2.2): partition of unity, the Bernstein special case, derivatives by finite
+differences.  Gauss-Legendre: exactness and the closed-form small rules.  The radial Dirac
+operator (Eq. TDDE, Eq. dualkinetic): the closed-form Dirac-Coulomb levels, kappa-degeneracies,
+no spurious states, Hermiticity and S positive definite, the 1s mean radius.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_21697_gb300 import workloads as W
+
+C = W.C_AU
+
+
+def dirac_level(n, kappa, Z=1.0, c=C):
+    """Sommerfeld fine-structure formula, shifted by -c^2 (Sec. 2.1, nonstandard beta)."""
+    a = Z / c
+    g = math.sqrt(kappa * kappa - a * a)
+    return c * c / math.sqrt(1 + (a / (n - abs(kappa) + g)) ** 2) - c * c
+
+
+def test_dirac_level_formula_values():
+    # the closed-form 1s energy c^2 (sqrt(1 - (Z/c)^2) - 1) and its nonrelativistic limit
+    a2 = 1 / C ** 2   # c^2 (sqrt(1 - a^2) - 1) written without the cancellation
+    assert abs(dirac_level(1, -1) - (-C * C * a2 / (1 + math.sqrt(1 - a2)))) < 1e-11
+    assert abs(dirac_level(1, -1, c=1e6) + 0.5) < 1e-9
+    assert abs(dirac_level(2, 1) - dirac_level(2, -1)) < 1e-15
+
+
+def small_oracle(oracle_mod, **over):
+    p = W.oracle_params(W.SMALL)
+    p.update(over)
+    return oracle_mod.Oracle(**p)
+
+
+def test_gauss_legendre(oracle_mod):
+    x, w = oracle_mod.gauss_legendre(2)
+    assert np.allclose(sorted(x), [-1 / math.sqrt(3), 1 / math.sqrt(3)], atol=1e-15, rtol=0)
+    x, w = oracle_mod.gauss_legendre(3)
+    assert np.allclose(sorted(x), [-math.sqrt(0.6), 0, math.sqrt(0.6)], atol=1e-15, rtol=0)
+    assert np.allclose(sorted(w), [5 / 9, 5 / 9, 8 / 9], atol=1e-15, rtol=0)
+    for q in (5, 14, 21):
+        x, w = oracle_mod.gauss_legendre(q)
+        for deg in range(2 * q):
+            exact = 0.0 if deg % 2 else 2.0 / (deg + 1)
+            assert abs(np.dot(w, x ** deg) - exact) < 1e-13
+        # first inexact degree: the Gauss-Legendre remainder for x^(2q) is
+        # 2^(2q+1) (q!)^4 / ((2q+1) ((2q)!)^2)
+        err = 2.0 / (2 * q + 1) - np.dot(w, x ** (2 * q))
+        pred = 2.0 ** (2 * q + 1) * math.factorial(q) ** 4 / ((2 * q + 1) * math.factorial(2 * q) ** 2)
+        assert abs(err - pred) < 1e-13 + 1e-9 * pred
+
+
+def test_bspline_partition_and_derivatives(oracle_mod):
+    o = small_oracle(oracle_mod, N=20, R=10.0)
+    rng = np.random.default_rng(1)
+    for x in rng.uniform(0.01, 9.99, 25):
+        v, d1, d2 = o.bsplines(x)
+        assert abs(v.sum() - 1) < 1e-14
+        assert abs(d1.sum()) < 1e-11 and abs(d2.sum()) < 1e-9
+        assert v.min() >= -1e-16
+        h = 1e-5
+        vp, d1p, _ = o.bsplines(x + h)
+        vm, d1m, _ = o.bsplines(x - h)
+        assert np.allclose((vp - vm) / (2 * h), d1, atol=1e-6 * (1 + abs(d1).max()))
+        assert np.allclose((d1p - d1m) / (2 * h), d2, atol=1e-5 * (1 + abs(d2).max()))
+
+
+def test_bspline_bernstein_case(oracle_mod):
+    # one knot interval [0, R] with k-fold end knots: the B-splines are the Bernstein basis
+    k = 7
+    o = oracle_mod.Oracle(**dict(W.oracle_params(W.SMALL), N=k - 4, R=1.0, order=k))
+    for x in (0.13, 0.5, 0.77):
+        v, _, _ = o.bsplines(x)
+        bern = [math.comb(k - 1, i) * x ** i * (1 - x) ** (k - 1 - i) for i in range(k)]
+        assert np.allclose(v, bern, atol=1e-15, rtol=0)
+
+
+def test_knots_linear_and_geometric(oracle_mod):
+    o = small_oracle(oracle_mod)
+    t = o.knots()
+    k, N = 7, 60
+    assert len(t) == N + 4 + k
+    assert np.all(t[:k] == 0) and np.all(t[-k:] == 50.0)
+    inner = t[k - 1:len(t) - k + 1]
+    assert np.allclose(np.diff(inner), 50.0 / (N + 5 - k), rtol=1e-13)
+    p = W.oracle_params(W.SLICE)
+    o2 = oracle_mod.Oracle(**p)
+    t2 = o2.knots()
+    inner = t2[k - 1:len(t2) - k + 1]
+    d = np.diff(inner)
+    assert abs(inner[p["n_lin"]] - p["r_lin"]) < 1e-12 and abs(inner[-1] - p["R"]) < 1e-12
+    assert np.allclose(d[:p["n_lin"]], p["r_lin"] / p["n_lin"], rtol=1e-12)
+    ratios = d[p["n_lin"] + 1:] / d[p["n_lin"]:-1]
+    assert np.allclose(ratios, ratios[0], rtol=1e-9) and ratios[0] > 1
+
+
+@pytest.fixture(scope="module")
+def small(oracle_mod):
+    return small_oracle(oracle_mod)
+
+
+@pytest.mark.parametrize("kappa,levels", [(-1, [1, 2, 3]), (1, [2, 3]), (-2, [2, 3]), (2, [3]),
+                                          (-3, [3])])
+def test_dirac_coulomb_levels(small, kappa, levels):
+    E, V = small.eigen(kappa)
+    c2 = C * C
+    pos = E[E > -c2]
+    for i, n in enumerate(levels):
+        # measured basis error at this basis: <= 2e-9 for n <= 2, <= 1e-8 for n = 3 (box edge)
+        tol = 2e-9 if n <= 2 else 1e-8
+        assert abs(pos[i] - dirac_level(n, kappa)) < tol, (kappa, n, pos[i] - dirac_level(n, kappa))
+    neg = E[E <= -c2]
+    assert neg.max() < -2 * c2 + 1e-6  # negative continuum starts at -2c^2 with the shifted beta
+    assert pos.min() > -1.0
+
+
+def test_no_spurious_states(small):
+    c2 = C * C
+    for kappa in (-4, -3, -2, -1, 1, 2, 3, 4):
+        E, _ = small.eigen(kappa)
+        pos = E[E > -c2]
+        n_low = abs(kappa) + (1 if kappa > 0 else 0)  # principal quantum number of the lowest level
+        e_ex = dirac_level(n_low, kappa)
+        # a spurious state would sit far below the lowest physical level; the box (R = 50)
+        # only lifts the n = 4 levels, by a few 1e-6
+        assert pos[0] > e_ex - 1e-9, kappa
+        assert pos[0] - e_ex < {1: 1e-8, 2: 1e-8, 3: 1e-8, 4: 1e-5, 5: 1e-3}[n_low], kappa
+
+
+def test_kappa_sign_degeneracy(small):
+    # Dirac-Coulomb levels depend on n and j only: n s1/2 = n p1/2, n p3/2 = n d3/2
+    c2 = C * C
+    pos = {k: small.eigen(k)[0][small.eigen(k)[0] > -c2] for k in (-1, 1, -2, 2)}
+    assert abs(pos[-1][1] - pos[1][0]) < 1e-10      # 2s1/2 vs 2p1/2
+    assert abs(pos[-1][2] - pos[1][1]) < 2e-8       # 3s1/2 vs 3p1/2
+    assert abs(pos[-2][1] - pos[2][0]) < 2e-8       # 3p3/2 vs 3d3/2
+    assert pos[-2][0] - pos[1][0] > 1e-6            # fine structure 2p3/2 above 2p1/2
+
+
+def test_radial_matrices_symmetric(small):
+    for kappa in (-2, -1, 1, 3):
+        S, H = small.radial(kappa)
+        m = small.active_mask()[:small.nb] if kappa == small.kappa[0] else None
+        assert np.abs(H - H.T).max() <= 1e-13 * np.abs(H).max()
+        assert np.abs(S - S.T).max() <= 1e-15
+        act = np.ones(small.nb, bool)
+        act[0] = kappa == -1
+        act[small.N + 1] = kappa == 1
+        assert np.linalg.eigvalsh(S[np.ix_(act, act)]).min() > 0
+        assert np.all(S[~act] == 0) and np.all(H[:, ~act] == 0)
+
+
+def test_1s_mean_radius(small):
+    E, V = small.eigen(-1)
+    v = V[np.nonzero(E > -C * C)[0][0]]
+    R = small.rmoment(-1)
+    g = math.sqrt(1 - 1 / C ** 2)
+    assert abs(v @ R @ v - (2 * g + 1) / 2) < 1e-7   # first order in the basis error
+    S, _ = small.radial(-1)
+    assert abs(v @ S @ v - 1) < 1e-13
