@@ -1,0 +1,294 @@
+"""Benchmark: Crank-Nicolson steps/s of the 3D time-dependent Dirac equation on one GB300.
+
+Workload (default): the production-shaped hydrogen system -- R = 300 a.u., 1000 order-7
+B-splines on a linear-then-geometric grid, |kappa| <= 30 with every mu (1860 channels,
+n = 3.72 M complex unknowns), multipoles l <= 6, 3-cycle 800 nm sin^2 pulse at E0 = 0.1 a.u.,
+dt = 0.005, BiCGSTAB to relative residual 1e-10.  Every step runs the whole hot path: pulse
+factors, coupling assembly, A_- psi, BiCGSTAB (operator applies, preconditioner, updates).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+       [--precision 0|1] [--t0 T] [--workload production|slice|small]
+Prints one JSON line (rank 0).  N > 1 (torchrun) runs N independent replicas, one per GPU,
+with no data-path communication; the value is the total steps/s over all ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CN steps/s + SpMV HBM GB/s, 1 GB300: mixed/learned vs plain FP64 @ equal resid"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e3 / 1e6   # SMs x FP64 FMA/clk/SM x 2 flop x max clock (GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="production")
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--t0", type=float, default=None, help="start time (default: 0, the pulse start)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=8.0)
+    return ap.parse_args()
+
+
+def workload_desc(name, cfg):
+    return ("%s: hydrogen Z=%g, R=%g a.u., N=%d order-%d B-splines (%s grid), |kappa|<=%d, %s, l<=%d, "
+            "%g-cycle sin^2 pulse omega=%.6f a.u. E0=%g, dt=%g, tol=%g" %
+            (name, cfg["Z"], cfg["R"], cfg["N"], cfg["order"], "linear" if cfg["grid"] == 0 else
+             "linear-then-geometric", cfg["kappa_max"], "all mu" if cfg["two_mu_max"] <= 0 else
+             "|mu|<=%g" % (cfg["two_mu_max"] / 2), cfg["l_max"], cfg["n_cycles"], cfg["omega"], cfg["E0"],
+             cfg["dt"], cfg["tol"]))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def operator_counts(bas, cfg):
+    """Algorithmic bytes and flops of one FP64 operator apply A_+- x."""
+    n1, bd = cfg["N"] + 1, 2 * cfg["order"] - 1
+    coup = bas.npairs * n1 * bd * 4           # stored coupling values (upper pairs only)
+    diag = bas.nch * n1 * bd * 4              # radial block entries applied (S and H0 each)
+    nk2 = 2 * cfg["kappa_max"]
+    flops = 8 * coup + 2 * 8 * diag           # W x and W^T x: 2 complex FMAs per value; (S + i t H) x
+    bytes_ = 8 * coup + 2 * 16 * bas.n + 2 * 8 * nk2 * n1 * bd * 4
+    return coup, flops, bytes_
+
+
+def cpu_baseline(cfg, its_per_step, seconds, seed=5):
+    """The oracle, as it stands, on a bounded sample: rows of A_+ x at the full workload."""
+    import numpy as np
+    import oracle
+    from paper_2512_21697_gb300 import workloads as W
+    oracle.build()
+    orc = oracle.Oracle(**W.oracle_params(cfg))
+    x = W.random_state(orc.n, seed)
+    x[~orc.active_mask()] = 0
+    rng = np.random.default_rng(seed)
+    T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
+    done, elapsed, batch = 0, 0.0, 256
+    while elapsed < seconds:
+        rows = rng.integers(0, orc.n, batch)
+        t0 = time.perf_counter()
+        orc.apply_rows(0.5 * T, +1, x, rows // orc.nb, rows % orc.nb)
+        elapsed += time.perf_counter() - t0
+        done += batch
+    t_apply = elapsed / done * orc.n
+    applies = 3 + 2 * its_per_step
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / (t_apply * applies), "unit": "steps/s", "cores": cores, "kind": "oracle",
+            "sample": "%d rows of A_+ x (of n=%d) at the full workload, %.1f s; step = %.1f operator "
+                      "applies (3 + 2 x %.2f BiCGSTAB iterations/step)" % (done, orc.n, elapsed, applies,
+                                                                         its_per_step)}
+
+
+def reference_arm(args):
+    """Oracle arm: the CPU oracle as it stands, same workload, metric and unit."""
+    from paper_2512_21697_gb300 import workloads as W
+    cfg = W.WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # iterations per step: the oracle's own BiCGSTAB on the slice system in the same window
+    import oracle
+    sl = oracle.Oracle(**W.oracle_params(W.SLICE))
+    T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
+    t0 = args.t0 if args.t0 is not None else 0.0
+    x, _ = sl.ground_state()
+    its = []
+    for s in range(2):
+        x, it, _ = sl.step(x, t0 + s * cfg["dt"], tol=cfg["tol"])
+        its.append(it)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(cfg, sum(its) / len(its), max(2.0, args.cpu_seconds / 2))["value"])
+    cb = cpu_baseline(cfg, sum(its) / len(its), 1.0)
+    v = statistics.median(vals[args.warmup:])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, cfg), "t_start": t0},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+    import numpy as np
+    import torch
+    from paper_2512_21697_gb300 import binding as B, workloads as W
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    cfg = dict(W.WORKLOADS[args.workload])
+    T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
+    t0 = args.t0 if args.t0 is not None else 0.0
+
+    bas = B.Basis(cfg)
+    psi0_h, e0 = bas.initial_state()
+    stream = torch.cuda.Stream()
+    op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=args.precision, max_iter=1000)
+    dev = torch.device("cuda", local)
+    with torch.cuda.stream(stream):
+        psi = torch.from_numpy(psi0_h).to(dev)
+        hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev)
+    nh = 0
+    tcur = t0
+    # warm-up steps
+    _, _, nh = op.step(psi, args.warmup, tcur, hist=hist, n_hist=nh)
+    tcur += args.warmup * cfg["dt"]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    op.profile(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    its, res, nh = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    phase_ms, phase_n, launches = op.profile_read()
+    op.profile(False)
+    tcur += args.steps * cfg["dt"]
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sps = args.steps / (ms / 1000.0)
+    value = sps * world
+
+    # end to end through the C ABI with host buffers: H2D of the state, K steps, D2H of the result
+    psi_h = torch.from_numpy(psi0_h).pin_memory()
+    out_h = torch.empty_like(psi_h).pin_memory()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        psi_e = torch.empty_like(psi)
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    ee0.record(stream)
+    te = tcur
+    for s in range(e2e_steps):
+        with torch.cuda.stream(stream):
+            psi_e.copy_(psi_h if s == 0 else out_h, non_blocking=True)
+        op.step(psi_e, 1, te)
+        with torch.cuda.stream(stream):
+            out_h.copy_(psi_e, non_blocking=True)
+        te += cfg["dt"]
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    e2e_sps = e2e_steps / (ee0.elapsed_time(ee1) / 1000.0) * world
+
+    coup, flops, bytes_ = operator_counts(bas, cfg)
+    n_apply = max(1, phase_n["apply"])
+    t_apply = phase_ms["apply"] / n_apply / 1000.0
+    achieved_tf = flops / t_apply / 1e12
+    gbs = bytes_ / t_apply / 1e9
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    obs = op.observables(psi)
+    line = {
+        "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "c64+f64", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, cfg), "n": bas.n, "channels": bas.nch,
+                   "pairs": bas.npairs, "t_start": t0, "precision": ["fp64", "mixed c64/fp64"][args.precision],
+                   "l2": "inputs larger than L2: %.1f GB of coupling values streamed per operator apply" %
+                         (8 * coup / 1e9),
+                   "parallelism": "replicas x%d (independent instances, no collective)" % world},
+        "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)),
+        "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+        "spmv_gbs": gbs,
+        "roofline": {"bound": "alu", "kernel": "k_apply64 (FP64 operator apply)", "achieved": achieved_tf,
+                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                     "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                     "gbs": gbs, "apply_ms": t_apply * 1000.0, "flops_per_apply": flops,
+                     "bytes_per_apply": bytes_},
+        "e2e": {"value": e2e_sps, "unit": "steps/s", "h2d_bytes_per_step": bas.n * 16,
+                "d2h_bytes_per_step": bas.n * 16},
+        "gpu_launches": launches,
+        "clocks": ck,
+        "observables": obs,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline(cfg, float(np.mean(its)), args.cpu_seconds)
+        except Exception as e:  # the baseline is reported, never required
+            line["cpu_baseline"] = {"error": str(e)}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

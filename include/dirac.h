@@ -1,0 +1,158 @@
+/*
+ * dirac.h -- C ABI of libdirac_gb300.so: the Crank-Nicolson time step of the 3D time-dependent
+ * Dirac equation in a dual-kinetic-balance B-spline x spherical-spinor basis, on one GB300
+ * (sm_103a).  Method: arXiv 2512.21697 ("GaDE"), Sec. 2 (theory) and Sec. 3 (time loop).
+ *
+ * Conventions shared by every call
+ *  - Atomic units.  Every call returns a dirac_status; on failure dirac_last_error() returns a
+ *    thread-local message.  Parameters are validated before anything is allocated.  No C++
+ *    exception crosses this boundary.
+ *  - Device buffers are plain device pointers owned by the caller (e.g. torch tensors'
+ *    data_ptr()); the library never frees them.  Opaque handles are owned by the library and
+ *    released with the matching *_free call.
+ *  - All device work is ordered on the CUDA stream given to dirac_operator_setup.  Calls that
+ *    return host-visible numbers synchronise that stream before returning.
+ *  - State vectors are complex128 (interleaved re, im doubles), "library order": channel-major
+ *    (channels as listed by dirac_basis_channels), then radial slot r = 0 .. N, then DKB type
+ *    (0 = large: P = u, Q = (u' + kappa u / r)/2c; 1 = small: P = (u' - kappa u / r)/2c, Q = u;
+ *    Eq. dualkinetic), where slot r carries B-spline B_{r+1} of the knot vector B_0 .. B_{N+3}.
+ *    Length n = n_channels * 2 (N + 1).  The zero boundary condition at r = 0 (Sec. 2.2) leaves
+ *    slot 0 type 0 used only for kappa = -1 and slot 0 type 1 only for kappa = +1; those unused
+ *    entries must be zero on input and stay zero (the operators act on them as the identity).
+ */
+#ifndef DIRAC_GB300_H
+#define DIRAC_GB300_H
+#include <stdint.h>
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DIRAC_OK = 0,
+    DIRAC_E_ARG = 1,        /* invalid argument (nothing was allocated or changed)           */
+    DIRAC_E_NOMEM = 2,      /* host or device allocation failed                              */
+    DIRAC_E_CUDA = 3,       /* a CUDA runtime call failed (message names it)                 */
+    DIRAC_E_NOCONV = 4,     /* BiCGSTAB hit max_iter before tol                              */
+    DIRAC_E_BREAKDOWN = 5,  /* BiCGSTAB breakdown persisted after one restart                */
+    DIRAC_E_NUMERIC = 6,    /* non-finite residual                                           */
+    DIRAC_E_STATE = 7       /* handle in the wrong state (e.g. no GPU, freed basis)          */
+} dirac_status;
+
+typedef struct dirac_basis dirac_basis; /* host-side basis and operator data                  */
+typedef struct dirac_op dirac_op;       /* device operator, factors, workspaces               */
+
+/* Radial and angular discretisation (Sec. 2.2).  n_splines = N B-splines kept for every kappa
+ * (B_2 .. B_{N+1}); order = B-spline order k; grid 0 = linear breakpoints on [0, R]; grid 1 =
+ * n_lin linear intervals up to r_lin then geometrically growing intervals up to R (the growth
+ * factor is fixed by the interval count N + 5 - k); kappa_max bounds |kappa|; two_mu_max bounds
+ * |2 mu| (<= 0: every mu); l_max truncates the multipole (plane-wave) expansion of the pulse
+ * (Eq. bdpA); quad_pts = Gauss-Legendre points per knot interval. */
+typedef struct {
+    double Z, c, R;
+    int n_splines, order, grid;
+    double r_lin;
+    int n_lin, kappa_max, two_mu_max, l_max, quad_pts;
+} dirac_basis_params;
+
+/* sin^2 pulse, Eq. (ndpPot): A_x = (E0/omega) sin^2(pi (t-z/c)/T) sin(omega (t-z/c)),
+ * T = n_cycles 2 pi / omega, polarised along x, travelling along z, on for 0 <= t <= T.
+ * t0 shifts the pulse start (field at time t uses t - t0). */
+typedef struct {
+    double E0, omega, n_cycles, t0;
+} dirac_pulse;
+
+/* Time stepping (Eq. solPsi) and its BiCGSTAB solve.
+ * dt: step; tol: relative residual ||b - A_+ x|| / ||b||; max_iter: BiCGSTAB iteration cap per
+ * step (per inner solve in mixed precision); precision: 0 = FP64 throughout, 1 = complex64
+ * BiCGSTAB inside FP64 iterative refinement; tol_inner: inner relative tolerance (precision 1);
+ * max_outer: refinement cap (precision 1); guess: 0 = psi_n, 1 = quadratic extrapolation
+ * 3 psi_n - 3 psi_{n-1} + psi_{n-2}; time_eval: 0 = H at t + dt/2 (midpoint rule of Sec. 2.4),
+ * 1 = H at t + dt (Eq. solPsi as printed); precond: 0 = none, 1 = LU of M = S + i dt/2 H0
+ * (Eq. matrixM). */
+typedef struct {
+    double dt, tol, tol_inner;
+    int max_iter, precision, max_outer, guess, time_eval, precond;
+} dirac_solver_opts;
+
+/* Build the basis, the kappa-polynomial radial matrices h_n, s_n (Eq. fullH and Sec. 2.3), the
+ * projected pulse matrices g^n_{alpha,l} (Eq. fullH), the angular coefficients H^theta_l
+ * (Eq. Htheta via Eq. HthetaExpand and Eq. GauntCoef) and the channel-pair list.  Host only.
+ * psi0_host (nullable, n complex128 in library order): receives the 1s1/2, mu = +1/2 state,
+ * the lowest kappa = -1 solution of H0 v = E S v above -c^2 (Sec. 2.3), v^T S v = 1, largest
+ * component positive.  e0 (nullable) receives its energy. */
+dirac_status dirac_basis_build(const dirac_basis_params* params, dirac_basis** out,
+                               double* psi0_host, double* e0);
+void dirac_basis_free(dirac_basis* basis);
+int64_t dirac_basis_dim(const dirac_basis* basis);          /* n, or -1 for NULL            */
+int dirac_basis_nchannels(const dirac_basis* basis);
+/* channel labels in library order: kappa[i], two_mu[i] (host arrays of n_channels ints) */
+dirac_status dirac_basis_channels(const dirac_basis* basis, int* kappa, int* two_mu);
+/* number of coupled unordered channel pairs (a < b) */
+int64_t dirac_basis_npairs(const dirac_basis* basis);
+/* Host copies of setup data for parity checks.  Radial blocks of one kappa as dense
+ * (2(N+1))^2 row-major matrices in library order (slot-major, type-minor). */
+dirac_status dirac_basis_radial(const dirac_basis* basis, int kappa, double* S, double* H0);
+/* Coupling block X_ab(t) of H_ab = i X_ab (Eq. fullH) for channels a != b (library indices),
+ * dense (2(N+1))^2 row-major in library order, pulse and time t given.  Host only. */
+dirac_status dirac_basis_coupling(const dirac_basis* basis, const dirac_pulse* pulse, int a, int b,
+                                  double t, double* X);
+/* 4 pi Y_l0(z) <X_{k1 m1}| sigma_x Y_l0 |X_{k2 m2}> (the Eq. Htheta coefficient with the
+ * bra's kappa written out), two_mu = 2 mu. */
+double dirac_angular(int kappa1, int two_mu1, int kappa2, int two_mu2, int l);
+
+/* Upload the operator for one pulse and solver setting: radial blocks, pulse matrices, pair
+ * coefficients and the block-banded LU factors of M = S + i dt/2 H0, and allocate every device
+ * workspace (coupling values, Krylov vectors).  cuda_stream: a cudaStream_t (NULL = legacy
+ * default stream).  Device memory is reported by dirac_op_device_bytes. */
+dirac_status dirac_operator_setup(const dirac_basis* basis, const dirac_pulse* pulse,
+                                  const dirac_solver_opts* opts, void* cuda_stream, dirac_op** out);
+void dirac_op_free(dirac_op* op);
+int64_t dirac_op_device_bytes(const dirac_op* op);
+
+/* y = A_sign(t) x, A_+- = S +- i dt/2 H(t) (Eq. solPsi), H evaluated at time t.  Assembles the
+ * coupling values for t first.  x_dev, y_dev: device complex128[n], must not alias. */
+dirac_status dirac_apply(dirac_op* op, int sign, double t, const void* x_dev, void* y_dev);
+/* z = M^-1 r with M = S + i dt/2 H0 (Eq. matrixM).  r_dev, z_dev: device complex128[n]. */
+dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, void* z_dev);
+
+/* Advance psi by n_steps Crank-Nicolson steps starting at t_start (step s covers
+ * [t_start + s dt, t_start + (s+1) dt]): psi <- A_+^{-1} A_- psi, each solve by BiCGSTAB
+ * (precision 0) or mixed-precision refinement (precision 1) to opts.tol.
+ * psi_dev: device complex128[n], in/out.  hist_dev: nullable device complex128[2n] holding
+ * psi_{n-1}, psi_{n-2} for the extrapolated guess; n_hist (nullable, in/out) says how many of
+ * them are valid (0..2) -- with NULL history the guess restarts from psi_n.
+ * iters_out / resid_out: nullable host arrays of n_steps receiving BiCGSTAB iterations (total
+ * inner iterations in precision 1) and the final relative residual per step.
+ * Returns DIRAC_E_NOCONV / DIRAC_E_BREAKDOWN / DIRAC_E_NUMERIC if a step fails (psi then holds
+ * the last iterate of that step). */
+dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
+                        double t_start, int* iters_out, double* resid_out);
+
+/* Observables of a state (Sec. 4.3): out[0] = psi^H S psi, out[1] = psi^H H0 psi,
+ * out[2] = |v_1s^T S psi_{kappa=-1, mu=+1/2}|^2 (ground-state population).  n_out <= 3. */
+dirac_status dirac_observables(dirac_op* op, const void* psi_dev, double* out, int n_out);
+
+/* y = A_sign x with the coupling values assembled by the most recent dirac_apply or dirac_step
+ * (no reassembly).  Same buffers and errors as dirac_apply. */
+dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, void* y_dev);
+
+/* Kernel-phase timers.  dirac_profile(op, 1) resets and starts timing every launch group with a
+ * pair of CUDA events on the op's stream (0 stops); dirac_profile_read synchronises the stream and
+ * returns, per phase, the summed milliseconds and the number of timed launch groups, plus the
+ * number of kernel launches since the reset (counted whether or not timing is on).
+ * Phases: DIRAC_PHASE_ASSEMBLE (pulse factors + coupling values), DIRAC_PHASE_APPLY (operator
+ * products), DIRAC_PHASE_PRECOND, DIRAC_PHASE_VECTOR (updates, reductions, copies). */
+#define DIRAC_PHASE_ASSEMBLE 0
+#define DIRAC_PHASE_APPLY 1
+#define DIRAC_PHASE_PRECOND 2
+#define DIRAC_PHASE_VECTOR 3
+#define DIRAC_NPHASE 4
+dirac_status dirac_profile(dirac_op* op, int enable);
+dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches);
+
+const char* dirac_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

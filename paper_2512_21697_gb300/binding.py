@@ -1,0 +1,247 @@
+"""ctypes binding of libdirac_gb300.so: the C ABI of include/dirac.h under the same names.
+
+Argument marshalling only; every step of the method runs in the library (host setup in C++,
+the time step in CUDA kernels).  Device buffers are torch CUDA tensors (complex128, contiguous).
+Importing works without a GPU; a missing library raises immediately -- there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdirac_gb300.so")
+
+DIRAC_OK, DIRAC_E_ARG, DIRAC_E_NOMEM, DIRAC_E_CUDA, DIRAC_E_NOCONV, DIRAC_E_BREAKDOWN, DIRAC_E_NUMERIC, \
+    DIRAC_E_STATE = range(8)
+STATUS_NAMES = ["OK", "E_ARG", "E_NOMEM", "E_CUDA", "E_NOCONV", "E_BREAKDOWN", "E_NUMERIC", "E_STATE"]
+
+
+class DiracError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES[status] if 0 <= status < 8 else status, msg))
+        self.status = status
+
+
+class dirac_basis_params(C.Structure):
+    _fields_ = [("Z", C.c_double), ("c", C.c_double), ("R", C.c_double), ("n_splines", C.c_int),
+                ("order", C.c_int), ("grid", C.c_int), ("r_lin", C.c_double), ("n_lin", C.c_int),
+                ("kappa_max", C.c_int), ("two_mu_max", C.c_int), ("l_max", C.c_int), ("quad_pts", C.c_int)]
+
+
+class dirac_pulse(C.Structure):
+    _fields_ = [("E0", C.c_double), ("omega", C.c_double), ("n_cycles", C.c_double), ("t0", C.c_double)]
+
+
+class dirac_solver_opts(C.Structure):
+    _fields_ = [("dt", C.c_double), ("tol", C.c_double), ("tol_inner", C.c_double), ("max_iter", C.c_int),
+                ("precision", C.c_int), ("max_outer", C.c_int), ("guess", C.c_int), ("time_eval", C.c_int),
+                ("precond", C.c_int)]
+
+
+_lib = None
+_VP, _DP, _IP = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+SIGNATURES = {
+    "dirac_basis_build": (C.c_int, [C.POINTER(dirac_basis_params), C.POINTER(_VP), _DP, _DP]),
+    "dirac_basis_free": (None, [_VP]),
+    "dirac_basis_dim": (C.c_int64, [_VP]),
+    "dirac_basis_nchannels": (C.c_int, [_VP]),
+    "dirac_basis_channels": (C.c_int, [_VP, _IP, _IP]),
+    "dirac_basis_npairs": (C.c_int64, [_VP]),
+    "dirac_basis_radial": (C.c_int, [_VP, C.c_int, _DP, _DP]),
+    "dirac_basis_coupling": (C.c_int, [_VP, C.POINTER(dirac_pulse), C.c_int, C.c_int, C.c_double, _DP]),
+    "dirac_angular": (C.c_double, [C.c_int] * 5),
+    "dirac_operator_setup": (C.c_int, [_VP, C.POINTER(dirac_pulse), C.POINTER(dirac_solver_opts), _VP,
+                                       C.POINTER(_VP)]),
+    "dirac_op_free": (None, [_VP]),
+    "dirac_op_device_bytes": (C.c_int64, [_VP]),
+    "dirac_apply": (C.c_int, [_VP, C.c_int, C.c_double, _VP, _VP]),
+    "dirac_precond_apply": (C.c_int, [_VP, _VP, _VP]),
+    "dirac_step": (C.c_int, [_VP, _VP, _VP, _IP, C.c_int, C.c_double, _IP, _DP]),
+    "dirac_observables": (C.c_int, [_VP, _VP, _DP, C.c_int]),
+    "dirac_apply_assembled": (C.c_int, [_VP, C.c_int, _VP, _VP]),
+    "dirac_profile": (C.c_int, [_VP, C.c_int]),
+    "dirac_profile_read": (C.c_int, [_VP, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "dirac_last_error": (C.c_char_p, []),
+}
+
+
+def lib():
+    """Load libdirac_gb300.so (built by ``paper_2512_21697_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libdirac_gb300.so is not built (run __graft_entry__.build()); "
+                              "there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, what):
+    if status != DIRAC_OK:
+        raise DiracError(status, "%s: %s" % (what, lib().dirac_last_error().decode()))
+
+
+def _dp(a):
+    return a.ctypes.data_as(_DP)
+
+
+def _ip(a):
+    return a.ctypes.data_as(_IP)
+
+
+def _ptr(t):
+    """Device pointer of a contiguous complex128 CUDA tensor."""
+    import torch
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128):
+        raise ValueError("expected a contiguous complex128 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def basis_params(cfg):
+    return dirac_basis_params(Z=cfg["Z"], c=cfg["c"], R=cfg["R"], n_splines=cfg["N"], order=cfg["order"],
+                              grid=cfg["grid"], r_lin=cfg["r_lin"], n_lin=cfg["n_lin"],
+                              kappa_max=cfg["kappa_max"], two_mu_max=cfg["two_mu_max"], l_max=cfg["l_max"],
+                              quad_pts=cfg["quad"])
+
+
+def pulse_params(cfg):
+    return dirac_pulse(E0=cfg["E0"], omega=cfg["omega"], n_cycles=cfg["n_cycles"], t0=cfg.get("t0", 0.0))
+
+
+def solver_opts(cfg, **over):
+    d = dict(dt=cfg["dt"], tol=cfg.get("tol", 1e-12), tol_inner=cfg.get("tol_inner", 1e-5),
+             max_iter=cfg.get("max_iter", 500), precision=cfg.get("precision", 0),
+             max_outer=cfg.get("max_outer", 20), guess=cfg.get("guess", 1),
+             time_eval=cfg.get("time_eval", 0), precond=cfg.get("precond", 1))
+    d.update(over)
+    return dirac_solver_opts(**d)
+
+
+class Basis:
+    """dirac_basis: host-side basis, radial/pulse/angular setup data and the initial state."""
+
+    def __init__(self, cfg):
+        L = lib()
+        self.cfg = dict(cfg)
+        self.params = basis_params(cfg)
+        h = _VP()
+        n_guess = None
+        # first call sizes the state; psi0 written in library order
+        st = L.dirac_basis_build(C.byref(self.params), C.byref(h), None, None)
+        _check(st, "dirac_basis_build")
+        self._h = h
+        self.n = L.dirac_basis_dim(h)
+        self.nch = L.dirac_basis_nchannels(h)
+        self.N = cfg["N"]
+        self.nb = 2 * (self.N + 1)
+        k = np.zeros(self.nch, np.int32)
+        m = np.zeros(self.nch, np.int32)
+        _check(L.dirac_basis_channels(h, _ip(k), _ip(m)), "dirac_basis_channels")
+        self.kappa, self.two_mu = k, m
+        self.npairs = L.dirac_basis_npairs(h)
+        del n_guess
+
+    def initial_state(self):
+        """(psi0, e0): the 1s1/2 mu=+1/2 state in library order and its energy."""
+        L = lib()
+        psi = np.zeros(self.n, np.complex128)
+        e0 = C.c_double(0)
+        h = _VP()
+        _check(L.dirac_basis_build(C.byref(self.params), C.byref(h), _dp(psi.view(np.float64)), C.byref(e0)),
+               "dirac_basis_build")
+        L.dirac_basis_free(h)
+        return psi, e0.value
+
+    def radial(self, kappa):
+        S = np.zeros((self.nb, self.nb))
+        H = np.zeros((self.nb, self.nb))
+        _check(lib().dirac_basis_radial(self._h, int(kappa), _dp(S), _dp(H)), "dirac_basis_radial")
+        return S, H
+
+    def coupling(self, cfg, a, b, t):
+        X = np.zeros((self.nb, self.nb))
+        p = pulse_params(cfg)
+        _check(lib().dirac_basis_coupling(self._h, C.byref(p), int(a), int(b), float(t), _dp(X)),
+               "dirac_basis_coupling")
+        return X
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.dirac_basis_free(h)
+            self._h = None
+
+
+def angular(k1, tm1, k2, tm2, l):
+    return lib().dirac_angular(int(k1), int(tm1), int(k2), int(tm2), int(l))
+
+
+class Operator:
+    """dirac_op: the device operator of one basis, pulse and solver setting."""
+
+    def __init__(self, basis, cfg, stream=None, **opt_over):
+        import torch
+        self.basis = basis
+        self.pulse = pulse_params(cfg)
+        self.opts = solver_opts(cfg, **opt_over)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = _VP()
+        _check(lib().dirac_operator_setup(basis._h, C.byref(self.pulse), C.byref(self.opts),
+                                          C.c_void_p(stream.cuda_stream), C.byref(h)), "dirac_operator_setup")
+        self._h = h
+        self.n = basis.n
+
+    def device_bytes(self):
+        return lib().dirac_op_device_bytes(self._h)
+
+    def apply(self, sign, t, x, y):
+        _check(lib().dirac_apply(self._h, int(sign), float(t), _ptr(x), _ptr(y)), "dirac_apply")
+
+    def apply_assembled(self, sign, x, y):
+        _check(lib().dirac_apply_assembled(self._h, int(sign), _ptr(x), _ptr(y)), "dirac_apply_assembled")
+
+    def profile(self, enable=True):
+        _check(lib().dirac_profile(self._h, 1 if enable else 0), "dirac_profile")
+
+    PHASES = ("assemble", "apply", "precond", "vector")
+
+    def profile_read(self):
+        """({phase: ms}, {phase: timed launch groups}, kernel launches) since the last reset."""
+        ms = np.zeros(4)
+        cnt = np.zeros(4, np.int64)
+        nl = C.c_int64(0)
+        _check(lib().dirac_profile_read(self._h, _dp(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(nl)),
+               "dirac_profile_read")
+        return dict(zip(self.PHASES, ms)), dict(zip(self.PHASES, cnt)), nl.value
+
+    def precond(self, r, z):
+        _check(lib().dirac_precond_apply(self._h, _ptr(r), _ptr(z)), "dirac_precond_apply")
+
+    def step(self, psi, n_steps, t_start, hist=None, n_hist=0):
+        """Advance psi (CUDA complex128 tensor) in place; returns (iters, resid, n_hist)."""
+        it = np.zeros(max(n_steps, 1), np.int32)
+        res = np.zeros(max(n_steps, 1))
+        nh = C.c_int(n_hist)
+        st = lib().dirac_step(self._h, _ptr(psi), _ptr(hist) if hist is not None else None,
+                              C.byref(nh), int(n_steps), float(t_start), _ip(it), _dp(res))
+        _check(st, "dirac_step")
+        return it[:n_steps], res[:n_steps], nh.value
+
+    def observables(self, psi):
+        out = np.zeros(3)
+        _check(lib().dirac_observables(self._h, _ptr(psi), _dp(out), 3), "dirac_observables")
+        return dict(norm=out[0], energy=out[1], p_ground=out[2])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.dirac_op_free(h)
+            self._h = None

@@ -1,0 +1,610 @@
+// capi.cu -- C ABI of libdirac_gb300: operator upload, operator apply, preconditioner apply,
+// the Crank-Nicolson step loop (Eq. solPsi solved by right-preconditioned BiCGSTAB) and
+// observables.  All device work is ordered on the stream given at setup.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "internal.h"
+#include "kernels.h"
+
+namespace dg {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+#define CUDA_TRY(call)                                                                           \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+            return e_ == cudaErrorMemoryAllocation ? DIRAC_E_NOMEM : DIRAC_E_CUDA;               \
+        }                                                                                        \
+    } while (0)
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace dg
+
+struct dirac_op {
+    dg::Basis B;                 // host copy of the basis data the operator needs
+    dirac_pulse pulse{};
+    dirac_solver_opts opts{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int64_t n = 0, npairs = 0;
+    int nparts_apply = 0, nparts_vec = 0, nparts_prec = 0;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    dg::OpView ov{};
+    dg::PulseView pv{};
+    double* G = nullptr;         // G^n_l(t) bands
+    double* s = nullptr;         // time factors
+    double* t_eval = nullptr;
+    double* W = nullptr;         // coupling values, FP64
+    double2 *b, *x, *r, *rh, *p, *v, *ph, *sv, *sh, *t, *tmp;
+    double2* part_d;
+    double* part_n;
+    double2* part_d2;
+    dg::KState* ks = nullptr;
+    double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
+    int ground_ch = -1;
+    // kernel-phase timers (CUDA events on the op's stream) and the launch counter
+    bool profiling = false;
+    int64_t launches = 0;
+    double phase_ms[DIRAC_NPHASE] = {0};
+    int64_t phase_n[DIRAC_NPHASE] = {0};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> event_pool;
+};
+
+namespace dg {
+
+template <class T>
+static dirac_status dev_alloc(dirac_op* op, T** out, size_t count)
+{
+    void* p = nullptr;
+    size_t bytes = std::max<size_t>(count, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc of " + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? DIRAC_E_NOMEM : DIRAC_E_CUDA;
+    }
+    op->allocs.push_back(p);
+    op->bytes += bytes;
+    *out = (T*)p;
+    return DIRAC_OK;
+}
+
+template <class T>
+static dirac_status upload(dirac_op* op, T** out, const std::vector<T>& host)
+{
+    dirac_status s = dev_alloc(op, out, host.size());
+    if (s) return s;
+    if (!host.empty()) CUDA_TRY(cudaMemcpy(*out, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return DIRAC_OK;
+}
+
+static int grid_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+
+// ---- phase timers: one event pair around each timed launch, read back at the next sync ------
+static cudaEvent_t take_event(dirac_op* op)
+{
+    if (!op->event_pool.empty()) {
+        cudaEvent_t e = op->event_pool.back();
+        op->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct PhaseScope {
+    dirac_op* op;
+    int phase;
+    cudaEvent_t a = nullptr;
+    PhaseScope(dirac_op* o, int ph, int nlaunch) : op(o), phase(ph)
+    {
+        op->launches += nlaunch;
+        if (op->profiling) {
+            a = take_event(op);
+            cudaEventRecord(a, op->st);
+        }
+    }
+    ~PhaseScope()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(op);
+        cudaEventRecord(b, op->st);
+        op->pending.push_back({phase, {a, b}});
+    }
+};
+
+// accumulate finished event pairs (call after a stream synchronisation)
+static void collect_phases(dirac_op* op)
+{
+    for (auto& pe : op->pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+            op->phase_ms[pe.first] += ms;
+            op->phase_n[pe.first] += 1;
+        }
+        op->event_pool.push_back(pe.second.first);
+        op->event_pool.push_back(pe.second.second);
+    }
+    op->pending.clear();
+}
+
+// ---- launch helpers ------------------------------------------------------------------------
+static void launch_apply(dirac_op* op, int sign, const double2* x, double2* y, const double2* bsub,
+                         const double2* dv, double2* pdot, double* pnrm, const KState* skip)
+{
+    PhaseScope ps(op, DIRAC_PHASE_APPLY, 1);
+    dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
+    launch_apply64(grid, op->st, op->ov, sign, x, op->W, y, bsub, dv, pdot, pnrm, skip);
+}
+
+static void launch_assemble(dirac_op* op)
+{
+    PhaseScope ps(op, DIRAC_PHASE_ASSEMBLE, op->npairs ? 3 : 2);
+    k_time_factors<<<1, 128, 0, op->st>>>(op->pv, op->t_eval, op->s);
+    int be = op->ov.n1 * op->ov.bd * 4;
+    k_field_combine<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->G);
+    if (op->npairs)
+        k_assemble64<<<dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128), (unsigned)std::min<int64_t>(op->npairs, 65535)), 128, 0, op->st>>>(
+            op->ov, op->G, op->W);
+}
+
+static void launch_precond(dirac_op* op, int mode, const double2* r, const double2* v, double2* io, double2* z,
+                           double* pn)
+{
+    PhaseScope ps(op, DIRAC_PHASE_PRECOND, 1);
+    k_precond64<<<op->nparts_prec, 32, 0, op->st>>>(op->ov, mode, mode ? op->ks : nullptr, r, v, io, z, pn);
+}
+
+static void finish(dirac_op* op, int what, int np, const double2* pd, const double* pn, const double2* pd2 = nullptr)
+{
+    PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+    k_finish64<<<1, 1024, 0, op->st>>>(what, op->ks, np, pd, pn, pd2, nullptr, op->opts.max_iter);
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" const char* dirac_last_error(void) { return g_err.c_str(); }
+
+extern "C" void dirac_op_free(dirac_op* op)
+{
+    if (!op) return;
+    cudaStreamSynchronize(op->st);
+    collect_phases(op);
+    for (cudaEvent_t e : op->event_pool) cudaEventDestroy(e);
+    for (void* p : op->allocs) cudaFree(p);
+    delete op;
+}
+
+extern "C" dirac_status dirac_profile(dirac_op* op, int enable)
+{
+    if (!op) { set_error("dirac_profile: NULL op"); return DIRAC_E_ARG; }
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    collect_phases(op);
+    op->profiling = enable != 0;
+    for (int i = 0; i < DIRAC_NPHASE; i++) { op->phase_ms[i] = 0; op->phase_n[i] = 0; }
+    op->launches = 0;
+    return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches)
+{
+    if (!op) { set_error("dirac_profile_read: NULL op"); return DIRAC_E_ARG; }
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    collect_phases(op);
+    for (int i = 0; i < DIRAC_NPHASE; i++) {
+        if (ms) ms[i] = op->phase_ms[i];
+        if (count) count[i] = op->phase_n[i];
+    }
+    if (launches) *launches = op->launches;
+    return DIRAC_OK;
+}
+
+extern "C" int64_t dirac_op_device_bytes(const dirac_op* op) { return op ? (int64_t)op->bytes : -1; }
+
+extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dirac_pulse* pulse,
+                                             const dirac_solver_opts* opts, void* stream, dirac_op** out)
+{
+    if (!basis || !pulse || !opts || !out) { set_error("dirac_operator_setup: NULL argument"); return DIRAC_E_ARG; }
+    if (!(opts->dt != 0) || !(opts->tol > 0) || opts->max_iter < 1 || !(pulse->omega > 0) ||
+        !(pulse->n_cycles > 0) || (opts->precision != 0 && opts->precision != 1)) {
+        set_error("dirac_operator_setup: invalid pulse or solver options");
+        return DIRAC_E_ARG;
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        set_error("dirac_operator_setup: no CUDA device");
+        return DIRAC_E_STATE;
+    }
+    dirac_op* op = new dirac_op();
+    op->B = basis->b;
+    op->pulse = *pulse;
+    op->opts = *opts;
+    op->st = (cudaStream_t)stream;
+    cudaGetDevice(&op->device);
+    const Basis& B = op->B;
+    int n1 = B.n1, bd = B.bd, half = B.half, nk2 = 2 * B.p.kappa_max;
+    op->n = B.n();
+    op->npairs = (int64_t)B.pa.size();
+    double tau = 0.5 * opts->dt;
+    dirac_status s = DIRAC_OK;
+#define TRY(x)                          \
+    do {                                \
+        s = (x);                        \
+        if (s) { dirac_op_free(op); return s; } \
+    } while (0)
+
+    // radial blocks per kappa
+    std::vector<double> hS((size_t)nk2 * n1 * bd * 4), hH(hS.size());
+    for (int ks = 0; ks < nk2; ks++) {
+        int kappa = (ks % 2 ? 1 : -1) * (ks / 2 + 1);
+        Band Sb, Hb;
+        radial_blocks(B, kappa, Sb, Hb);
+        std::copy(Sb.v.begin(), Sb.v.end(), hS.begin() + (size_t)ks * n1 * bd * 4);
+        std::copy(Hb.v.begin(), Hb.v.end(), hH.begin() + (size_t)ks * n1 * bd * 4);
+    }
+    double *dS, *dH;
+    TRY(upload(op, &dS, hS));
+    TRY(upload(op, &dH, hH));
+    std::vector<int> kslot(B.nch);
+    for (int a = 0; a < B.nch; a++) kslot[a] = kappa_slot(B.kap[a]);
+    int *dks, *dkap;
+    TRY(upload(op, &dks, kslot));
+    TRY(upload(op, &dkap, B.kap));
+
+    // adjacency: per channel, pairs where it is the lower channel (direct) or the upper one
+    std::vector<std::vector<int>> adjp(B.nch), adjn(B.nch), adjt(B.nch);
+    for (int64_t q = 0; q < op->npairs; q++) {
+        int a = B.pa[q], b = B.pb[q];
+        adjp[a].push_back((int)q); adjn[a].push_back(b); adjt[a].push_back(0);
+        adjp[b].push_back((int)q); adjn[b].push_back(a); adjt[b].push_back(1);
+    }
+    std::vector<int> as(1, 0), ap, an, at;
+    for (int a = 0; a < B.nch; a++) {
+        ap.insert(ap.end(), adjp[a].begin(), adjp[a].end());
+        an.insert(an.end(), adjn[a].begin(), adjn[a].end());
+        at.insert(at.end(), adjt[a].begin(), adjt[a].end());
+        as.push_back((int)ap.size());
+    }
+    int *das, *dap, *dan, *dat, *dpa, *dpb, *dts, *dtl;
+    TRY(upload(op, &das, as));
+    TRY(upload(op, &dap, ap));
+    TRY(upload(op, &dan, an));
+    TRY(upload(op, &dat, at));
+    TRY(upload(op, &dpa, B.pa));
+    TRY(upload(op, &dpb, B.pb));
+    TRY(upload(op, &dts, B.pterm_start));
+    // pair terms: cA[n] = -c tau A1 m_n(ka, kb), cB[n] = c tau A2 m_n(kb, ka), m = (1, k', k, k'k)
+    std::vector<int> tl(B.pterm.size());
+    std::vector<double> tc(B.pterm.size() * 8);
+    for (int64_t q = 0; q < op->npairs; q++) {
+        double ka = B.kap[B.pa[q]], kb = B.kap[B.pb[q]];
+        double mab[4] = {1, ka, kb, ka * kb}, mba[4] = {1, kb, ka, ka * kb};
+        for (int e = B.pterm_start[q]; e < B.pterm_start[q + 1]; e++) {
+            tl[e] = B.pterm[e].l;
+            for (int nn = 0; nn < 4; nn++) {
+                tc[(size_t)e * 8 + nn] = -B.p.c * tau * B.pterm[e].A1 * mab[nn];
+                tc[(size_t)e * 8 + 4 + nn] = B.p.c * tau * B.pterm[e].A2 * mba[nn];
+            }
+        }
+    }
+    double* dtc;
+    TRY(upload(op, &dtl, tl));
+    TRY(upload(op, &dtc, tc));
+
+    // preconditioner factors, one per radial block
+    int kb = 2 * half + 1, ns = 2 * n1, wu = 2 * kb;
+    std::vector<double2> hU((size_t)nk2 * ns * (wu + 1)), hL((size_t)nk2 * ns * kb);
+    std::vector<int> hP((size_t)nk2 * ns);
+    for (int ks = 0; ks < nk2; ks++) {
+        int kappa = (ks % 2 ? 1 : -1) * (ks / 2 + 1);
+        BandLU<cd> lu;
+        if (!precond_factor(B, kappa, tau, lu)) {
+            set_error("dirac_operator_setup: singular preconditioner block");
+            dirac_op_free(op);
+            return DIRAC_E_NUMERIC;
+        }
+        for (size_t e = 0; e < lu.U.size(); e++)
+            hU[(size_t)ks * ns * (wu + 1) + e] = make_double2(lu.U[e].real(), lu.U[e].imag());
+        for (size_t e = 0; e < lu.L.size(); e++)
+            hL[(size_t)ks * ns * kb + e] = make_double2(lu.L[e].real(), lu.L[e].imag());
+        std::copy(lu.piv.begin(), lu.piv.end(), hP.begin() + (size_t)ks * ns);
+    }
+    double2 *dU, *dL;
+    int *dP, *dord;
+    TRY(upload(op, &dU, hU));
+    TRY(upload(op, &dL, hL));
+    TRY(upload(op, &dP, hP));
+    std::vector<int> ord(B.nch);
+    for (int a = 0; a < B.nch; a++) ord[a] = a;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return kslot[x] < kslot[y]; });
+    TRY(upload(op, &dord, ord));
+
+    // pulse matrices
+    PulseData P;
+    pulse_matrices(B, *pulse, P);
+    size_t be = (size_t)n1 * bd * 4;
+    std::vector<double> hM((size_t)P.L * 3 * 4 * be);
+    for (size_t gi = 0; gi < P.g.size(); gi++) std::copy(P.g[gi].v.begin(), P.g[gi].v.end(), hM.begin() + gi * be);
+    double* dM;
+    TRY(upload(op, &dM, hM));
+    TRY(dev_alloc(op, &op->G, (size_t)P.L * 4 * be));
+    TRY(dev_alloc(op, &op->s, (size_t)P.L * 3));
+    TRY(dev_alloc(op, &op->t_eval, 1));
+    TRY(dev_alloc(op, &op->W, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+
+    // Krylov vectors and reduction partials
+    int64_t n = op->n;
+    double2** vecs[] = {&op->b, &op->x, &op->r, &op->rh, &op->p, &op->v, &op->ph, &op->sv, &op->sh, &op->t, &op->tmp};
+    for (auto v : vecs) TRY(dev_alloc(op, v, (size_t)n));
+    op->nparts_apply = grid_for(n1, 128) * B.nch;
+    op->nparts_vec = grid_for(n, 256);
+    op->nparts_prec = grid_for(B.nch, 32);
+    int np = std::max({op->nparts_apply, op->nparts_vec, op->nparts_prec});
+    TRY(dev_alloc(op, &op->part_d, (size_t)np));
+    TRY(dev_alloc(op, &op->part_d2, (size_t)np));
+    TRY(dev_alloc(op, &op->part_n, (size_t)np));
+    TRY(dev_alloc(op, &op->ks, 1));
+    KState k0{};
+    k0.tol2 = opts->tol * opts->tol;
+    CUDA_TRY(cudaMemcpy(op->ks, &k0, sizeof(k0), cudaMemcpyHostToDevice));
+    // ground state of the kappa = -1, mu = +1/2 channel for the observables
+    for (int a = 0; a < B.nch; a++)
+        if (B.kap[a] == -1 && B.tmu[a] == 1) op->ground_ch = a;
+    std::vector<double2> g0(2 * n1);
+    if (op->ground_ch >= 0)
+        for (int i = 0; i < 2 * n1; i++)
+            g0[i] = make_double2(B.psi0[((size_t)op->ground_ch * 2 * n1 + i) * 2],
+                                 B.psi0[((size_t)op->ground_ch * 2 * n1 + i) * 2 + 1]);
+    TRY(upload(op, &op->psi0_g, g0));
+
+    OpView& o = op->ov;
+    o.n1 = n1; o.bd = bd; o.half = half; o.nch = B.nch; o.npairs = op->npairs; o.tau = tau; o.c = B.p.c;
+    o.ch_kslot = dks; o.ch_kappa = dkap; o.S = dS; o.H = dH;
+    o.adj_start = das; o.adj_pair = dap; o.adj_nbr = dan; o.adj_tr = dat;
+    o.pair_a = dpa; o.pair_b = dpb; o.term_start = dts; o.term_l = dtl; o.term_coef = dtc;
+    o.kb = kb; o.luU = dU; o.luL = dL; o.luP = dP; o.prec_order = dord;
+    PulseView& pv = op->pv;
+    pv.L = P.L; pv.T = P.T; pv.amp = P.amp; pv.t0 = pulse->t0; pv.dt = opts->dt;
+    for (int c = 0; c < 3; c++) { pv.w[c] = P.w[c]; pv.wt[c] = P.wt[c]; }
+    pv.M = dM;
+    *out = op;
+#undef TRY
+    return DIRAC_OK;
+}
+
+static dirac_status check_launch(const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        return DIRAC_E_CUDA;
+    }
+    return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_apply(dirac_op* op, int sign, double t, const void* x_dev, void* y_dev)
+{
+    if (!op || !x_dev || !y_dev || x_dev == y_dev || (sign != 1 && sign != -1)) {
+        set_error("dirac_apply: bad argument");
+        return DIRAC_E_ARG;
+    }
+    k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, t);
+    op->launches++;
+    launch_assemble(op);
+    launch_apply(op, sign, (const double2*)x_dev, (double2*)y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return check_launch("dirac_apply");
+}
+
+extern "C" dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, void* y_dev)
+{
+    if (!op || !x_dev || !y_dev || x_dev == y_dev || (sign != 1 && sign != -1)) {
+        set_error("dirac_apply_assembled: bad argument");
+        return DIRAC_E_ARG;
+    }
+    launch_apply(op, sign, (const double2*)x_dev, (double2*)y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    return check_launch("dirac_apply_assembled");
+}
+
+extern "C" dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, void* z_dev)
+{
+    if (!op || !r_dev || !z_dev || r_dev == z_dev) { set_error("dirac_precond_apply: bad argument"); return DIRAC_E_ARG; }
+    launch_precond(op, 0, (const double2*)r_dev, nullptr, nullptr, (double2*)z_dev, nullptr);
+    return check_launch("dirac_precond_apply");
+}
+
+// One BiCGSTAB iteration, all launches conditional on the device state (no host sync).
+static void bicgstab_iteration(dirac_op* op)
+{
+    int npa = op->nparts_apply, npp = op->nparts_prec, npv = op->nparts_vec;
+    int64_t n = op->n;
+    // p = r + beta (p - omega v); ph = M^-1 p
+    launch_precond(op, 1, op->r, op->v, op->p, op->ph, nullptr);
+    // v = A ph, <rh, v>
+    launch_apply(op, +1, op->ph, op->v, nullptr, op->rh, op->part_d, nullptr, op->ks);
+    finish(op, 2, npa, op->part_d, nullptr);
+    // s = r - alpha v; sh = M^-1 s; ||s||^2
+    launch_precond(op, 2, op->r, op->v, op->sv, op->sh, op->part_n);
+    finish(op, 3, npp, nullptr, op->part_n);
+    // t = A sh, <t, s>, <t, t>: dot of t with s via dv = s gives <s, t>; we need <t, s> = conj
+    launch_apply(op, +1, op->sh, op->t, nullptr, op->sv, op->part_d, op->part_n, op->ks);
+    finish(op, 6, npa, op->part_d, op->part_n);
+    // x += alpha ph + omega sh; r = s - omega t; <rh, r>, ||r||^2
+    {
+        PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+        k_update_xr64<<<npv, 256, 0, op->st>>>(n, op->ks, op->x, op->r, op->ph, op->sh, op->sv, op->t, op->rh,
+                                               op->part_d, op->part_n);
+    }
+    finish(op, 5, npv, op->part_d, op->part_n);
+}
+
+// r = b - A x and a fresh Krylov start (rh = r, p = v = 0)
+static void bicgstab_begin(dirac_op* op)
+{
+    int64_t n = op->n;
+    launch_apply(op, +1, op->x, op->r, op->b, nullptr, nullptr, op->part_n, nullptr);
+    finish(op, 1, op->nparts_apply, nullptr, op->part_n);
+    PhaseScope ps(op, DIRAC_PHASE_VECTOR, 3);
+    k_copy64<<<op->nparts_vec, 256, 0, op->st>>>(n, op->r, op->rh);
+    k_zero64<<<op->nparts_vec, 256, 0, op->st>>>(n, op->p);
+    k_zero64<<<op->nparts_vec, 256, 0, op->st>>>(n, op->v);
+}
+
+extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
+                                   double t_start, int* iters_out, double* resid_out)
+{
+    if (!op || !psi_dev || n_steps < 0) { set_error("dirac_step: bad argument"); return DIRAC_E_ARG; }
+    int64_t n = op->n;
+    double2* psi = (double2*)psi_dev;
+    double2* h1 = hist_dev ? (double2*)hist_dev : nullptr;
+    double2* h2 = hist_dev ? (double2*)hist_dev + n : nullptr;
+    int nh = (hist_dev && n_hist) ? std::max(0, std::min(2, *n_hist)) : 0;
+    const dirac_solver_opts& o = op->opts;
+    int npv = op->nparts_vec;
+    dirac_status result = DIRAC_OK;
+    for (int step = 0; step < n_steps; step++) {
+        double tn = t_start + step * o.dt;
+        double ts = tn + (o.time_eval ? o.dt : 0.5 * o.dt);
+        k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, ts);
+        op->launches++;
+        launch_assemble(op);
+        // b = A_- psi, ||b||^2
+        launch_apply(op, -1, psi, op->b, nullptr, nullptr, nullptr, op->part_n, nullptr);
+        finish(op, 0, op->nparts_apply, nullptr, op->part_n);
+        // initial guess
+        op->launches++;
+        if (o.guess == 1 && nh == 2)
+            k_lincomb64<<<npv, 256, 0, op->st>>>(n, 3.0, psi, -3.0, h1, 1.0, h2, op->x);
+        else if (o.guess == 1 && nh == 1)
+            k_lincomb64<<<npv, 256, 0, op->st>>>(n, 2.0, psi, -1.0, h1, 0.0, nullptr, op->x);
+        else
+            k_copy64<<<npv, 256, 0, op->st>>>(n, psi, op->x);
+        int total_it = 0, restarts = 0;
+        KState hs{};
+        for (;;) {
+            bicgstab_begin(op);
+            CUDA_TRY(cudaMemcpyAsync(&hs, op->ks, sizeof(hs), cudaMemcpyDeviceToHost, op->st));
+            CUDA_TRY(cudaStreamSynchronize(op->st));
+            collect_phases(op);
+            if (hs.status || hs.done) break;   // converged on the true residual (or failed)
+            // iterate until the recursive residual converges; check the device state every chunk
+            int chunk = 4;
+            while (true) {
+                for (int c = 0; c < chunk; c++) bicgstab_iteration(op);
+                CUDA_TRY(cudaMemcpyAsync(&hs, op->ks, sizeof(hs), cudaMemcpyDeviceToHost, op->st));
+                CUDA_TRY(cudaStreamSynchronize(op->st));
+                if (hs.done) break;
+            }
+            total_it += hs.it;
+            if (hs.status == 5 && restarts < 2) {   // breakdown: restart from the current iterate
+                restarts++;
+                continue;
+            }
+            if (hs.status) break;
+            if (total_it >= o.max_iter) { hs.status = 4; break; }
+            restarts++;
+            if (restarts > 8) { hs.status = 4; break; }
+        }
+        double res = std::sqrt(hs.rnorm2 / (hs.bnorm2 > 0 ? hs.bnorm2 : 1.0));
+        if (iters_out) iters_out[step] = total_it;
+        if (resid_out) resid_out[step] = res;
+        // history shift and accept the iterate (also on failure, as documented)
+        if (h1) {
+            if (h2 && nh >= 1) { k_copy64<<<npv, 256, 0, op->st>>>(n, h1, h2); op->launches++; }
+            k_copy64<<<npv, 256, 0, op->st>>>(n, psi, h1);
+            op->launches++;
+            nh = std::min(2, nh + 1);
+        }
+        k_copy64<<<npv, 256, 0, op->st>>>(n, op->x, psi);
+        op->launches++;
+        dirac_status e = check_launch("dirac_step");
+        if (e) return e;
+        if (hs.status) {
+            result = (dirac_status)hs.status;
+            set_error("dirac_step: step " + std::to_string(step) + " failed with status " + std::to_string(hs.status) +
+                      " (residual " + std::to_string(res) + ")");
+            break;
+        }
+    }
+    if (n_hist) *n_hist = nh;
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    collect_phases(op);
+    return result;
+}
+
+__global__ void k_observe(OpView A, const double2* __restrict__ x, const double2* __restrict__ g, int gch,
+                          double2* part_a, double* part_b, double2* part_c)
+{
+    // per thread (channel, slot): (S x), (H0 x); partial x^H S x, x^H H0 x and g^T S x_gch
+    int ch = blockIdx.y, r = blockIdx.x * blockDim.x + threadIdx.x;
+    double xs = 0, xh = 0;
+    double2 gp = make_double2(0, 0);
+    if (r < A.n1) {
+        const double2* xa = x + (int64_t)ch * 2 * A.n1;
+        int ks = A.ch_kslot[ch];
+        const double* Sk = A.S + ((int64_t)ks * A.n1 + r) * A.bd * 4;
+        const double* Hk = A.H + ((int64_t)ks * A.n1 + r) * A.bd * 4;
+        for (int t = 0; t < 2; t++) {
+            double2 sx = make_double2(0, 0), hx = make_double2(0, 0);
+            for (int d = 0; d < A.bd; d++) {
+                int rr = r + d - A.half;
+                if (rr < 0 || rr >= A.n1) continue;
+                for (int u = 0; u < 2; u++) {
+                    double2 xv = xa[2 * rr + u];
+                    double sv = Sk[d * 4 + t * 2 + u], hv = Hk[d * 4 + t * 2 + u];
+                    sx.x += sv * xv.x; sx.y += sv * xv.y;
+                    hx.x += hv * xv.x; hx.y += hv * xv.y;
+                }
+            }
+            double2 xi = xa[2 * r + t];
+            xs += xi.x * sx.x + xi.y * sx.y;
+            xh += xi.x * hx.x + xi.y * hx.y;
+            if (ch == gch) {
+                double2 gv = g[2 * r + t];  // real eigenvector (imaginary part zero)
+                gp.x += gv.x * sx.x;
+                gp.y += gv.x * sx.y;
+            }
+        }
+    }
+    int64_t slot = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    block_reduce_store(make_double2(xs, xh), 0.0, part_a, nullptr, slot);
+    block_reduce_store(gp, 0.0, part_c, nullptr, slot);
+}
+
+extern "C" dirac_status dirac_observables(dirac_op* op, const void* psi_dev, double* out, int n_out)
+{
+    if (!op || !psi_dev || !out || n_out < 1 || n_out > 3) { set_error("dirac_observables: bad argument"); return DIRAC_E_ARG; }
+    dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
+    k_observe<<<grid, 128, 0, op->st>>>(op->ov, (const double2*)psi_dev, op->psi0_g, op->ground_ch, op->part_d, nullptr,
+                                         op->part_d2);
+    dirac_status e = check_launch("dirac_observables");
+    if (e) return e;
+    int np = op->nparts_apply;
+    std::vector<double2> a(np), c(np);
+    CUDA_TRY(cudaMemcpyAsync(a.data(), op->part_d, sizeof(double2) * np, cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaMemcpyAsync(c.data(), op->part_d2, sizeof(double2) * np, cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    double ns = 0, nh = 0, gx = 0, gy = 0;
+    for (int i = 0; i < np; i++) { ns += a[i].x; nh += a[i].y; gx += c[i].x; gy += c[i].y; }
+    double vals[3] = {ns, nh, gx * gx + gy * gy};
+    for (int i = 0; i < n_out; i++) out[i] = vals[i];
+    return DIRAC_OK;
+}

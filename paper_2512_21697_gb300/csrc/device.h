@@ -1,0 +1,49 @@
+// device.h -- device-side data structures and kernel launchers of libdirac_gb300.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace dg {
+
+// BiCGSTAB scalars (always double precision, Sec. 2.4 / right-preconditioned van der Vorst form).
+struct KState {
+    double2 rho, rho_prev, alpha, omega, beta;
+    double bnorm2, rnorm2, snorm2, tol2;
+    int it, done, status, first;
+};
+
+// Geometry and operator data read by the kernels.
+struct OpView {
+    int n1, bd, half, nch;
+    int64_t npairs;
+    double tau, c;
+    const int* ch_kslot;      // [nch] radial-block index of each channel
+    const int* ch_kappa;      // [nch]
+    const double* S;          // [2 kappa_max][n1][bd][4]
+    const double* H;          // [2 kappa_max][n1][bd][4]
+    const int* adj_start;     // [nch + 1]
+    const int* adj_pair;      // pair of each adjacency entry
+    const int* adj_nbr;       // neighbour channel
+    const int* adj_tr;        // 0: channel is the pair's lower channel (W x), 1: upper (W^T x)
+    const int* pair_a;        // [npairs]
+    const int* pair_b;
+    const int* term_start;    // [npairs + 1]
+    const int* term_l;        // [nterms]
+    const double* term_coef;  // [nterms][8]: cA[4] (direct), cB[4] (transposed), tau included
+    // preconditioner: per radial block LU of M = S + i tau H0 (scalar bandwidth kb)
+    int kb;
+    const double2* luU;       // [2 kappa_max][2 n1][2 kb + 1]
+    const double2* luL;       // [2 kappa_max][2 n1][kb]
+    const int* luP;           // [2 kappa_max][2 n1]
+    const int* prec_order;    // channels sorted by radial block
+};
+
+struct PulseView {
+    int L;
+    double T, amp, t0, dt;
+    double w[3], wt[3];
+    const double* M;          // [L][3][4][n1][bd][4]
+};
+
+}  // namespace dg

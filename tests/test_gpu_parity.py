@@ -1,0 +1,139 @@
+"""GPU parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (double precision everywhere):
+ - operator apply: |y_gpu - y_oracle| <= 1e-12 max|y| -- sums of ~10^3 terms of size <= max|A| max|x|
+   in a different order differ by ~10^3 eps relative to that scale.
+ - preconditioner: relative 2-norm 1e-10 -- two LU factorisations of a matrix with condition
+   number up to ~1e4 (dense vs banded, different pivot order) agree to cond * eps.
+ - CN step / run: wavefunction relative L2 <= 1e-10, observables <= 1e-9 (the stated parity bar);
+   the GPU solves to its configured tolerance, the oracle to 1e-14.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2512_21697_gb300 import binding as B, layout, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+class Case:
+    def __init__(self, cfg, oracle_mod, **opt):
+        import torch
+        self.torch = torch
+        self.cfg = cfg
+        self.bas = B.Basis(cfg)
+        self.orc = oracle_mod.Oracle(**W.oracle_params(cfg))
+        self.perm = layout.lib_to_paper_perm(self.bas.kappa, self.bas.two_mu, cfg["kappa_max"],
+                                             cfg["two_mu_max"], cfg["N"])
+        self.inv = np.empty_like(self.perm)
+        self.inv[self.perm] = np.arange(len(self.perm))
+        self.op = B.Operator(self.bas, cfg, **opt)
+        self.dev = torch.device("cuda")
+
+    def to_dev(self, x_paper):
+        return self.torch.from_numpy(np.ascontiguousarray(x_paper[self.inv])).to(self.dev)
+
+    def from_dev(self, xd):
+        return xd.cpu().numpy()[self.perm]
+
+    def random(self, seed):
+        x = W.random_state(self.orc.n, seed)
+        x[~self.orc.active_mask()] = 0
+        return x / np.linalg.norm(x)
+
+    def T(self):
+        return self.cfg["n_cycles"] * 2 * math.pi / self.cfg["omega"]
+
+
+@pytest.fixture(scope="module", params=["tiny", "small", "slice"])
+def case(request, oracle_mod):
+    cfg = W.WORKLOADS[request.param]
+    return Case(cfg, oracle_mod, tol=cfg["tol"], max_iter=1000)
+
+
+def test_apply_matches_oracle(case):
+    x = case.random(1)
+    xd = case.to_dev(x)
+    yd = case.torch.empty_like(xd)
+    for sign in (+1, -1):
+        for t in (0.0, 0.37 * case.T(), 0.81 * case.T()):
+            case.op.apply(sign, t, xd, yd)
+            y = case.from_dev(yd)
+            ref = case.orc.apply(t, sign, x)
+            assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max(), (sign, t)
+            # unused functions stay untouched (identity)
+            assert np.all(y[~case.orc.active_mask()] == 0)
+
+
+def test_precond_matches_oracle(case):
+    r = case.random(2)
+    rd = case.to_dev(r)
+    zd = case.torch.empty_like(rd)
+    case.op.precond(rd, zd)
+    z = case.from_dev(zd)
+    ref = case.orc.precond(r)
+    assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_step_matches_oracle(case):
+    # a few steps inside the pulse (peak-field window) from a random state
+    psi0 = case.random(3)
+    t0 = 0.5 * case.T()
+    n = 3
+    psid = case.to_dev(psi0)
+    its, res, _ = case.op.step(psid, n, t0)
+    ref = psi0.copy()
+    for s in range(n):
+        ref, _, _ = case.orc.step(ref, t0 + s * case.cfg["dt"], tol=1e-14)
+    got = case.from_dev(psid)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert np.all(res <= case.cfg["tol"])
+    assert np.all(got[~case.orc.active_mask()] == 0)
+
+
+def test_small_full_run_matches_oracle(oracle_mod):
+    # the 200-step small workload from the 1s1/2 state, tol 1e-12; oracle at 1e-14
+    cfg = W.SMALL
+    c = Case(cfg, oracle_mod, tol=cfg["tol"], max_iter=1000)
+    psi0, _ = c.orc.ground_state()
+    psid = c.to_dev(psi0)
+    hist = c.torch.zeros(2 * c.bas.n, dtype=c.torch.complex128, device=c.dev)
+    its, res, nh = c.op.step(psid, cfg["steps"], 0.0, hist=hist, n_hist=0)
+    ref, _ = c.orc.run(psi0, cfg["steps"], 0.0, tol=1e-14)
+    got = c.from_dev(psid)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    o_gpu = c.op.observables(psid)
+    o_ref = c.orc.observables(ref)
+    for k in ("norm", "energy", "p_ground"):
+        assert abs(o_gpu[k] - o_ref[k]) <= 1e-9 * max(1.0, abs(o_ref[k])), k
+    assert nh == 2 and np.all(res <= cfg["tol"])
+
+
+def test_production_apply_sampled_rows(oracle_mod):
+    # full production operator on the GPU; the oracle computes sampled rows one by one
+    import torch
+    cfg = W.PRODUCTION
+    bas = B.Basis(cfg)
+    orc = oracle_mod.Oracle(**W.oracle_params(cfg))
+    op = B.Operator(bas, cfg, tol=cfg["tol"])
+    perm = layout.lib_to_paper_perm(bas.kappa, bas.two_mu, cfg["kappa_max"], cfg["two_mu_max"], cfg["N"])
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    x = W.random_state(orc.n, 5)
+    x[~orc.active_mask()] = 0
+    xd = torch.from_numpy(x[inv]).cuda()
+    yd = torch.empty_like(xd)
+    T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
+    t = 0.43 * T
+    op.apply(+1, t, xd, yd)
+    y = yd.cpu().numpy()[perm]
+    rng = np.random.default_rng(9)
+    nb = orc.nb
+    rows = np.concatenate([rng.choice(orc.n, 40, replace=False),
+                           [0, nb - 1, orc.n - 1, orc.n - nb, nb * 900 + cfg["N"], nb * 1859 + 2 * cfg["N"] + 1]])
+    ch, idx = rows // nb, rows % nb
+    ref = orc.apply_rows(t, +1, x, ch, idx)
+    scale = np.abs(y).max()
+    assert np.abs(y[rows] - ref).max() <= 1e-12 * scale
