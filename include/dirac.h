@@ -140,13 +140,15 @@ dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, vo
  * pair of CUDA events on the op's stream (0 stops); dirac_profile_read synchronises the stream and
  * returns, per phase, the summed milliseconds and the number of timed launch groups, plus the
  * number of kernel launches since the reset (counted whether or not timing is on).
- * Phases: DIRAC_PHASE_ASSEMBLE (pulse factors + coupling values), DIRAC_PHASE_APPLY (operator
- * products), DIRAC_PHASE_PRECOND, DIRAC_PHASE_VECTOR (updates, reductions, copies). */
+ * Phases: DIRAC_PHASE_ASSEMBLE (pulse factors + coupling values), DIRAC_PHASE_APPLY (double
+ * precision operator products), DIRAC_PHASE_PRECOND, DIRAC_PHASE_VECTOR (updates, reductions,
+ * copies), DIRAC_PHASE_APPLY32 (complex64 operator products of the mixed-precision inner solve). */
 #define DIRAC_PHASE_ASSEMBLE 0
 #define DIRAC_PHASE_APPLY 1
 #define DIRAC_PHASE_PRECOND 2
 #define DIRAC_PHASE_VECTOR 3
-#define DIRAC_NPHASE 4
+#define DIRAC_PHASE_APPLY32 4
+#define DIRAC_NPHASE 5
 dirac_status dirac_profile(dirac_op* op, int enable);
 dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches);
 

@@ -211,12 +211,12 @@ class Operator:
     def profile(self, enable=True):
         _check(lib().dirac_profile(self._h, 1 if enable else 0), "dirac_profile")
 
-    PHASES = ("assemble", "apply", "precond", "vector")
+    PHASES = ("assemble", "apply", "precond", "vector", "apply32")
 
     def profile_read(self):
         """({phase: ms}, {phase: timed launch groups}, kernel launches) since the last reset."""
-        ms = np.zeros(4)
-        cnt = np.zeros(4, np.int64)
+        ms = np.zeros(len(self.PHASES))
+        cnt = np.zeros(len(self.PHASES), np.int64)
         nl = C.c_int64(0)
         _check(lib().dirac_profile_read(self._h, _dp(ms), cnt.ctypes.data_as(C.POINTER(C.c_int64)), C.byref(nl)),
                "dirac_profile_read")

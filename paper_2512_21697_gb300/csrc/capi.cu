@@ -1,6 +1,7 @@
 // capi.cu -- C ABI of libdirac_gb300: operator upload, operator apply, preconditioner apply,
-// the Crank-Nicolson step loop (Eq. solPsi solved by right-preconditioned BiCGSTAB) and
-// observables.  All device work is ordered on the stream given at setup.
+// the Crank-Nicolson step loop (Eq. solPsi) solved by right-preconditioned BiCGSTAB in double
+// precision or by complex64 BiCGSTAB inside double-precision iterative refinement, phase timers
+// and observables.  All device work is ordered on the stream given at setup.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -8,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "device.h"
@@ -28,9 +30,14 @@ void set_error(const std::string& msg) { g_err = msg; }
         }                                                                                        \
     } while (0)
 
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
+// Krylov workspace in one working precision (prec 0: complex128, 1: complex64): the vectors
+// of BiCGSTAB, its scalar state and the operator data it multiplies with.
+struct Krylov {
+    int prec = 0;
+    void *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *ph = nullptr,
+         *sv = nullptr, *sh = nullptr, *t = nullptr;
+    KState* ks = nullptr;
+    const void *S = nullptr, *H = nullptr, *W = nullptr, *U = nullptr, *L = nullptr;
 };
 
 }  // namespace dg
@@ -51,11 +58,11 @@ struct dirac_op {
     double* s = nullptr;         // time factors
     double* t_eval = nullptr;
     double* W = nullptr;         // coupling values, FP64
-    double2 *b, *x, *r, *rh, *p, *v, *ph, *sv, *sh, *t, *tmp;
-    double2* part_d;
-    double* part_n;
-    double2* part_d2;
-    dg::KState* ks = nullptr;
+    float* W32 = nullptr;        // their FP32 rounding (mixed precision only)
+    dg::Krylov k64, k32;         // FP64 solve (outer loop in mixed precision), FP32 inner solve
+    double2* part_d = nullptr;
+    double* part_n = nullptr;
+    double2* part_d2 = nullptr;
     double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
     int ground_ch = -1;
     // kernel-phase timers (CUDA events on the op's stream) and the launch counter
@@ -96,7 +103,7 @@ static dirac_status upload(dirac_op* op, T** out, const std::vector<T>& host)
 
 static int grid_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
-// ---- phase timers: one event pair around each timed launch, read back at the next sync ------
+// ---- phase timers: one event pair around each timed launch group, read at the next sync ----
 static cudaEvent_t take_event(dirac_op* op)
 {
     if (!op->event_pool.empty()) {
@@ -130,7 +137,6 @@ struct PhaseScope {
     }
 };
 
-// accumulate finished event pairs (call after a stream synchronisation)
 static void collect_phases(dirac_op* op)
 {
     for (auto& pe : op->pending) {
@@ -146,12 +152,17 @@ static void collect_phases(dirac_op* op)
 }
 
 // ---- launch helpers ------------------------------------------------------------------------
-static void launch_apply(dirac_op* op, int sign, const double2* x, double2* y, const double2* bsub,
-                         const double2* dv, double2* pdot, double* pnrm, const KState* skip)
+static void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
+                           const void* dv, double2* pdot, double* pnrm, const KState* skip)
 {
-    PhaseScope ps(op, DIRAC_PHASE_APPLY, 1);
+    PhaseScope ps(op, K.prec == 0 ? DIRAC_PHASE_APPLY : DIRAC_PHASE_APPLY32, 1);
     dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
-    launch_apply64(grid, op->st, op->ov, sign, x, op->W, y, bsub, dv, pdot, pnrm, skip);
+    if (K.prec == 0)
+        launch_apply_t<double>(grid, op->st, op->ov, (const double*)K.S, (const double*)K.H, sign, x,
+                               (const double*)K.W, y, bsub, dv, pdot, pnrm, skip);
+    else
+        launch_apply_t<float>(grid, op->st, op->ov, (const float*)K.S, (const float*)K.H, sign, x,
+                              (const float*)K.W, y, bsub, dv, pdot, pnrm, skip);
 }
 
 static void launch_assemble(dirac_op* op)
@@ -161,21 +172,133 @@ static void launch_assemble(dirac_op* op)
     int be = op->ov.n1 * op->ov.bd * 4;
     k_field_combine<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->G);
     if (op->npairs)
-        k_assemble64<<<dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128), (unsigned)std::min<int64_t>(op->npairs, 65535)), 128, 0, op->st>>>(
-            op->ov, op->G, op->W);
+        k_assemble64<<<dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
+                            (unsigned)std::min<int64_t>(op->npairs, 65535)), 128, 0, op->st>>>(op->ov, op->G, op->W,
+                                                                                               op->W32);
 }
 
-static void launch_precond(dirac_op* op, int mode, const double2* r, const double2* v, double2* io, double2* z,
-                           double* pn)
+static void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks, const void* r,
+                             const void* v, void* io, void* z, double* pn)
 {
     PhaseScope ps(op, DIRAC_PHASE_PRECOND, 1);
-    k_precond64<<<op->nparts_prec, 32, 0, op->st>>>(op->ov, mode, mode ? op->ks : nullptr, r, v, io, z, pn);
+    if (K.prec == 0)
+        launch_precond_t<double>(op->nparts_prec, op->st, op->ov, K.U, K.L, mode, ks, r, v, io, z, pn);
+    else
+        launch_precond_t<float>(op->nparts_prec, op->st, op->ov, K.U, K.L, mode, ks, r, v, io, z, pn);
 }
 
-static void finish(dirac_op* op, int what, int np, const double2* pd, const double* pn, const double2* pd2 = nullptr)
+static void finish(dirac_op* op, KState* ks, int what, int np, const double2* pd, const double* pn, int max_iter)
 {
     PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
-    k_finish64<<<1, 1024, 0, op->st>>>(what, op->ks, np, pd, pn, pd2, nullptr, op->opts.max_iter);
+    k_finish64<<<1, 1024, 0, op->st>>>(what, ks, np, pd, pn, nullptr, nullptr, max_iter);
+}
+
+static void vcopy(dirac_op* op, const Krylov& K, const void* a, void* b)
+{
+    PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+    if (K.prec == 0) k_copy64<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)a, (double2*)b);
+    else k_copy32<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const float2*)a, (float2*)b);
+}
+
+static void vzero(dirac_op* op, const Krylov& K, void* a)
+{
+    PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+    if (K.prec == 0) k_zero64<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (double2*)a);
+    else k_zero32<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (float2*)a);
+}
+
+static dirac_status check_launch(const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        return DIRAC_E_CUDA;
+    }
+    return DIRAC_OK;
+}
+
+// One BiCGSTAB iteration on K (right preconditioned); every launch is conditional on K.ks.
+static void bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter)
+{
+    int npa = op->nparts_apply, npp = op->nparts_prec, npv = op->nparts_vec;
+    // p = r + beta (p - omega v); ph = M^-1 p
+    k_precond_launch(op, K, 1, K.ks, K.r, K.v, K.p, K.ph, nullptr);
+    // v = A ph, <rh, v>
+    k_apply_launch(op, K, +1, K.ph, K.v, nullptr, K.rh, op->part_d, nullptr, K.ks);
+    finish(op, K.ks, 2, npa, op->part_d, nullptr, max_iter);
+    // s = r - alpha v; sh = M^-1 s; ||s||^2
+    k_precond_launch(op, K, 2, K.ks, K.r, K.v, K.sv, K.sh, op->part_n);
+    finish(op, K.ks, 3, npp, nullptr, op->part_n, max_iter);
+    // t = A sh; <s, t>, ||t||^2 -> omega
+    k_apply_launch(op, K, +1, K.sh, K.t, nullptr, K.sv, op->part_d, op->part_n, K.ks);
+    finish(op, K.ks, 6, npa, op->part_d, op->part_n, max_iter);
+    // x += alpha ph + omega sh; r = s - omega t; <rh, r>, ||r||^2
+    {
+        PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+        if (K.prec == 0)
+            launch_update_xr_t<double>(npv, op->st, op->n, K.ks, K.x, K.r, K.ph, K.sh, K.sv, K.t, K.rh, op->part_d,
+                                       op->part_n);
+        else
+            launch_update_xr_t<float>(npv, op->st, op->n, K.ks, K.x, K.r, K.ph, K.sh, K.sv, K.t, K.rh, op->part_d,
+                                      op->part_n);
+    }
+    finish(op, K.ks, 5, npv, op->part_d, op->part_n, max_iter);
+}
+
+// r = b - A x (true residual) and a fresh Krylov start: rh = r, p = v = 0.  rel_start: the
+// tolerance is relative to this starting residual (inner solves, zero initial guess).
+static void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start = false)
+{
+    k_apply_launch(op, K, +1, K.x, K.r, K.b, nullptr, nullptr, op->part_n, nullptr);
+    finish(op, K.ks, rel_start ? 8 : 1, op->nparts_apply, nullptr, op->part_n, max_iter);
+    vcopy(op, K, K.r, K.rh);
+    vzero(op, K, K.p);
+    vzero(op, K, K.v);
+}
+
+static dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs)
+{
+    CUDA_TRY(cudaMemcpyAsync(&hs, K.ks, sizeof(hs), cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    collect_phases(op);
+    return DIRAC_OK;
+}
+
+// Iterate on K until the recursive residual meets K's tolerance (or a failure).  The device state
+// is read after every `chunk` iterations; launches after convergence exit at once.
+static dirac_status iterate(dirac_op* op, const Krylov& K, int max_iter, KState& hs)
+{
+    int chunk = op->n > (1 << 20) ? 1 : 4;   // large systems: one sync per iteration costs nothing
+    for (;;) {
+        for (int c = 0; c < chunk; c++) bicgstab_iteration(op, K, max_iter);
+        dirac_status e = read_state(op, K, hs);
+        if (e) return e;
+        if (hs.done) return DIRAC_OK;
+    }
+}
+
+// Solve A_+ x = b in K's precision to the tolerance in K.ks.  With true_check the solve ends only
+// on the true residual (restarting on recursive-residual drift or breakdown); without it, on the
+// recursive one.  Total iterations in *its.
+static dirac_status solve(dirac_op* op, const Krylov& K, int max_iter, KState& hs, int* its, bool true_check)
+{
+    int total = 0, restarts = 0;
+    for (;;) {
+        bicgstab_begin(op, K, max_iter, !true_check && restarts == 0);
+        dirac_status e = read_state(op, K, hs);
+        if (e) return e;
+        if (hs.status || hs.done) break;   // converged on the true residual (or failed)
+        e = iterate(op, K, std::max(1, max_iter - total), hs);
+        if (e) return e;
+        total += hs.it;
+        if (hs.status == 5 && restarts < 2) { restarts++; continue; }   // breakdown: restart from x
+        if (hs.status) break;
+        if (!true_check) break;
+        if (total >= max_iter) { hs.status = 4; break; }
+        if (++restarts > 8) { hs.status = 4; break; }
+    }
+    *its = total;
+    return DIRAC_OK;
 }
 
 }  // namespace dg
@@ -220,12 +343,32 @@ extern "C" dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* co
 
 extern "C" int64_t dirac_op_device_bytes(const dirac_op* op) { return op ? (int64_t)op->bytes : -1; }
 
+static dirac_status alloc_krylov(dirac_op* op, Krylov& K, int prec, double tol)
+{
+    size_t es = prec == 0 ? sizeof(double2) : sizeof(float2);
+    void** vecs[] = {&K.b, &K.x, &K.r, &K.rh, &K.p, &K.v, &K.ph, &K.sv, &K.sh, &K.t};
+    for (auto v : vecs) {
+        char* p = nullptr;
+        dirac_status s = dev_alloc(op, &p, (size_t)op->n * es);
+        if (s) return s;
+        *v = p;
+    }
+    dirac_status s = dev_alloc(op, &K.ks, 1);
+    if (s) return s;
+    KState k0{};
+    k0.tol2 = tol * tol;
+    CUDA_TRY(cudaMemcpy(K.ks, &k0, sizeof(k0), cudaMemcpyHostToDevice));
+    K.prec = prec;
+    return DIRAC_OK;
+}
+
 extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dirac_pulse* pulse,
                                              const dirac_solver_opts* opts, void* stream, dirac_op** out)
 {
     if (!basis || !pulse || !opts || !out) { set_error("dirac_operator_setup: NULL argument"); return DIRAC_E_ARG; }
     if (!(opts->dt != 0) || !(opts->tol > 0) || opts->max_iter < 1 || !(pulse->omega > 0) ||
-        !(pulse->n_cycles > 0) || (opts->precision != 0 && opts->precision != 1)) {
+        !(pulse->n_cycles > 0) || (opts->precision != 0 && opts->precision != 1) ||
+        (opts->precision == 1 && (!(opts->tol_inner > 0) || opts->tol_inner >= 1 || opts->max_outer < 1))) {
         set_error("dirac_operator_setup: invalid pulse or solver options");
         return DIRAC_E_ARG;
     }
@@ -242,13 +385,14 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     cudaGetDevice(&op->device);
     const Basis& B = op->B;
     int n1 = B.n1, bd = B.bd, half = B.half, nk2 = 2 * B.p.kappa_max;
+    bool mixed = opts->precision == 1;
     op->n = B.n();
     op->npairs = (int64_t)B.pa.size();
     double tau = 0.5 * opts->dt;
     dirac_status s = DIRAC_OK;
-#define TRY(x)                          \
-    do {                                \
-        s = (x);                        \
+#define TRY(x)                                  \
+    do {                                        \
+        s = (x);                                \
         if (s) { dirac_op_free(op); return s; } \
     } while (0)
 
@@ -270,7 +414,7 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     TRY(upload(op, &dks, kslot));
     TRY(upload(op, &dkap, B.kap));
 
-    // adjacency: per channel, pairs where it is the lower channel (direct) or the upper one
+    // adjacency: per channel, pairs where it is the lower channel (W x) or the upper one (W^T x)
     std::vector<std::vector<int>> adjp(B.nch), adjn(B.nch), adjt(B.nch);
     for (int64_t q = 0; q < op->npairs; q++) {
         int a = B.pa[q], b = B.pb[q];
@@ -351,21 +495,31 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     TRY(dev_alloc(op, &op->t_eval, 1));
     TRY(dev_alloc(op, &op->W, (size_t)std::max<int64_t>(op->npairs, 1) * be));
 
-    // Krylov vectors and reduction partials
-    int64_t n = op->n;
-    double2** vecs[] = {&op->b, &op->x, &op->r, &op->rh, &op->p, &op->v, &op->ph, &op->sv, &op->sh, &op->t, &op->tmp};
-    for (auto v : vecs) TRY(dev_alloc(op, v, (size_t)n));
+    // Krylov workspaces and reduction partials
+    TRY(alloc_krylov(op, op->k64, 0, opts->tol));
+    op->k64.S = dS; op->k64.H = dH; op->k64.W = op->W; op->k64.U = dU; op->k64.L = dL;
+    if (mixed) {
+        TRY(dev_alloc(op, &op->W32, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+        TRY(alloc_krylov(op, op->k32, 1, opts->tol_inner));
+        std::vector<float> fS(hS.begin(), hS.end()), fH(hH.begin(), hH.end());
+        std::vector<float2> fU(hU.size()), fL(hL.size());
+        for (size_t e = 0; e < hU.size(); e++) fU[e] = make_float2((float)hU[e].x, (float)hU[e].y);
+        for (size_t e = 0; e < hL.size(); e++) fL[e] = make_float2((float)hL[e].x, (float)hL[e].y);
+        float *fdS, *fdH;
+        float2 *fdU, *fdL;
+        TRY(upload(op, &fdS, fS));
+        TRY(upload(op, &fdH, fH));
+        TRY(upload(op, &fdU, fU));
+        TRY(upload(op, &fdL, fL));
+        op->k32.S = fdS; op->k32.H = fdH; op->k32.W = op->W32; op->k32.U = fdU; op->k32.L = fdL;
+    }
     op->nparts_apply = grid_for(n1, 128) * B.nch;
-    op->nparts_vec = grid_for(n, 256);
+    op->nparts_vec = grid_for(op->n, 256);
     op->nparts_prec = grid_for(B.nch, 32);
     int np = std::max({op->nparts_apply, op->nparts_vec, op->nparts_prec});
     TRY(dev_alloc(op, &op->part_d, (size_t)np));
     TRY(dev_alloc(op, &op->part_d2, (size_t)np));
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
-    TRY(dev_alloc(op, &op->ks, 1));
-    KState k0{};
-    k0.tol2 = opts->tol * opts->tol;
-    CUDA_TRY(cudaMemcpy(op->ks, &k0, sizeof(k0), cudaMemcpyHostToDevice));
     // ground state of the kappa = -1, mu = +1/2 channel for the observables
     for (int a = 0; a < B.nch; a++)
         if (B.kap[a] == -1 && B.tmu[a] == 1) op->ground_ch = a;
@@ -391,16 +545,6 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     return DIRAC_OK;
 }
 
-static dirac_status check_launch(const char* what)
-{
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error(std::string(what) + ": " + cudaGetErrorString(e));
-        return DIRAC_E_CUDA;
-    }
-    return DIRAC_OK;
-}
-
 extern "C" dirac_status dirac_apply(dirac_op* op, int sign, double t, const void* x_dev, void* y_dev)
 {
     if (!op || !x_dev || !y_dev || x_dev == y_dev || (sign != 1 && sign != -1)) {
@@ -410,7 +554,7 @@ extern "C" dirac_status dirac_apply(dirac_op* op, int sign, double t, const void
     k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, t);
     op->launches++;
     launch_assemble(op);
-    launch_apply(op, sign, (const double2*)x_dev, (double2*)y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    k_apply_launch(op, op->k64, sign, x_dev, y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
     return check_launch("dirac_apply");
 }
 
@@ -420,52 +564,15 @@ extern "C" dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void
         set_error("dirac_apply_assembled: bad argument");
         return DIRAC_E_ARG;
     }
-    launch_apply(op, sign, (const double2*)x_dev, (double2*)y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    k_apply_launch(op, op->k64, sign, x_dev, y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
     return check_launch("dirac_apply_assembled");
 }
 
 extern "C" dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, void* z_dev)
 {
     if (!op || !r_dev || !z_dev || r_dev == z_dev) { set_error("dirac_precond_apply: bad argument"); return DIRAC_E_ARG; }
-    launch_precond(op, 0, (const double2*)r_dev, nullptr, nullptr, (double2*)z_dev, nullptr);
+    k_precond_launch(op, op->k64, 0, nullptr, r_dev, nullptr, nullptr, z_dev, nullptr);
     return check_launch("dirac_precond_apply");
-}
-
-// One BiCGSTAB iteration, all launches conditional on the device state (no host sync).
-static void bicgstab_iteration(dirac_op* op)
-{
-    int npa = op->nparts_apply, npp = op->nparts_prec, npv = op->nparts_vec;
-    int64_t n = op->n;
-    // p = r + beta (p - omega v); ph = M^-1 p
-    launch_precond(op, 1, op->r, op->v, op->p, op->ph, nullptr);
-    // v = A ph, <rh, v>
-    launch_apply(op, +1, op->ph, op->v, nullptr, op->rh, op->part_d, nullptr, op->ks);
-    finish(op, 2, npa, op->part_d, nullptr);
-    // s = r - alpha v; sh = M^-1 s; ||s||^2
-    launch_precond(op, 2, op->r, op->v, op->sv, op->sh, op->part_n);
-    finish(op, 3, npp, nullptr, op->part_n);
-    // t = A sh, <t, s>, <t, t>: dot of t with s via dv = s gives <s, t>; we need <t, s> = conj
-    launch_apply(op, +1, op->sh, op->t, nullptr, op->sv, op->part_d, op->part_n, op->ks);
-    finish(op, 6, npa, op->part_d, op->part_n);
-    // x += alpha ph + omega sh; r = s - omega t; <rh, r>, ||r||^2
-    {
-        PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
-        k_update_xr64<<<npv, 256, 0, op->st>>>(n, op->ks, op->x, op->r, op->ph, op->sh, op->sv, op->t, op->rh,
-                                               op->part_d, op->part_n);
-    }
-    finish(op, 5, npv, op->part_d, op->part_n);
-}
-
-// r = b - A x and a fresh Krylov start (rh = r, p = v = 0)
-static void bicgstab_begin(dirac_op* op)
-{
-    int64_t n = op->n;
-    launch_apply(op, +1, op->x, op->r, op->b, nullptr, nullptr, op->part_n, nullptr);
-    finish(op, 1, op->nparts_apply, nullptr, op->part_n);
-    PhaseScope ps(op, DIRAC_PHASE_VECTOR, 3);
-    k_copy64<<<op->nparts_vec, 256, 0, op->st>>>(n, op->r, op->rh);
-    k_zero64<<<op->nparts_vec, 256, 0, op->st>>>(n, op->p);
-    k_zero64<<<op->nparts_vec, 256, 0, op->st>>>(n, op->v);
 }
 
 extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
@@ -479,6 +586,7 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
     int nh = (hist_dev && n_hist) ? std::max(0, std::min(2, *n_hist)) : 0;
     const dirac_solver_opts& o = op->opts;
     int npv = op->nparts_vec;
+    Krylov& K = op->k64;
     dirac_status result = DIRAC_OK;
     for (int step = 0; step < n_steps; step++) {
         double tn = t_start + step * o.dt;
@@ -487,55 +595,61 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
         op->launches++;
         launch_assemble(op);
         // b = A_- psi, ||b||^2
-        launch_apply(op, -1, psi, op->b, nullptr, nullptr, nullptr, op->part_n, nullptr);
-        finish(op, 0, op->nparts_apply, nullptr, op->part_n);
+        k_apply_launch(op, K, -1, psi, K.b, nullptr, nullptr, nullptr, op->part_n, nullptr);
+        finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, o.max_iter);
         // initial guess
-        op->launches++;
-        if (o.guess == 1 && nh == 2)
-            k_lincomb64<<<npv, 256, 0, op->st>>>(n, 3.0, psi, -3.0, h1, 1.0, h2, op->x);
-        else if (o.guess == 1 && nh == 1)
-            k_lincomb64<<<npv, 256, 0, op->st>>>(n, 2.0, psi, -1.0, h1, 0.0, nullptr, op->x);
-        else
-            k_copy64<<<npv, 256, 0, op->st>>>(n, psi, op->x);
-        int total_it = 0, restarts = 0;
+        {
+            PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+            double2* x = (double2*)K.x;
+            if (o.guess == 1 && nh == 2) k_lincomb64<<<npv, 256, 0, op->st>>>(n, 3.0, psi, -3.0, h1, 1.0, h2, x);
+            else if (o.guess == 1 && nh == 1) k_lincomb64<<<npv, 256, 0, op->st>>>(n, 2.0, psi, -1.0, h1, 0.0, nullptr, x);
+            else k_copy64<<<npv, 256, 0, op->st>>>(n, psi, x);
+        }
         KState hs{};
-        for (;;) {
-            bicgstab_begin(op);
-            CUDA_TRY(cudaMemcpyAsync(&hs, op->ks, sizeof(hs), cudaMemcpyDeviceToHost, op->st));
-            CUDA_TRY(cudaStreamSynchronize(op->st));
-            collect_phases(op);
-            if (hs.status || hs.done) break;   // converged on the true residual (or failed)
-            // iterate until the recursive residual converges; check the device state every chunk
-            int chunk = 4;
-            while (true) {
-                for (int c = 0; c < chunk; c++) bicgstab_iteration(op);
-                CUDA_TRY(cudaMemcpyAsync(&hs, op->ks, sizeof(hs), cudaMemcpyDeviceToHost, op->st));
-                CUDA_TRY(cudaStreamSynchronize(op->st));
-                if (hs.done) break;
+        int total_it = 0;
+        dirac_status e;
+        if (o.precision == 0) {
+            e = solve(op, K, o.max_iter, hs, &total_it, true);
+            if (e) return e;
+        } else {
+            // iterative refinement: r = b - A x in FP64, A d = r / ||r|| by FP32 BiCGSTAB, x += ||r|| d
+            Krylov& I = op->k32;
+            int outer = 0;
+            for (;;) {
+                bicgstab_begin(op, K, o.max_iter);   // FP64 true residual; done when ||r|| <= tol ||b||
+                e = read_state(op, K, hs);
+                if (e) return e;
+                if (hs.done || hs.status) break;
+                if (outer++ >= o.max_outer) { hs.status = 4; break; }
+                {
+                    PhaseScope ps(op, DIRAC_PHASE_VECTOR, 2);
+                    k_to_float_scaled<<<npv, 256, 0, op->st>>>(n, (const double2*)K.r, K.ks, (float2*)I.b);
+                    k_zero32<<<npv, 256, 0, op->st>>>(n, (float2*)I.x);
+                }
+                KState hi{};
+                int its = 0;
+                e = solve(op, I, o.max_iter, hi, &its, false);
+                if (e) return e;
+                total_it += its;
+                if (hi.status && hi.status != 4) { hs.status = hi.status; break; }
+                PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+                k_add_float_scaled<<<npv, 256, 0, op->st>>>(n, (const float2*)I.x, K.ks, (double2*)K.x);
             }
-            total_it += hs.it;
-            if (hs.status == 5 && restarts < 2) {   // breakdown: restart from the current iterate
-                restarts++;
-                continue;
-            }
-            if (hs.status) break;
-            if (total_it >= o.max_iter) { hs.status = 4; break; }
-            restarts++;
-            if (restarts > 8) { hs.status = 4; break; }
         }
         double res = std::sqrt(hs.rnorm2 / (hs.bnorm2 > 0 ? hs.bnorm2 : 1.0));
         if (iters_out) iters_out[step] = total_it;
         if (resid_out) resid_out[step] = res;
         // history shift and accept the iterate (also on failure, as documented)
-        if (h1) {
-            if (h2 && nh >= 1) { k_copy64<<<npv, 256, 0, op->st>>>(n, h1, h2); op->launches++; }
-            k_copy64<<<npv, 256, 0, op->st>>>(n, psi, h1);
-            op->launches++;
-            nh = std::min(2, nh + 1);
+        {
+            PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1 + (h1 ? 1 : 0) + (h2 && nh >= 1 ? 1 : 0));
+            if (h1) {
+                if (h2 && nh >= 1) k_copy64<<<npv, 256, 0, op->st>>>(n, h1, h2);
+                k_copy64<<<npv, 256, 0, op->st>>>(n, psi, h1);
+                nh = std::min(2, nh + 1);
+            }
+            k_copy64<<<npv, 256, 0, op->st>>>(n, (const double2*)K.x, psi);
         }
-        k_copy64<<<npv, 256, 0, op->st>>>(n, op->x, psi);
-        op->launches++;
-        dirac_status e = check_launch("dirac_step");
+        e = check_launch("dirac_step");
         if (e) return e;
         if (hs.status) {
             result = (dirac_status)hs.status;
@@ -551,7 +665,7 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
 }
 
 __global__ void k_observe(OpView A, const double2* __restrict__ x, const double2* __restrict__ g, int gch,
-                          double2* part_a, double* part_b, double2* part_c)
+                          double2* part_a, double2* part_c)
 {
     // per thread (channel, slot): (S x), (H0 x); partial x^H S x, x^H H0 x and g^T S x_gch
     int ch = blockIdx.y, r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -593,8 +707,9 @@ extern "C" dirac_status dirac_observables(dirac_op* op, const void* psi_dev, dou
 {
     if (!op || !psi_dev || !out || n_out < 1 || n_out > 3) { set_error("dirac_observables: bad argument"); return DIRAC_E_ARG; }
     dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
-    k_observe<<<grid, 128, 0, op->st>>>(op->ov, (const double2*)psi_dev, op->psi0_g, op->ground_ch, op->part_d, nullptr,
+    k_observe<<<grid, 128, 0, op->st>>>(op->ov, (const double2*)psi_dev, op->psi0_g, op->ground_ch, op->part_d,
                                          op->part_d2);
+    op->launches++;
     dirac_status e = check_launch("dirac_observables");
     if (e) return e;
     int np = op->nparts_apply;

@@ -34,17 +34,23 @@ __device__ __forceinline__ void block_reduce_store(double2 d, double n, double2*
 
 __global__ void k_time_factors(PulseView P, const double* t_eval, double* s);
 __global__ void k_field_combine(PulseView P, int block_elems, const double* s, double* G);
-__global__ void k_assemble64(OpView A, const double* G, double* W);
-// y = A_sign x (+ epilogues), 128 threads per block, grid (slots / 128, channels)
-void launch_apply64(dim3 grid, cudaStream_t st, const OpView& A, int sign, const double2* x, const double* W,
-                    double2* y, const double2* bsub, const double2* dv, double2* pdot, double* pnrm,
+__global__ void k_assemble64(OpView A, const double* G, double* W, float* W32);
+// y = A_sign x (+ epilogues) in precision T, 128 threads per block, grid (slots / 128, channels)
+template <class T>
+void launch_apply_t(dim3 grid, cudaStream_t st, const OpView& A, const T* S, const T* H, int sign, const void* x,
+                    const T* W, void* y, const void* bsub, const void* dv, double2* pdot, double* pnrm,
                     const KState* skip);
-__global__ void k_precond64(OpView A, int mode, const KState* st, const double2* __restrict__ r,
-                            const double2* __restrict__ v, double2* __restrict__ io, double2* __restrict__ z,
-                            double* part_nrm);
-__global__ void k_update_xr64(int64_t n, KState* st, double2* x, double2* r, const double2* ph, const double2* sh,
-                              const double2* s, const double2* t, const double2* rh, double2* part_dot,
-                              double* part_nrm);
+// z = M^-1 (prologue-formed vector) in precision T, 32 threads (channels) per block
+template <class T>
+void launch_precond_t(int blocks, cudaStream_t st, const OpView& A, const void* U, const void* L, int mode,
+                      const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
+template <class T>
+void launch_update_xr_t(int blocks, cudaStream_t st, int64_t n, const KState* ks, void* x, void* r, const void* ph,
+                        const void* sh, const void* s, const void* t, const void* rh, double2* pd, double* pn);
+__global__ void k_to_float_scaled(int64_t n, const double2* a, const KState* st, float2* b);
+__global__ void k_add_float_scaled(int64_t n, const float2* d, const KState* st, double2* x);
+__global__ void k_copy32(int64_t n, const float2* a, float2* b);
+__global__ void k_zero32(int64_t n, float2* a);
 __global__ void k_copy64(int64_t n, const double2* a, double2* b);
 __global__ void k_zero64(int64_t n, double2* a);
 __global__ void k_lincomb64(int64_t n, double c0, const double2* a, double c1, const double2* b, double c2,

@@ -137,3 +137,22 @@ def test_production_apply_sampled_rows(oracle_mod):
     ref = orc.apply_rows(t, +1, x, ch, idx)
     scale = np.abs(y).max()
     assert np.abs(y[rows] - ref).max() <= 1e-12 * scale
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "slice"])
+def test_mixed_precision_step_matches_oracle(oracle_mod, name):
+    # complex64 BiCGSTAB inside double-precision refinement: the refinement stops on the FP64 true
+    # residual, so the result meets the same parity bar as the FP64 path
+    cfg = W.WORKLOADS[name]
+    c = Case(cfg, oracle_mod, tol=cfg["tol"], max_iter=1000, precision=1, tol_inner=1e-5, max_outer=30)
+    psi0 = c.random(11)
+    t0 = 0.5 * c.T()
+    n = 3
+    psid = c.to_dev(psi0)
+    its, res, _ = c.op.step(psid, n, t0)
+    ref = psi0.copy()
+    for s in range(n):
+        ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+    got = c.from_dev(psid)
+    assert np.all(res <= cfg["tol"])
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
