@@ -152,6 +152,22 @@ dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, vo
 dirac_status dirac_profile(dirac_op* op, int enable);
 dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches);
 
+/* dirac_observables with no allocation in the call (the paper has no counterpart; this serves
+ * callers that cannot allocate GPU memory at that point: code running while a stream is captured
+ * into a CUDA graph, real-time or monitoring threads that must not hit the implicit device
+ * synchronisation of cudaMalloc/cudaFree, processes whose device footprint is fixed after setup).
+ * Same arguments, outputs and errors as dirac_observables.  Its scratch (block partials and the
+ * final sums) is a library-static device array of 2 DIRAC_STATIC_MAX_PARTIALS + 2 complex128
+ * values (about 2 MB), held by every GPU that loads the library until the process exits; it
+ * supports systems with channels x ceil((N+1)/128) <= DIRAC_STATIC_MAX_PARTIALS and returns
+ * DIRAC_E_ARG beyond that.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
+ * one array: calls whose work overlaps on the GPU (other streams, other host threads on the same
+ * device) race on it and must be serialised by the caller.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine.  The op's device must be current. */
+#define DIRAC_STATIC_MAX_PARTIALS 65536
+dirac_status dirac_observables_static(dirac_op* op, const void* psi_dev, double* out, int n_out);
+
 const char* dirac_last_error(void);
 
 #ifdef __cplusplus

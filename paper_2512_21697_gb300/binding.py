@@ -62,6 +62,7 @@ SIGNATURES = {
     "dirac_apply_assembled": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "dirac_profile": (C.c_int, [_VP, C.c_int]),
     "dirac_profile_read": (C.c_int, [_VP, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "dirac_observables_static": (C.c_int, [_VP, _VP, _DP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
 }
 
@@ -238,6 +239,12 @@ class Operator:
     def observables(self, psi):
         out = np.zeros(3)
         _check(lib().dirac_observables(self._h, _ptr(psi), _dp(out), 3), "dirac_observables")
+        return dict(norm=out[0], energy=out[1], p_ground=out[2])
+
+    def observables_static(self, psi):
+        """dirac_observables_static: the same observables with library-static scratch."""
+        out = np.zeros(3)
+        _check(lib().dirac_observables_static(self._h, _ptr(psi), _dp(out), 3), "dirac_observables_static")
         return dict(norm=out[0], energy=out[1], p_ground=out[2])
 
     def __del__(self):

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -720,6 +721,106 @@ extern "C" dirac_status dirac_observables(dirac_op* op, const void* psi_dev, dou
     double ns = 0, nh = 0, gx = 0, gy = 0;
     for (int i = 0; i < np; i++) { ns += a[i].x; nh += a[i].y; gx += c[i].x; gy += c[i].y; }
     double vals[3] = {ns, nh, gx * gx + gy * gy};
+    for (int i = 0; i < n_out; i++) out[i] = vals[i];
+    return DIRAC_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Observables with library-static scratch (no allocation in the call).
+//
+// Some callers cannot allocate GPU memory when they need the observables: code that runs while a
+// stream is being captured into a CUDA graph (an allocation there is either forbidden or breaks
+// the capture), real-time or monitoring threads that must not hit the implicit device
+// synchronisation of cudaMalloc/cudaFree, and hosts that fix the process's device footprint
+// after setup.  dirac_observables_static serves them: its block partials and the final sums live
+// in the file-scope array below, which every GPU that loads the library holds until the process
+// exits.  No cudaMalloc, cudaFree or other allocating routine is called, on the device or the host.
+// ---------------------------------------------------------------------------------------------
+static __device__ __align__(256) double2 g_obs_scratch[2 * DIRAC_STATIC_MAX_PARTIALS + 2];
+
+namespace dg {
+
+// device address of g_obs_scratch, looked up once per device (host code must not use the symbol
+// itself as a device address)
+static std::mutex g_obs_mutex;
+static void* g_obs_addr[64] = {nullptr};
+
+static dirac_status obs_scratch_address(int device, double2** out)
+{
+    if (device < 0 || device >= 64) { set_error("dirac_observables_static: device index beyond 63"); return DIRAC_E_ARG; }
+    std::lock_guard<std::mutex> lock(g_obs_mutex);
+    if (!g_obs_addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_obs_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("dirac_observables_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            return DIRAC_E_CUDA;
+        }
+        g_obs_addr[device] = p;
+    }
+    *out = (double2*)g_obs_addr[device];
+    return DIRAC_OK;
+}
+
+// fixed-order sum of the block partials into out[0] = (sum a.x, sum a.y), out[1] = (sum c.x, sum c.y)
+__global__ void k_obs_sum(int np, const double2* part_a, const double2* part_c, double2* out)
+{
+    __shared__ double s[4][1024];
+    int t = threadIdx.x;
+    double v[4] = {0, 0, 0, 0};
+    for (int i = t; i < np; i += blockDim.x) {
+        v[0] += part_a[i].x; v[1] += part_a[i].y;
+        v[2] += part_c[i].x; v[3] += part_c[i].y;
+    }
+    for (int k = 0; k < 4; k++) s[k][t] = v[k];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 4; k++) s[k][t] += s[k][t + w];
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[0] = make_double2(s[0][0], s[1][0]);
+        out[1] = make_double2(s[2][0], s[3][0]);
+    }
+}
+
+}  // namespace dg
+
+extern "C" dirac_status dirac_observables_static(dirac_op* op, const void* psi_dev, double* out, int n_out)
+{
+    if (!op || !psi_dev || !out || n_out < 1 || n_out > 3) {
+        set_error("dirac_observables_static: bad argument");
+        return DIRAC_E_ARG;
+    }
+    int np = op->nparts_apply;
+    if (np > DIRAC_STATIC_MAX_PARTIALS) {
+        set_error("dirac_observables_static: " + std::to_string(np) + " block partials (channels x ceil((N+1)/128)) "
+                  "exceed the static scratch of " + std::to_string(DIRAC_STATIC_MAX_PARTIALS) +
+                  "; use dirac_observables");
+        return DIRAC_E_ARG;
+    }
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != op->device) { set_error("dirac_observables_static: current device differs from the op's"); return DIRAC_E_STATE; }
+    double2* scratch = nullptr;
+    dirac_status e = obs_scratch_address(dev, &scratch);
+    if (e) return e;
+    // layout: [0, np) partials of (x^H S x, x^H H0 x); [M, M + np) partials of g^T S x; 2M, 2M+1: sums.
+    // Every slot read below is written earlier in this call, so nothing has to be cleared.
+    double2* pa = scratch;
+    double2* pc = scratch + DIRAC_STATIC_MAX_PARTIALS;
+    double2* sums = scratch + 2 * DIRAC_STATIC_MAX_PARTIALS;
+    dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
+    k_observe<<<grid, 128, 0, op->st>>>(op->ov, (const double2*)psi_dev, op->psi0_g, op->ground_ch, pa, pc);
+    k_obs_sum<<<1, 1024, 0, op->st>>>(np, pa, pc, sums);
+    op->launches += 2;
+    e = check_launch("dirac_observables_static");
+    if (e) return e;
+    double2 h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    double vals[3] = {h[0].x, h[0].y, h[1].x * h[1].x + h[1].y * h[1].y};
     for (int i = 0; i < n_out; i++) out[i] = vals[i];
     return DIRAC_OK;
 }

@@ -44,7 +44,12 @@ TINY = _base(R=12.0, N=12, kappa_max=2, two_mu_max=0, l_max=3, E0=2.0,
 SLICE = _base(R=300.0, N=157, grid=1, r_lin=60.0, n_lin=76, kappa_max=5, two_mu_max=0, l_max=6,
               E0=0.1, omega=omega_from_nm(800), n_cycles=3.0, dt=0.005, steps=20, tol=1e-12)
 
-WORKLOADS = {"small": SMALL, "production": PRODUCTION, "tiny": TINY, "slice": SLICE}
+# Medium system for profiler captures: the production grid family at |kappa| <= 14, 600 splines;
+# its coupling values (a few GB) exceed the L2 cache.
+MEDIUM = _base(R=300.0, N=600, grid=1, r_lin=60.0, n_lin=299, kappa_max=14, two_mu_max=0, l_max=6,
+               E0=0.1, omega=omega_from_nm(800), n_cycles=3.0, dt=0.005, steps=20, tol=1e-10)
+
+WORKLOADS = {"small": SMALL, "production": PRODUCTION, "tiny": TINY, "slice": SLICE, "medium": MEDIUM}
 
 
 def oracle_params(cfg):
