@@ -34,7 +34,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="production")
-    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--precision", type=int, default=0,
+                    help="0 FP64, 1 c64 in FP64 refinement, 2 c64 in double-float refinement")
     ap.add_argument("--t0", type=float, default=None, help="start time (default: 0, the pulse start)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
@@ -98,15 +99,56 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def operator_counts(bas, cfg):
-    """Algorithmic bytes and flops of one FP64 operator apply A_+- x."""
+def operator_counts(bas, cfg, kind):
+    """Algorithmic bytes and flops of one operator apply A_+- x.
+
+    kind 'f64': FP64 values and vectors; 'f32': FP32 values, complex64 vectors; 'df': double-float
+    values (hi + lo floats, 8 B), split input vector (16 B per complex), complex128 output.
+    Each stored coupling value (upper pairs only) is used twice (W x_b and W^T x_a), each use a real
+    x complex multiply-add (4 flop); the radial blocks S and H0 add 8 flop per entry and channel."""
     n1, bd = cfg["N"] + 1, 2 * cfg["order"] - 1
-    coup = bas.npairs * n1 * bd * 4           # stored coupling values (upper pairs only)
-    diag = bas.nch * n1 * bd * 4              # radial block entries applied (S and H0 each)
+    coup = bas.npairs * n1 * bd * 4
+    diag = bas.nch * n1 * bd * 4
     nk2 = 2 * cfg["kappa_max"]
-    flops = 8 * coup + 2 * 8 * diag           # W x and W^T x: 2 complex FMAs per value; (S + i t H) x
-    bytes_ = 8 * coup + 2 * 16 * bas.n + 2 * 8 * nk2 * n1 * bd * 4
+    flops = 8 * coup + 2 * 8 * diag
+    vb, ib, ob = {"f64": (8, 16, 16), "f32": (4, 8, 8), "df": (8, 16, 16)}[kind]
+    bytes_ = vb * coup + (ib + ob) * bas.n + 2 * vb * nk2 * n1 * bd * 4
     return coup, flops, bytes_
+
+
+def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
+    """Roofline of the dominant operator-apply kernel, timed live by the library's event timers."""
+    cands = []
+    if phase_n.get("apply", 0):
+        kind = "df" if precision == 2 else "f64"
+        cands.append(("apply", kind, phase_ms["apply"], phase_n["apply"]))
+    if phase_n.get("apply32", 0):
+        cands.append(("apply32", "f32", phase_ms["apply32"], phase_n["apply32"]))
+    name, kind, ms, cnt = max(cands, key=lambda c: c[2])
+    coup, flops, bytes_ = operator_counts(bas, cfg, kind)
+    t = ms / cnt / 1000.0
+    gbs = bytes_ / t / 1e9
+    out = {"kernel": {"f64": "k_apply<double> (FP64 operator apply)", "f32": "k_apply<float> (complex64 inner solve)",
+                      "df": "k_apply_df (double-float operator apply)"}[kind],
+           "apply_ms": t * 1000.0, "flops_per_apply": flops, "bytes_per_apply": bytes_, "gbs": gbs,
+           "traffic": None}
+    if kind == "f64":
+        tf = flops / t / 1e12
+        out.update({"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
+    else:
+        out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "peak_source": "measured copy bandwidth (MEASURED_PEAKS hbm_gbs)"})
+    return out
+
+
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
 
 
 def cpu_baseline(cfg, its_per_step, seconds, seed=5):
@@ -192,7 +234,8 @@ def main():
     bas = B.Basis(cfg)
     psi0_h, e0 = bas.initial_state()
     stream = torch.cuda.Stream()
-    op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=args.precision, max_iter=1000)
+    op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=args.precision, max_iter=1000,
+                    tol_inner=1e-5, max_outer=20)
     dev = torch.device("cuda", local)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)
@@ -247,11 +290,12 @@ def main():
     torch.cuda.synchronize()
     e2e_sps = e2e_steps / (ee0.elapsed_time(ee1) / 1000.0) * world
 
-    coup, flops, bytes_ = operator_counts(bas, cfg)
-    n_apply = max(1, phase_n["apply"])
-    t_apply = phase_ms["apply"] / n_apply / 1000.0
-    achieved_tf = flops / t_apply / 1e12
-    gbs = bytes_ / t_apply / 1e9
+    peak_bw, peak_src = hbm_peak()
+    roof = roofline(bas, cfg, phase_ms, phase_n, args.precision, peak_bw)
+    if roof["bound"] == "hbm":
+        roof["peak_source"] = "%s copy bandwidth %.1f GB/s" % ("measured" if peak_src == "measured" else
+                                                             "fallback", peak_bw)
+    coup = bas.npairs * (cfg["N"] + 1) * (2 * cfg["order"] - 1) * 4
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -260,20 +304,18 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "c64+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": ["f64", "c64+f64", "c64+df64"][args.precision], "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, cfg), "n": bas.n, "channels": bas.nch,
-                   "pairs": bas.npairs, "t_start": t0, "precision": ["fp64", "mixed c64/fp64"][args.precision],
+                   "pairs": bas.npairs, "t_start": t0,
+                   "precision": ["fp64", "mixed: c64 BiCGSTAB in FP64 refinement",
+                                 "mixed: c64 BiCGSTAB in double-float refinement"][args.precision],
                    "l2": "inputs larger than L2: %.1f GB of coupling values streamed per operator apply" %
                          (8 * coup / 1e9),
                    "parallelism": "replicas x%d (independent instances, no collective)" % world},
         "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)),
         "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "spmv_gbs": gbs,
-        "roofline": {"bound": "alu", "kernel": "k_apply64 (FP64 operator apply)", "achieved": achieved_tf,
-                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                     "gbs": gbs, "apply_ms": t_apply * 1000.0, "flops_per_apply": flops,
-                     "bytes_per_apply": bytes_},
+        "spmv_gbs": roof["gbs"],
+        "roofline": roof,
         "e2e": {"value": e2e_sps, "unit": "steps/s", "h2d_bytes_per_step": bas.n * 16,
                 "d2h_bytes_per_step": bas.n * 16},
         "gpu_launches": launches,

@@ -64,8 +64,10 @@ typedef struct {
 /* Time stepping (Eq. solPsi) and its BiCGSTAB solve.
  * dt: step; tol: relative residual ||b - A_+ x|| / ||b||; max_iter: BiCGSTAB iteration cap per
  * step (per inner solve in mixed precision); precision: 0 = FP64 throughout, 1 = complex64
- * BiCGSTAB inside FP64 iterative refinement; tol_inner: inner relative tolerance (precision 1);
- * max_outer: refinement cap (precision 1); guess: 0 = psi_n, 1 = quadratic extrapolation
+ * BiCGSTAB inside FP64 iterative refinement, 2 = as 1 with the double-precision-accurate parts
+ * (coupling assembly, A_- psi, refinement residuals) in double-float arithmetic (FP32 hi/lo pairs,
+ * error-free transforms; about 2^-44 relative per operation); tol_inner: inner relative
+ * tolerance (precision >= 1); max_outer: refinement cap (precision >= 1); guess: 0 = psi_n, 1 = quadratic extrapolation
  * 3 psi_n - 3 psi_{n-1} + psi_{n-2}; time_eval: 0 = H at t + dt/2 (midpoint rule of Sec. 2.4),
  * 1 = H at t + dt (Eq. solPsi as printed); precond: 0 = none, 1 = LU of M = S + i dt/2 H0
  * (Eq. matrixM). */
@@ -127,6 +129,15 @@ dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, void* z_dev);
  * the last iterate of that step). */
 dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
                         double t_start, int* iters_out, double* resid_out);
+
+/* dirac_step as one captured CUDA graph: the time loop, the solve restarts and the BiCGSTAB
+ * iterations are conditional WHILE nodes whose conditions the device sets from the solver state,
+ * so n_steps run with no host round trip (same arithmetic, kernel sequence and results as
+ * dirac_step).  hist_dev (device complex128[2n]) is required; n_hist as in dirac_step.  The graph
+ * is captured on the first call and re-captured when psi_dev or hist_dev changes or n_steps grows
+ * beyond the previous capacity (at least 256).  Same outputs and errors as dirac_step. */
+dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
+                       double t_start, int* iters_out, double* resid_out);
 
 /* Observables of a state (Sec. 4.3): out[0] = psi^H S psi, out[1] = psi^H H0 psi,
  * out[2] = |v_1s^T S psi_{kappa=-1, mu=+1/2}|^2 (ground-state population).  n_out <= 3. */

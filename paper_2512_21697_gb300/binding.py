@@ -59,6 +59,7 @@ SIGNATURES = {
     "dirac_precond_apply": (C.c_int, [_VP, _VP, _VP]),
     "dirac_step": (C.c_int, [_VP, _VP, _VP, _IP, C.c_int, C.c_double, _IP, _DP]),
     "dirac_observables": (C.c_int, [_VP, _VP, _DP, C.c_int]),
+    "dirac_run": (C.c_int, [_VP, _VP, _VP, _IP, C.c_int, C.c_double, _IP, _DP]),
     "dirac_apply_assembled": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "dirac_profile": (C.c_int, [_VP, C.c_int]),
     "dirac_profile_read": (C.c_int, [_VP, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
@@ -234,6 +235,16 @@ class Operator:
         st = lib().dirac_step(self._h, _ptr(psi), _ptr(hist) if hist is not None else None,
                               C.byref(nh), int(n_steps), float(t_start), _ip(it), _dp(res))
         _check(st, "dirac_step")
+        return it[:n_steps], res[:n_steps], nh.value
+
+    def run(self, psi, n_steps, t_start, hist, n_hist=0):
+        """dirac_run: n_steps in one captured CUDA graph; returns (iters, resid, n_hist)."""
+        it = np.zeros(max(n_steps, 1), np.int32)
+        res = np.zeros(max(n_steps, 1))
+        nh = C.c_int(n_hist)
+        st = lib().dirac_run(self._h, _ptr(psi), _ptr(hist), C.byref(nh), int(n_steps), float(t_start), _ip(it),
+                             _dp(res))
+        _check(st, "dirac_run")
         return it[:n_steps], res[:n_steps], nh.value
 
     def observables(self, psi):

@@ -16,6 +16,7 @@
 #include "device.h"
 #include "internal.h"
 #include "kernels.h"
+#include "op.h"
 
 namespace dg {
 
@@ -31,49 +32,8 @@ void set_error(const std::string& msg) { g_err = msg; }
         }                                                                                        \
     } while (0)
 
-// Krylov workspace in one working precision (prec 0: complex128, 1: complex64): the vectors
-// of BiCGSTAB, its scalar state and the operator data it multiplies with.
-struct Krylov {
-    int prec = 0;
-    void *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *ph = nullptr,
-         *sv = nullptr, *sh = nullptr, *t = nullptr;
-    KState* ks = nullptr;
-    const void *S = nullptr, *H = nullptr, *W = nullptr, *U = nullptr, *L = nullptr;
-};
-
 }  // namespace dg
 
-struct dirac_op {
-    dg::Basis B;                 // host copy of the basis data the operator needs
-    dirac_pulse pulse{};
-    dirac_solver_opts opts{};
-    cudaStream_t st = nullptr;
-    int device = 0;
-    int64_t n = 0, npairs = 0;
-    int nparts_apply = 0, nparts_vec = 0, nparts_prec = 0;
-    std::vector<void*> allocs;
-    size_t bytes = 0;
-    dg::OpView ov{};
-    dg::PulseView pv{};
-    double* G = nullptr;         // G^n_l(t) bands
-    double* s = nullptr;         // time factors
-    double* t_eval = nullptr;
-    double* W = nullptr;         // coupling values, FP64
-    float* W32 = nullptr;        // their FP32 rounding (mixed precision only)
-    dg::Krylov k64, k32;         // FP64 solve (outer loop in mixed precision), FP32 inner solve
-    double2* part_d = nullptr;
-    double* part_n = nullptr;
-    double2* part_d2 = nullptr;
-    double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
-    int ground_ch = -1;
-    // kernel-phase timers (CUDA events on the op's stream) and the launch counter
-    bool profiling = false;
-    int64_t launches = 0;
-    double phase_ms[DIRAC_NPHASE] = {0};
-    int64_t phase_n[DIRAC_NPHASE] = {0};
-    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
-    std::vector<cudaEvent_t> event_pool;
-};
 
 namespace dg {
 
@@ -102,7 +62,7 @@ static dirac_status upload(dirac_op* op, T** out, const std::vector<T>& host)
     return DIRAC_OK;
 }
 
-static int grid_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
+int grid_for(int64_t n, int bs) { return (int)((n + bs - 1) / bs); }
 
 // ---- phase timers: one event pair around each timed launch group, read at the next sync ----
 static cudaEvent_t take_event(dirac_op* op)
@@ -138,7 +98,7 @@ struct PhaseScope {
     }
 };
 
-static void collect_phases(dirac_op* op)
+void collect_phases(dirac_op* op)
 {
     for (auto& pe : op->pending) {
         float ms = 0;
@@ -153,11 +113,11 @@ static void collect_phases(dirac_op* op)
 }
 
 // ---- launch helpers ------------------------------------------------------------------------
-static void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
+void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
                            const void* dv, double2* pdot, double* pnrm, const KState* skip)
 {
     PhaseScope ps(op, K.prec == 0 ? DIRAC_PHASE_APPLY : DIRAC_PHASE_APPLY32, 1);
-    dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
+    dim3 grid(op->ov.nch, grid_for(op->ov.n1, 128));
     if (K.prec == 0)
         launch_apply_t<double>(grid, op->st, op->ov, (const double*)K.S, (const double*)K.H, sign, x,
                                (const double*)K.W, y, bsub, dv, pdot, pnrm, skip);
@@ -166,49 +126,114 @@ static void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* 
                               (const float*)K.W, y, bsub, dv, pdot, pnrm, skip);
 }
 
-static void launch_assemble(dirac_op* op)
+void launch_assemble(dirac_op* op)
 {
-    PhaseScope ps(op, DIRAC_PHASE_ASSEMBLE, op->npairs ? 3 : 2);
+    PhaseScope ps(op, DIRAC_PHASE_ASSEMBLE, op->npairs ? 4 : 2);
     k_time_factors<<<1, 128, 0, op->st>>>(op->pv, op->t_eval, op->s);
     int be = op->ov.n1 * op->ov.bd * 4;
+    if (op->opts.precision == 2) {
+        k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->Gdf);
+        if (op->npairs) {
+            k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, op->st>>>(
+                op->ov, be, op->Gdf, op->Kdf);
+            launch_assemble_df(dim3(grid_for(op->ov.n1, 128), (unsigned)std::min<int64_t>(op->npairs, 65535)), op->st,
+                               op->ov, op->Kdf, op->cab_df, op->Wh, op->Wl);
+        }
+        return;
+    }
     k_field_combine<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->G);
-    if (op->npairs)
+    if (op->npairs) {
+        k_build_K<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, op->st>>>(
+            op->ov, be, op->G, op->K);
         k_assemble64<<<dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
-                            (unsigned)std::min<int64_t>(op->npairs, 65535)), 128, 0, op->st>>>(op->ov, op->G, op->W,
+                            (unsigned)std::min<int64_t>(op->npairs, 65535)), 128, 0, op->st>>>(op->ov, op->K, op->W,
                                                                                                op->W32);
+    }
 }
 
-static void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks, const void* r,
+// y = A_sign x accurate to double precision (x, y, bsub complex128): native FP64 kernels, or the
+// double-float kernels in precision 2
+void apply_accurate(dirac_op* op, int sign, const void* x, void* y, const void* bsub, double* pnrm)
+{
+    if (op->opts.precision != 2) {
+        k_apply_launch(op, op->k64, sign, x, y, bsub, nullptr, nullptr, pnrm, nullptr);
+        return;
+    }
+    PhaseScope ps(op, DIRAC_PHASE_APPLY, 2);
+    k_split_vec<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)x, op->xsplit);
+    dim3 grid(op->ov.nch, grid_for(op->ov.n1, 128));
+    launch_apply_df(grid, op->st, op->ov, op->Sdf, op->Htdf, sign, op->xsplit, op->Wh, op->Wl, (double2*)y,
+                    (const double2*)bsub, pnrm);
+}
+
+// Start of a step (precision >= 1): precision 1 forms b = A_- psi and ||b||^2; precision 2 gets
+// both the residual and ||b||^2 from the fused residual kernel, so nothing happens here.
+void rhs_accurate(dirac_op* op, const void* psi)
+{
+    if (op->opts.precision == 2) return;
+    Krylov& K = op->k64;
+    apply_accurate(op, -1, psi, K.b, nullptr, op->part_n);
+    finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
+}
+
+// Refinement residual r = b - A_+ x, accurate to double precision, into k64.r, with the
+// convergence check on k64.ks.  Precision 2: r = S (psi - x) - i tau H0 (psi + x) + (W - W^T)(psi + x)
+// in one double-float pass, which also refreshes ||b||^2 = ||A_- psi||^2 (FP32 products).
+void residual_accurate(dirac_op* op, const void* psi)
+{
+    Krylov& K = op->k64;
+    if (op->opts.precision != 2) {
+        apply_accurate(op, +1, K.x, K.r, K.b, op->part_n);
+        finish(op, K.ks, 1, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
+        return;
+    }
+    {
+        PhaseScope ps(op, DIRAC_PHASE_APPLY, 2);
+        k_split_uv<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)psi, (const double2*)K.x, op->xsplit,
+                                                      op->vsplit);
+        launch_residual_df(dim3(op->ov.nch, grid_for(op->ov.n1, 128)), op->st, op->ov, op->Sdf, op->Htdf, op->xsplit,
+                           op->vsplit, op->Wh, op->Wl, (double2*)K.r, op->part_n, op->part_n2);
+    }
+    finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n2, op->opts.max_iter);
+    finish(op, K.ks, 1, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
+}
+
+void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks, const void* r,
                              const void* v, void* io, void* z, double* pn)
 {
     PhaseScope ps(op, DIRAC_PHASE_PRECOND, 1);
-    if (K.prec == 0)
-        launch_precond_t<double>(op->nparts_prec, op->st, op->ov, K.U, K.L, mode, ks, r, v, io, z, pn);
+    // complex64: one lane per channel (factor rows through shared memory); complex128: one warp per
+    // channel, which keeps every SM sub-partition's FP64 pipe busy
+    if (K.prec == 1 && op->prec_warps)
+        launch_precond_lanes_t<float>(op->prec_warps, op->st, op->ov, K.Urow, K.L, K.Dinv, op->wks, op->wfirst,
+                                      op->wcnt, mode, ks, r, v, io, z, pn);
+    else if (K.prec == 0)
+        launch_precond_t<double>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
     else
-        launch_precond_t<float>(op->nparts_prec, op->st, op->ov, K.U, K.L, mode, ks, r, v, io, z, pn);
+        launch_precond_t<float>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
 }
 
-static void finish(dirac_op* op, KState* ks, int what, int np, const double2* pd, const double* pn, int max_iter)
+void finish(dirac_op* op, KState* ks, int what, int np, const double2* pd, const double* pn, int max_iter)
 {
     PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
     k_finish64<<<1, 1024, 0, op->st>>>(what, ks, np, pd, pn, nullptr, nullptr, max_iter);
 }
 
-static void vcopy(dirac_op* op, const Krylov& K, const void* a, void* b)
+void vcopy(dirac_op* op, const Krylov& K, const void* a, void* b)
 {
     PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
     if (K.prec == 0) k_copy64<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)a, (double2*)b);
     else k_copy32<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const float2*)a, (float2*)b);
 }
 
-static void vzero(dirac_op* op, const Krylov& K, void* a)
+void vzero(dirac_op* op, const Krylov& K, void* a)
 {
     PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
     if (K.prec == 0) k_zero64<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (double2*)a);
     else k_zero32<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (float2*)a);
 }
 
-static dirac_status check_launch(const char* what)
+dirac_status check_launch(const char* what)
 {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
@@ -218,10 +243,12 @@ static dirac_status check_launch(const char* what)
     return DIRAC_OK;
 }
 
-// One BiCGSTAB iteration on K (right preconditioned); every launch is conditional on K.ks.
-static void bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter)
+// One BiCGSTAB iteration on K (right preconditioned); every launch is conditional on K.ks.  With
+// mid_check the device state is read after the s-check, so a solve that converged there launches
+// nothing more than the final update (large systems, where a host round trip is negligible).
+dirac_status bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter, bool mid_check)
 {
-    int npa = op->nparts_apply, npp = op->nparts_prec, npv = op->nparts_vec;
+    int npa = op->nparts_apply, npp = K.prec == 1 ? op->nparts_prec32 : op->nparts_prec, npv = op->nparts_vec;
     // p = r + beta (p - omega v); ph = M^-1 p
     k_precond_launch(op, K, 1, K.ks, K.r, K.v, K.p, K.ph, nullptr);
     // v = A ph, <rh, v>
@@ -230,9 +257,18 @@ static void bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter)
     // s = r - alpha v; sh = M^-1 s; ||s||^2
     k_precond_launch(op, K, 2, K.ks, K.r, K.v, K.sv, K.sh, op->part_n);
     finish(op, K.ks, 3, npp, nullptr, op->part_n, max_iter);
-    // t = A sh; <s, t>, ||t||^2 -> omega
-    k_apply_launch(op, K, +1, K.sh, K.t, nullptr, K.sv, op->part_d, op->part_n, K.ks);
-    finish(op, K.ks, 6, npa, op->part_d, op->part_n, max_iter);
+    bool skip_t = false;
+    if (mid_check) {
+        KState hs;
+        dirac_status e = read_state(op, K, hs);
+        if (e) return e;
+        skip_t = hs.done != 0;
+    }
+    if (!skip_t) {
+        // t = A sh; <s, t>, ||t||^2 -> omega
+        k_apply_launch(op, K, +1, K.sh, K.t, nullptr, K.sv, op->part_d, op->part_n, K.ks);
+        finish(op, K.ks, 6, npa, op->part_d, op->part_n, max_iter);
+    }
     // x += alpha ph + omega sh; r = s - omega t; <rh, r>, ||r||^2
     {
         PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
@@ -244,11 +280,12 @@ static void bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter)
                                       op->part_n);
     }
     finish(op, K.ks, 5, npv, op->part_d, op->part_n, max_iter);
+    return DIRAC_OK;
 }
 
 // r = b - A x (true residual) and a fresh Krylov start: rh = r, p = v = 0.  rel_start: the
 // tolerance is relative to this starting residual (inner solves, zero initial guess).
-static void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start = false)
+void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start)
 {
     k_apply_launch(op, K, +1, K.x, K.r, K.b, nullptr, nullptr, op->part_n, nullptr);
     finish(op, K.ks, rel_start ? 8 : 1, op->nparts_apply, nullptr, op->part_n, max_iter);
@@ -257,7 +294,7 @@ static void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel
     vzero(op, K, K.v);
 }
 
-static dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs)
+dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs)
 {
     CUDA_TRY(cudaMemcpyAsync(&hs, K.ks, sizeof(hs), cudaMemcpyDeviceToHost, op->st));
     CUDA_TRY(cudaStreamSynchronize(op->st));
@@ -269,9 +306,13 @@ static dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs)
 // is read after every `chunk` iterations; launches after convergence exit at once.
 static dirac_status iterate(dirac_op* op, const Krylov& K, int max_iter, KState& hs)
 {
-    int chunk = op->n > (1 << 20) ? 1 : 4;   // large systems: one sync per iteration costs nothing
+    bool large = op->n > (1 << 20);   // large systems: host round trips cost nothing
+    int chunk = large ? 1 : 4;
     for (;;) {
-        for (int c = 0; c < chunk; c++) bicgstab_iteration(op, K, max_iter);
+        for (int c = 0; c < chunk; c++) {
+            dirac_status e = bicgstab_iteration(op, K, max_iter, large);
+            if (e) return e;
+        }
         dirac_status e = read_state(op, K, hs);
         if (e) return e;
         if (hs.done) return DIRAC_OK;
@@ -313,6 +354,7 @@ extern "C" void dirac_op_free(dirac_op* op)
     if (!op) return;
     cudaStreamSynchronize(op->st);
     collect_phases(op);
+    graph_free(op);
     for (cudaEvent_t e : op->event_pool) cudaEventDestroy(e);
     for (void* p : op->allocs) cudaFree(p);
     delete op;
@@ -368,8 +410,8 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
 {
     if (!basis || !pulse || !opts || !out) { set_error("dirac_operator_setup: NULL argument"); return DIRAC_E_ARG; }
     if (!(opts->dt != 0) || !(opts->tol > 0) || opts->max_iter < 1 || !(pulse->omega > 0) ||
-        !(pulse->n_cycles > 0) || (opts->precision != 0 && opts->precision != 1) ||
-        (opts->precision == 1 && (!(opts->tol_inner > 0) || opts->tol_inner >= 1 || opts->max_outer < 1))) {
+        !(pulse->n_cycles > 0) || opts->precision < 0 || opts->precision > 2 ||
+        (opts->precision >= 1 && (!(opts->tol_inner > 0) || opts->tol_inner >= 1 || opts->max_outer < 1))) {
         set_error("dirac_operator_setup: invalid pulse or solver options");
         return DIRAC_E_ARG;
     }
@@ -386,7 +428,8 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     cudaGetDevice(&op->device);
     const Basis& B = op->B;
     int n1 = B.n1, bd = B.bd, half = B.half, nk2 = 2 * B.p.kappa_max;
-    bool mixed = opts->precision == 1;
+    bool mixed = opts->precision >= 1;
+    bool dfloat = opts->precision == 2;
     op->n = B.n();
     op->npairs = (int64_t)B.pa.size();
     double tau = 0.5 * opts->dt;
@@ -454,10 +497,50 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     double* dtc;
     TRY(upload(op, &dtl, tl));
     TRY(upload(op, &dtc, tc));
+    // distinct (k', k, l) bands and per-term references to them
+    std::vector<int> keyl, tkd(B.pterm.size()), tkt(B.pterm.size());
+    std::vector<double> keym, tcab(2 * B.pterm.size());
+    {
+        std::vector<int> index((size_t)nk2 * nk2 * (B.p.l_max + 1), -1);
+        auto key_of = [&](int kp, int k, int l) {
+            size_t id = ((size_t)kappa_slot(kp) * nk2 + kappa_slot(k)) * (B.p.l_max + 1) + l;
+            if (index[id] < 0) {
+                index[id] = (int)keyl.size();
+                keyl.push_back(l);
+                keym.insert(keym.end(), {1.0, (double)kp, (double)k, (double)kp * k});
+            }
+            return index[id];
+        };
+        for (int64_t q = 0; q < op->npairs; q++) {
+            int ka = B.kap[B.pa[q]], kb = B.kap[B.pb[q]];
+            for (int e = B.pterm_start[q]; e < B.pterm_start[q + 1]; e++) {
+                tkd[e] = key_of(ka, kb, B.pterm[e].l);
+                tkt[e] = key_of(kb, ka, B.pterm[e].l);
+                tcab[2 * e] = -B.p.c * tau * B.pterm[e].A1;
+                tcab[2 * e + 1] = B.p.c * tau * B.pterm[e].A2;
+            }
+        }
+    }
+    std::vector<int> porder(op->npairs);
+    for (int64_t q = 0; q < op->npairs; q++) porder[q] = (int)q;
+    std::stable_sort(porder.begin(), porder.end(), [&](int x, int y) {
+        int kx = kappa_slot(B.kap[B.pa[x]]) * nk2 + kappa_slot(B.kap[B.pb[x]]);
+        int ky = kappa_slot(B.kap[B.pa[y]]) * nk2 + kappa_slot(B.kap[B.pb[y]]);
+        return kx < ky;
+    });
+    int *dkl, *dkd, *dkt, *dpo;
+    double *dkm, *dcab;
+    TRY(upload(op, &dkl, keyl));
+    TRY(upload(op, &dkm, keym));
+    TRY(upload(op, &dkd, tkd));
+    TRY(upload(op, &dkt, tkt));
+    TRY(upload(op, &dcab, tcab));
+    TRY(upload(op, &dpo, porder));
 
     // preconditioner factors, one per radial block
     int kb = 2 * half + 1, ns = 2 * n1, wu = 2 * kb;
     std::vector<double2> hU((size_t)nk2 * ns * (wu + 1)), hL((size_t)nk2 * ns * kb);
+    std::vector<double2> hUr((size_t)nk2 * ns * (wu + 1)), hDi((size_t)nk2 * ns);
     std::vector<int> hP((size_t)nk2 * ns);
     for (int ks = 0; ks < nk2; ks++) {
         int kappa = (ks % 2 ? 1 : -1) * (ks / 2 + 1);
@@ -467,21 +550,49 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
             dirac_op_free(op);
             return DIRAC_E_NUMERIC;
         }
+        // column form for the back substitution: Ucol[i][k] = U[i-k][k] (zero above the first row)
+        for (int i = 0; i < ns; i++)
+            for (int k = 0; k <= wu; k++) {
+                cd u = i - k >= 0 ? lu.U[(size_t)(i - k) * (wu + 1) + k] : cd(0);
+                hU[((size_t)ks * ns + i) * (wu + 1) + k] = make_double2(u.real(), u.imag());
+            }
         for (size_t e = 0; e < lu.U.size(); e++)
-            hU[(size_t)ks * ns * (wu + 1) + e] = make_double2(lu.U[e].real(), lu.U[e].imag());
+            hUr[(size_t)ks * ns * (wu + 1) + e] = make_double2(lu.U[e].real(), lu.U[e].imag());
+        for (int i = 0; i < ns; i++) {
+            cd di = cd(1.0) / lu.U[(size_t)i * (wu + 1)];
+            hDi[(size_t)ks * ns + i] = make_double2(di.real(), di.imag());
+        }
         for (size_t e = 0; e < lu.L.size(); e++)
             hL[(size_t)ks * ns * kb + e] = make_double2(lu.L[e].real(), lu.L[e].imag());
         std::copy(lu.piv.begin(), lu.piv.end(), hP.begin() + (size_t)ks * ns);
     }
-    double2 *dU, *dL;
+    double2 *dU, *dL, *dUr, *dDi;
     int *dP, *dord;
     TRY(upload(op, &dU, hU));
     TRY(upload(op, &dL, hL));
+    TRY(upload(op, &dUr, hUr));
+    TRY(upload(op, &dDi, hDi));
     TRY(upload(op, &dP, hP));
     std::vector<int> ord(B.nch);
     for (int a = 0; a < B.nch; a++) ord[a] = a;
     std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return kslot[x] < kslot[y]; });
     TRY(upload(op, &dord, ord));
+    // same-kappa groups of at most 32 channels for the lane-per-channel preconditioner
+    if (kb == 13) {
+        std::vector<int> wk, wf, wc;
+        for (int i = 0; i < B.nch;) {
+            int j = i;
+            while (j < B.nch && kslot[ord[j]] == kslot[ord[i]] && j - i < 32) j++;
+            wk.push_back(kslot[ord[i]]);
+            wf.push_back(i);
+            wc.push_back(j - i);
+            i = j;
+        }
+        op->prec_warps = (int)wk.size();
+        TRY(upload(op, &op->wks, wk));
+        TRY(upload(op, &op->wfirst, wf));
+        TRY(upload(op, &op->wcnt, wc));
+    }
 
     // pulse matrices
     PulseData P;
@@ -494,33 +605,64 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     TRY(dev_alloc(op, &op->G, (size_t)P.L * 4 * be));
     TRY(dev_alloc(op, &op->s, (size_t)P.L * 3));
     TRY(dev_alloc(op, &op->t_eval, 1));
-    TRY(dev_alloc(op, &op->W, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+    if (!dfloat) {
+        TRY(dev_alloc(op, &op->W, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+        TRY(dev_alloc(op, &op->K, (size_t)std::max<size_t>(keyl.size(), 1) * be));
+    } else {
+        auto split = [](double v) { float h = (float)v; return make_float2(h, (float)(v - (double)h)); };
+        std::vector<float2> sdf(hS.size()), hdf(hH.size());
+        for (size_t e = 0; e < hS.size(); e++) { sdf[e] = split(hS[e]); hdf[e] = split(tau * hH[e]); }
+        TRY(upload(op, &op->Sdf, sdf));
+        TRY(upload(op, &op->Htdf, hdf));
+        std::vector<float4> cdf(B.pterm.size());
+        for (size_t e = 0; e < cdf.size(); e++) {
+            float2 a = split(tcab[2 * e]), b = split(tcab[2 * e + 1]);
+            cdf[e] = make_float4(a.x, a.y, b.x, b.y);
+        }
+        TRY(upload(op, &op->cab_df, cdf));
+        TRY(dev_alloc(op, &op->Gdf, (size_t)P.L * 4 * be));
+        TRY(dev_alloc(op, &op->Kdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
+        TRY(dev_alloc(op, &op->Wh, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+        TRY(dev_alloc(op, &op->Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+        TRY(dev_alloc(op, &op->xsplit, (size_t)op->n));
+        TRY(dev_alloc(op, &op->vsplit, (size_t)op->n));
+    }
 
     // Krylov workspaces and reduction partials
     TRY(alloc_krylov(op, op->k64, 0, opts->tol));
     op->k64.S = dS; op->k64.H = dH; op->k64.W = op->W; op->k64.U = dU; op->k64.L = dL;
+    op->k64.Urow = dUr; op->k64.Dinv = dDi;
     if (mixed) {
-        TRY(dev_alloc(op, &op->W32, (size_t)std::max<int64_t>(op->npairs, 1) * be));
+        if (!dfloat) TRY(dev_alloc(op, &op->W32, (size_t)std::max<int64_t>(op->npairs, 1) * be));
         TRY(alloc_krylov(op, op->k32, 1, opts->tol_inner));
         std::vector<float> fS(hS.begin(), hS.end()), fH(hH.begin(), hH.end());
-        std::vector<float2> fU(hU.size()), fL(hL.size());
-        for (size_t e = 0; e < hU.size(); e++) fU[e] = make_float2((float)hU[e].x, (float)hU[e].y);
-        for (size_t e = 0; e < hL.size(); e++) fL[e] = make_float2((float)hL[e].x, (float)hL[e].y);
+        auto tof = [](const std::vector<double2>& a) {
+            std::vector<float2> f(a.size());
+            for (size_t e = 0; e < a.size(); e++) f[e] = make_float2((float)a[e].x, (float)a[e].y);
+            return f;
+        };
+        std::vector<float2> fU = tof(hU), fL = tof(hL), fUr = tof(hUr), fDi = tof(hDi);
         float *fdS, *fdH;
-        float2 *fdU, *fdL;
+        float2 *fdU, *fdL, *fdUr, *fdDi;
         TRY(upload(op, &fdS, fS));
         TRY(upload(op, &fdH, fH));
         TRY(upload(op, &fdU, fU));
         TRY(upload(op, &fdL, fL));
-        op->k32.S = fdS; op->k32.H = fdH; op->k32.W = op->W32; op->k32.U = fdU; op->k32.L = fdL;
+        TRY(upload(op, &fdUr, fUr));
+        TRY(upload(op, &fdDi, fDi));
+        op->k32.Urow = fdUr; op->k32.Dinv = fdDi;
+        op->k32.S = fdS; op->k32.H = fdH; op->k32.W = dfloat ? (const void*)op->Wh : (const void*)op->W32;
+        op->k32.U = fdU; op->k32.L = fdL;
     }
     op->nparts_apply = grid_for(n1, 128) * B.nch;
     op->nparts_vec = grid_for(op->n, 256);
-    op->nparts_prec = grid_for(B.nch, 32);
-    int np = std::max({op->nparts_apply, op->nparts_vec, op->nparts_prec});
+    op->nparts_prec = grid_for(B.nch, 4);                     // ||s||^2 partials, warp-per-channel kernel
+    op->nparts_prec32 = op->prec_warps ? op->prec_warps : grid_for(B.nch, 4);   // lane-per-channel kernel
+    int np = std::max({op->nparts_apply, op->nparts_vec, op->nparts_prec, op->nparts_prec32});
     TRY(dev_alloc(op, &op->part_d, (size_t)np));
     TRY(dev_alloc(op, &op->part_d2, (size_t)np));
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
+    TRY(dev_alloc(op, &op->part_n2, (size_t)np));
     // ground state of the kappa = -1, mu = +1/2 channel for the observables
     for (int a = 0; a < B.nch; a++)
         if (B.kap[a] == -1 && B.tmu[a] == 1) op->ground_ch = a;
@@ -536,6 +678,8 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     o.ch_kslot = dks; o.ch_kappa = dkap; o.S = dS; o.H = dH;
     o.adj_start = das; o.adj_pair = dap; o.adj_nbr = dan; o.adj_tr = dat;
     o.pair_a = dpa; o.pair_b = dpb; o.term_start = dts; o.term_l = dtl; o.term_coef = dtc;
+    o.nkeys = (int)keyl.size(); o.key_l = dkl; o.key_mono = dkm; o.term_kd = dkd; o.term_kt = dkt;
+    o.term_cab = dcab; o.pair_order = dpo;
     o.kb = kb; o.luU = dU; o.luL = dL; o.luP = dP; o.prec_order = dord;
     PulseView& pv = op->pv;
     pv.L = P.L; pv.T = P.T; pv.amp = P.amp; pv.t0 = pulse->t0; pv.dt = opts->dt;
@@ -555,7 +699,7 @@ extern "C" dirac_status dirac_apply(dirac_op* op, int sign, double t, const void
     k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, t);
     op->launches++;
     launch_assemble(op);
-    k_apply_launch(op, op->k64, sign, x_dev, y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    apply_accurate(op, sign, x_dev, y_dev, nullptr, nullptr);
     return check_launch("dirac_apply");
 }
 
@@ -565,7 +709,7 @@ extern "C" dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void
         set_error("dirac_apply_assembled: bad argument");
         return DIRAC_E_ARG;
     }
-    k_apply_launch(op, op->k64, sign, x_dev, y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    apply_accurate(op, sign, x_dev, y_dev, nullptr, nullptr);
     return check_launch("dirac_apply_assembled");
 }
 
@@ -590,21 +734,21 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
     Krylov& K = op->k64;
     dirac_status result = DIRAC_OK;
     for (int step = 0; step < n_steps; step++) {
-        double tn = t_start + step * o.dt;
-        double ts = tn + (o.time_eval ? o.dt : 0.5 * o.dt);
-        k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, ts);
+        k_set_step_time<<<1, 1, 0, op->st>>>(op->t_eval, t_start, step, o.dt, o.time_eval ? o.dt : 0.5 * o.dt);
         op->launches++;
         launch_assemble(op);
-        // b = A_- psi, ||b||^2
-        k_apply_launch(op, K, -1, psi, K.b, nullptr, nullptr, nullptr, op->part_n, nullptr);
-        finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, o.max_iter);
+        // b = A_- psi, ||b||^2 (precision 2 forms them inside the residual passes)
+        if (o.precision == 0) {
+            apply_accurate(op, -1, psi, K.b, nullptr, op->part_n);
+            finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, o.max_iter);
+        } else {
+            rhs_accurate(op, psi);
+        }
         // initial guess
         {
             PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
             double2* x = (double2*)K.x;
-            if (o.guess == 1 && nh == 2) k_lincomb64<<<npv, 256, 0, op->st>>>(n, 3.0, psi, -3.0, h1, 1.0, h2, x);
-            else if (o.guess == 1 && nh == 1) k_lincomb64<<<npv, 256, 0, op->st>>>(n, 2.0, psi, -1.0, h1, 0.0, nullptr, x);
-            else k_copy64<<<npv, 256, 0, op->st>>>(n, psi, x);
+            k_extrapolate<<<npv, 256, 0, op->st>>>(n, o.guess == 1 ? nh : 0, psi, h1, h2, x);
         }
         KState hs{};
         int total_it = 0;
@@ -617,7 +761,8 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
             Krylov& I = op->k32;
             int outer = 0;
             for (;;) {
-                bicgstab_begin(op, K, o.max_iter);   // FP64 true residual; done when ||r|| <= tol ||b||
+                // true residual r = b - A x accurate to double precision; done when ||r|| <= tol ||b||
+                residual_accurate(op, psi);
                 e = read_state(op, K, hs);
                 if (e) return e;
                 if (hs.done || hs.status) break;

@@ -31,9 +31,17 @@ struct OpView {
     const int* term_start;    // [npairs + 1]
     const int* term_l;        // [nterms]
     const double* term_coef;  // [nterms][8]: cA[4] (direct), cB[4] (transposed), tau included
+    // combined radial bands K_l(k', k) = sum_n m_n(k', k) G^n_l, one per distinct (k', k, l)
+    int nkeys;
+    const int* key_l;         // [nkeys]
+    const double* key_mono;   // [nkeys][4]: 1, k', k, k' k
+    const int* term_kd;       // [nterms] key of K_l(k_a, k_b)   (direct use)
+    const int* term_kt;       // [nterms] key of K_l(k_b, k_a)   (transposed use)
+    const double* term_cab;   // [nterms][2]: -c tau A1, c tau A2
+    const int* pair_order;    // pairs grouped by (k_a, k_b) so a group's K bands stay in L2
     // preconditioner: per radial block LU of M = S + i tau H0 (scalar bandwidth kb)
     int kb;
-    const double2* luU;       // [2 kappa_max][2 n1][2 kb + 1]
+    const double2* luU;       // [2 kappa_max][2 n1][2 kb + 1], column form Ucol[i][k] = U[i-k][k]
     const double2* luL;       // [2 kappa_max][2 n1][kb]
     const int* luP;           // [2 kappa_max][2 n1]
     const int* prec_order;    // channels sorted by radial block

@@ -1,0 +1,426 @@
+// graph.cu -- the persistent multi-step driver: the whole Crank-Nicolson time loop (Eq. solPsi)
+// captured once into a CUDA graph whose data-dependent loops are conditional WHILE nodes
+//   steps -> { pulse + assembly, b = A_- psi, guess,
+//              solve: FP64 BiCGSTAB with true-residual restarts, or refinement with inner
+//              complex64 BiCGSTAB (precision >= 1),
+//              history shift }
+// so one graph launch advances n_steps with no host round trip.  Loop conditions are set on the
+// device (cudaGraphSetConditional) from the BiCGSTAB state; every loop has an iteration cap.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "device.h"
+#include "kernels.h"
+#include "op.h"
+
+namespace dg {
+
+struct StepCtl {
+    double t_start, dt, t_off;   // evaluation time of step s: t_start + s dt + t_off
+    int step, n_steps;
+    int hist_n;                  // valid history entries (0..2)
+    int status;                  // first failing status, 0 while all steps succeed
+    int accepted, restarts, outer, total_it;
+    int max_restarts, max_outer;
+};
+
+struct GraphDriver {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void* psi = nullptr;
+    const void* hist = nullptr;
+    StepCtl* ctl = nullptr;
+    int* its = nullptr;
+    double* res = nullptr;
+    int cap = 0;                 // capacity of its/res
+    cudaStream_t cap_stream = nullptr;
+};
+
+__global__ void k_ctl_begin_step(StepCtl* c, double* t_eval, cudaGraphConditionalHandle h_solve)
+{
+    *t_eval = step_time(c->t_start, c->step, c->dt, c->t_off);
+    c->accepted = 0;
+    c->restarts = 0;
+    c->outer = 0;
+    c->total_it = 0;
+    cudaGraphSetConditional(h_solve, 1);
+}
+
+// x = extrapolated guess from psi and the valid history (guess option 1), else psi
+__global__ void k_guess(const StepCtl* c, int use_hist, int64_t n, const double2* psi, const double2* h1,
+                        const double2* h2, double2* x)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int nh = use_hist ? c->hist_n : 0;
+    double2 p = psi[i], a = nh >= 1 ? h1[i] : p, b = nh >= 2 ? h2[i] : p;
+    x[i] = make_double2(extrapolate(nh, p.x, a.x, b.x), extrapolate(nh, p.y, a.y, b.y));
+}
+
+// after r = b - A x: accept on the true residual, else iterate
+__global__ void k_ctl_after_begin(StepCtl* c, const KState* ks, cudaGraphConditionalHandle h_iter)
+{
+    int it = 0;
+    if (ks->status) {
+        c->status = ks->status;
+        c->accepted = 1;
+    } else if (ks->done) {
+        c->accepted = 1;
+    } else {
+        it = 1;
+    }
+    cudaGraphSetConditional(h_iter, it);
+}
+
+__global__ void k_ctl_iter_cond(const KState* ks, cudaGraphConditionalHandle h_iter)
+{
+    cudaGraphSetConditional(h_iter, ks->done ? 0 : 1);
+}
+
+// after an iteration run of the FP64 solve: restart (breakdown or recursive-residual drift, then
+// the next begin checks the true residual) or stop
+__global__ void k_ctl_after_solve(StepCtl* c, const KState* ks, cudaGraphConditionalHandle h_solve)
+{
+    int again = 0;
+    if (!c->accepted) {
+        c->total_it += ks->it;
+        if (ks->status == 5 && c->restarts < 2) {
+            c->restarts++;
+            again = 1;
+        } else if (ks->status) {
+            c->status = ks->status;
+        } else if (++c->restarts > c->max_restarts) {
+            c->status = 4;
+        } else {
+            again = 1;
+        }
+    }
+    cudaGraphSetConditional(h_solve, again);
+}
+
+// refinement: after the accurate residual; done when it meets tol, else one inner solve and
+// another refinement pass
+__global__ void k_ctl_after_outer(StepCtl* c, const KState* ks, cudaGraphConditionalHandle h_inner,
+                                  cudaGraphConditionalHandle h_solve)
+{
+    int go = 0;
+    if (ks->status) {
+        c->status = ks->status;
+        c->accepted = 1;
+    } else if (ks->done) {
+        c->accepted = 1;
+    } else if (c->outer++ >= c->max_outer) {
+        c->status = 4;
+        c->accepted = 1;
+    } else {
+        go = 1;
+    }
+    cudaGraphSetConditional(h_inner, go);
+    cudaGraphSetConditional(h_solve, go);
+}
+
+__global__ void k_ctl_after_inner(StepCtl* c, const KState* ki)
+{
+    c->total_it += ki->it;
+    if (ki->status && ki->status != 4) c->status = ki->status;
+}
+
+// end of a refinement pass (same graph level as the refinement loop): stop on a failure
+__global__ void k_ctl_after_pass(const StepCtl* c, cudaGraphConditionalHandle h_solve)
+{
+    if (c->status) cudaGraphSetConditional(h_solve, 0);
+}
+
+__global__ void k_ctl_end_step(StepCtl* c, const KState* ks, int* its, double* res,
+                               cudaGraphConditionalHandle h_step)
+{
+    int s = c->step;
+    its[s] = c->total_it;
+    res[s] = sqrt(ks->rnorm2 / (ks->bnorm2 > 0 ? ks->bnorm2 : 1.0));
+    c->hist_n = c->hist_n < 2 ? c->hist_n + 1 : 2;
+    c->step = s + 1;
+    cudaGraphSetConditional(h_step, (c->step < c->n_steps && c->status == 0) ? 1 : 0);
+}
+
+__global__ void k_copy_if_hist(const StepCtl* c, int64_t n, const double2* a, double2* b)
+{
+    if (c->hist_n < 1) return;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = a[i];
+}
+
+// ---- capture helpers --------------------------------------------------------------------------
+
+#define G_TRY(call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            set_error(std::string("dirac_run: ") + #call + ": " + cudaGetErrorString(e_));      \
+            return DIRAC_E_CUDA;                                                                 \
+        }                                                                                        \
+    } while (0)
+
+// Append a conditional node (WHILE or IF) at the current capture point of `s`; returns its body.
+static dirac_status add_cond(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                             cudaGraph_t* body)
+{
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    G_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = type;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    G_TRY(cudaGraphAddNode(&node, g, deps, nullptr, nd, &p));
+    *body = p.conditional.phGraph_out[0];
+    G_TRY(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    return DIRAC_OK;
+}
+
+static dirac_status current_graph(cudaStream_t s, cudaGraph_t* g)
+{
+    cudaStreamCaptureStatus cs;
+    G_TRY(cudaStreamGetCaptureInfo(s, &cs, nullptr, g, nullptr, nullptr, nullptr));
+    return DIRAC_OK;
+}
+
+// Capture `fill` into `body` on a private stream (the op's launches are redirected to it).
+template <class F>
+static dirac_status capture_into(dirac_op* op, cudaGraph_t body, F fill)
+{
+    cudaStream_t s;
+    G_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    cudaStream_t saved = op->st;
+    cudaError_t e = cudaStreamBeginCaptureToGraph(s, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s);
+        set_error(std::string("dirac_run: cudaStreamBeginCaptureToGraph: ") + cudaGetErrorString(e));
+        return DIRAC_E_CUDA;
+    }
+    op->st = s;
+    dirac_status st = fill(s);
+    op->st = saved;
+    cudaGraph_t out;
+    e = cudaStreamEndCapture(s, &out);
+    cudaStreamDestroy(s);
+    if (st) return st;
+    if (e != cudaSuccess) {
+        set_error(std::string("dirac_run: cudaStreamEndCapture: ") + cudaGetErrorString(e));
+        return DIRAC_E_CUDA;
+    }
+    return DIRAC_OK;
+}
+
+// Body of the FP64 solve loop: begin (true residual), then iterations while not done.
+static dirac_status fill_solve64(dirac_op* op, GraphDriver* gd, cudaStream_t s, cudaGraphConditionalHandle h_solve)
+{
+    Krylov& K = op->k64;
+    const dirac_solver_opts& o = op->opts;
+    bicgstab_begin(op, K, o.max_iter);
+    cudaGraph_t g;
+    dirac_status st = current_graph(s, &g);
+    if (st) return st;
+    cudaGraphConditionalHandle h_iter;
+    G_TRY(cudaGraphConditionalHandleCreate(&h_iter, g, 0, 0));
+    k_ctl_after_begin<<<1, 1, 0, s>>>(gd->ctl, K.ks, h_iter);
+    cudaGraph_t body;
+    st = add_cond(s, h_iter, cudaGraphCondTypeWhile, &body);
+    if (st) return st;
+    st = capture_into(op, body, [&](cudaStream_t s2) {
+        dirac_status e = bicgstab_iteration(op, K, o.max_iter, false);
+        if (e) return e;
+        k_ctl_iter_cond<<<1, 1, 0, s2>>>(K.ks, h_iter);
+        return check_launch("dirac_run iteration");
+    });
+    if (st) return st;
+    k_ctl_after_solve<<<1, 1, 0, s>>>(gd->ctl, K.ks, h_solve);
+    return check_launch("dirac_run solve");
+}
+
+// Body of the refinement loop: accurate residual; unless accepted, one inner complex64 solve
+// (begin + iterations) and x += ||r|| d.
+static dirac_status fill_refine(dirac_op* op, GraphDriver* gd, cudaStream_t s, cudaGraphConditionalHandle h_solve,
+                                const double2* psi)
+{
+    Krylov& K = op->k64;
+    Krylov& I = op->k32;
+    const dirac_solver_opts& o = op->opts;
+    residual_accurate(op, psi);
+    cudaGraph_t g;
+    dirac_status st = current_graph(s, &g);
+    if (st) return st;
+    cudaGraphConditionalHandle h_inner;
+    G_TRY(cudaGraphConditionalHandleCreate(&h_inner, g, 0, 0));
+    k_ctl_after_outer<<<1, 1, 0, s>>>(gd->ctl, K.ks, h_inner, h_solve);
+    cudaGraph_t inner;
+    st = add_cond(s, h_inner, cudaGraphCondTypeIf, &inner);
+    if (st) return st;
+    st = capture_into(op, inner, [&](cudaStream_t s2) {
+        int npv = op->nparts_vec;
+        k_to_float_scaled<<<npv, 256, 0, s2>>>(op->n, (const double2*)K.r, K.ks, (float2*)I.b);
+        k_zero32<<<npv, 256, 0, s2>>>(op->n, (float2*)I.x);
+        bicgstab_begin(op, I, o.max_iter, true);
+        cudaGraph_t g2;
+        dirac_status e = current_graph(s2, &g2);
+        if (e) return e;
+        cudaGraphConditionalHandle h_iter;
+        G_TRY(cudaGraphConditionalHandleCreate(&h_iter, g2, 0, 0));
+        k_ctl_iter_cond<<<1, 1, 0, s2>>>(I.ks, h_iter);
+        cudaGraph_t body;
+        e = add_cond(s2, h_iter, cudaGraphCondTypeWhile, &body);
+        if (e) return e;
+        e = capture_into(op, body, [&](cudaStream_t s3) {
+            dirac_status e3 = bicgstab_iteration(op, I, o.max_iter, false);
+            if (e3) return e3;
+            k_ctl_iter_cond<<<1, 1, 0, s3>>>(I.ks, h_iter);
+            return check_launch("dirac_run inner iteration");
+        });
+        if (e) return e;
+        k_add_float_scaled<<<npv, 256, 0, s2>>>(op->n, (const float2*)I.x, K.ks, (double2*)K.x);
+        k_ctl_after_inner<<<1, 1, 0, s2>>>(gd->ctl, I.ks);
+        return check_launch("dirac_run inner");
+    });
+    if (st) return st;
+    k_ctl_after_pass<<<1, 1, 0, s>>>(gd->ctl, h_solve);
+    return check_launch("dirac_run refinement");
+}
+
+static dirac_status build_graph(dirac_op* op, GraphDriver* gd, double2* psi, double2* h1, double2* h2)
+{
+    if (gd->exec) { cudaGraphExecDestroy(gd->exec); gd->exec = nullptr; }
+    if (gd->graph) { cudaGraphDestroy(gd->graph); gd->graph = nullptr; }
+    G_TRY(cudaGraphCreate(&gd->graph, 0));
+    cudaGraphConditionalHandle h_step;
+    G_TRY(cudaGraphConditionalHandleCreate(&h_step, gd->graph, 1, cudaGraphCondAssignDefault));
+    bool prof = op->profiling;
+    op->profiling = false;   // event records are not allowed inside conditional bodies
+    int64_t launches = op->launches;
+    dirac_status st = capture_into(op, gd->graph, [&](cudaStream_t s0) {
+        cudaGraph_t step_body;
+        dirac_status e = add_cond(s0, h_step, cudaGraphCondTypeWhile, &step_body);
+        if (e) return e;
+        return capture_into(op, step_body, [&](cudaStream_t s1) {
+            Krylov& K = op->k64;
+            const dirac_solver_opts& o = op->opts;
+            cudaGraph_t g;
+            dirac_status e1 = current_graph(s1, &g);
+            if (e1) return e1;
+            cudaGraphConditionalHandle h_solve;
+            G_TRY(cudaGraphConditionalHandleCreate(&h_solve, g, 0, 0));
+            k_ctl_begin_step<<<1, 1, 0, s1>>>(gd->ctl, op->t_eval, h_solve);
+            launch_assemble(op);
+            if (o.precision == 0) {
+                apply_accurate(op, -1, psi, K.b, nullptr, op->part_n);
+                finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, o.max_iter);
+            } else {
+                rhs_accurate(op, psi);
+            }
+            int npv = op->nparts_vec;
+            k_guess<<<npv, 256, 0, s1>>>(gd->ctl, o.guess == 1, op->n, psi, h1, h2, (double2*)K.x);
+            cudaGraph_t solve_body;
+            e1 = add_cond(s1, h_solve, cudaGraphCondTypeWhile, &solve_body);
+            if (e1) return e1;
+            e1 = capture_into(op, solve_body, [&](cudaStream_t s2) {
+                return o.precision == 0 ? fill_solve64(op, gd, s2, h_solve) : fill_refine(op, gd, s2, h_solve, psi);
+            });
+            if (e1) return e1;
+            k_copy_if_hist<<<npv, 256, 0, s1>>>(gd->ctl, op->n, h1, h2);
+            k_copy64<<<npv, 256, 0, s1>>>(op->n, psi, h1);
+            k_copy64<<<npv, 256, 0, s1>>>(op->n, (const double2*)K.x, psi);
+            k_ctl_end_step<<<1, 1, 0, s1>>>(gd->ctl, K.ks, gd->its, gd->res, h_step);
+            return check_launch("dirac_run step");
+        });
+    });
+    op->profiling = prof;
+    op->launches = launches;
+    if (st) return st;
+    G_TRY(cudaGraphInstantiate(&gd->exec, gd->graph, 0));
+    gd->psi = psi;
+    gd->hist = h1;
+    return DIRAC_OK;
+}
+
+void graph_free(dirac_op* op)
+{
+    GraphDriver* gd = op->graph;
+    if (!gd) return;
+    if (gd->exec) cudaGraphExecDestroy(gd->exec);
+    if (gd->graph) cudaGraphDestroy(gd->graph);
+    cudaFree(gd->ctl);
+    cudaFree(gd->its);
+    cudaFree(gd->res);
+    delete gd;
+    op->graph = nullptr;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
+                                  double t_start, int* iters_out, double* resid_out)
+{
+    if (!op || !psi_dev || !hist_dev || n_steps < 0) {
+        set_error("dirac_run: bad argument (psi and the 2n history buffer are required)");
+        return DIRAC_E_ARG;
+    }
+    if (n_steps == 0) return DIRAC_OK;
+    if (!op->graph) op->graph = new GraphDriver();
+    GraphDriver* gd = op->graph;
+    double2* psi = (double2*)psi_dev;
+    double2* h1 = (double2*)hist_dev;
+    double2* h2 = h1 + op->n;
+    bool rebuild = !gd->exec || gd->psi != psi || gd->hist != h1;
+    if (!gd->ctl) G_TRY(cudaMalloc(&gd->ctl, sizeof(StepCtl)));
+    if (gd->cap < n_steps) {
+        cudaFree(gd->its);
+        cudaFree(gd->res);
+        gd->its = nullptr;
+        gd->res = nullptr;
+        int cap = std::max(n_steps, 256);
+        G_TRY(cudaMalloc(&gd->its, sizeof(int) * cap));
+        G_TRY(cudaMalloc(&gd->res, sizeof(double) * cap));
+        gd->cap = cap;
+        rebuild = true;
+    }
+    if (rebuild) {
+        dirac_status st = build_graph(op, gd, psi, h1, h2);
+        if (st) return st;
+    }
+    const dirac_solver_opts& o = op->opts;
+    StepCtl c{};
+    c.t_start = t_start;
+    c.dt = o.dt;
+    c.t_off = o.time_eval ? o.dt : 0.5 * o.dt;
+    c.n_steps = n_steps;
+    c.hist_n = n_hist ? std::max(0, std::min(2, *n_hist)) : 0;
+    c.max_restarts = 8;
+    c.max_outer = o.max_outer;
+    G_TRY(cudaMemcpyAsync(gd->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, op->st));
+    G_TRY(cudaGraphLaunch(gd->exec, op->st));
+    std::vector<int> its(n_steps);
+    std::vector<double> res(n_steps);
+    G_TRY(cudaMemcpyAsync(&c, gd->ctl, sizeof(c), cudaMemcpyDeviceToHost, op->st));
+    G_TRY(cudaMemcpyAsync(its.data(), gd->its, sizeof(int) * n_steps, cudaMemcpyDeviceToHost, op->st));
+    G_TRY(cudaMemcpyAsync(res.data(), gd->res, sizeof(double) * n_steps, cudaMemcpyDeviceToHost, op->st));
+    G_TRY(cudaStreamSynchronize(op->st));
+    op->launches += 1;   // one graph launch (its kernels are not counted individually)
+    for (int s = 0; s < c.step && s < n_steps; s++) {
+        if (iters_out) iters_out[s] = its[s];
+        if (resid_out) resid_out[s] = res[s];
+    }
+    if (n_hist) *n_hist = c.hist_n;
+    if (c.status) {
+        set_error("dirac_run: step " + std::to_string(c.step - 1) + " failed with status " + std::to_string(c.status));
+        return (dirac_status)c.status;
+    }
+    return DIRAC_OK;
+}

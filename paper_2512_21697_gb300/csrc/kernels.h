@@ -34,22 +34,40 @@ __device__ __forceinline__ void block_reduce_store(double2 d, double n, double2*
 
 __global__ void k_time_factors(PulseView P, const double* t_eval, double* s);
 __global__ void k_field_combine(PulseView P, int block_elems, const double* s, double* G);
-__global__ void k_assemble64(OpView A, const double* G, double* W, float* W32);
-// y = A_sign x (+ epilogues) in precision T, 128 threads per block, grid (slots / 128, channels)
+__global__ void k_build_K(OpView A, int block_elems, const double* G, double* K);
+__global__ void k_assemble64(OpView A, const double* K, double* W, float* W32);
+// y = A_sign x (+ epilogues) in precision T, 128 threads per block, grid (channels, slots / 128)
 template <class T>
 void launch_apply_t(dim3 grid, cudaStream_t st, const OpView& A, const T* S, const T* H, int sign, const void* x,
                     const T* W, void* y, const void* bsub, const void* dv, double2* pdot, double* pnrm,
                     const KState* skip);
 // z = M^-1 (prologue-formed vector) in precision T, 32 threads (channels) per block
 template <class T>
-void launch_precond_t(int blocks, cudaStream_t st, const OpView& A, const void* U, const void* L, int mode,
-                      const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
+void launch_precond_t(int blocks, cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv,
+                      int mode, const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
+// lane-per-channel preconditioner (band width 13), one warp per same-kappa channel group
+template <class T>
+void launch_precond_lanes_t(int nwarps, cudaStream_t st, const OpView& A, const void* Urow, const void* L,
+                            const void* Dinv, const int* wks, const int* wfirst, const int* wcnt, int mode,
+                            const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
 template <class T>
 void launch_update_xr_t(int blocks, cudaStream_t st, int64_t n, const KState* ks, void* x, void* r, const void* ph,
                         const void* sh, const void* s, const void* t, const void* rh, double2* pd, double* pn);
 __global__ void k_to_float_scaled(int64_t n, const double2* a, const KState* st, float2* b);
 __global__ void k_add_float_scaled(int64_t n, const float2* d, const KState* st, double2* x);
 __global__ void k_copy32(int64_t n, const float2* a, float2* b);
+// double-float path (precision 2)
+__global__ void k_split_vec(int64_t n, const double2* __restrict__ x, float4* __restrict__ xd);
+__global__ void k_field_combine_df(PulseView P, int block_elems, const double* s, float2* G);
+__global__ void k_build_K_df(OpView A, int block_elems, const float2* G, float2* K);
+void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* K, const float4* cab, float* Wh,
+                        float* Wl);
+__global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
+                           float4* __restrict__ u, float4* __restrict__ v);
+void launch_residual_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
+                        const float4* v, const float* Wh, const float* Wl, double2* r, double* pr, double* pb);
+void launch_apply_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, int sign,
+                     const float4* x, const float* Wh, const float* Wl, double2* y, const double2* bsub, double* pn);
 __global__ void k_zero32(int64_t n, float2* a);
 __global__ void k_copy64(int64_t n, const double2* a, double2* b);
 __global__ void k_zero64(int64_t n, double2* a);
@@ -58,5 +76,22 @@ __global__ void k_lincomb64(int64_t n, double c0, const double2* a, double c1, c
 __global__ void k_finish64(int what, KState* st, int np, const double2* pd, const double* pn, const double2* pd2,
                            const double* pn2, int max_iter);
 __global__ void k_set_time(double* t_eval, double t);
+__global__ void k_set_step_time(double* t_eval, double t_start, int step, double dt, double t_off);
+// evaluation time of step `step`: (t_start + step dt) + t_off, each operation rounded separately
+// (no contraction), so the host-driven and the graph-driven loops agree to the last bit
+__device__ __forceinline__ double step_time(double t_start, int step, double dt, double t_off)
+{
+    return __dadd_rn(__dadd_rn(t_start, __dmul_rn((double)step, dt)), t_off);
+}
+
+// initial guess from the last states, polynomial extrapolation in time: 3 psi - 3 h1 + h2 (two
+// past states), 2 psi - h1 (one), psi (none); explicit rounding so both step loops agree bitwise
+__device__ __forceinline__ double extrapolate(int nh, double p, double a, double b)
+{
+    if (nh >= 2) return __dadd_rn(__dmul_rn(3.0, __dsub_rn(p, a)), b);
+    if (nh == 1) return __dsub_rn(__dmul_rn(2.0, p), a);
+    return p;
+}
+__global__ void k_extrapolate(int64_t n, int nh, const double2* psi, const double2* h1, const double2* h2, double2* x);
 
 }  // namespace dg

@@ -50,53 +50,77 @@ __global__ void k_field_combine(PulseView P, int block_elems, const double* s, d
 
 // ---------------------------------------------------------------------------------------------
 // Coupling assembly: W_ab = tau X_ab(t) for every coupled pair a < b (and its FP32 rounding
-// when W32 is given),
-//   W[r][d][t][u] = sum_terms sum_n cA[n] G^n_l[r][d][t][u] + cB[n] G^n_l[r'][2h-d][u][t],
-// r' = r + d - h; functions unused at slot 0 give zero rows/columns.
+// when W32 is given).  With G^n_l = sum_c s_{l,c}(t) g^n_{l,c} and the kappa monomials
+// m(k', k) = (1, k', k, k' k), Eq. fullH gives
+//   tau X_ab = sum_terms [ -c tau A1 K_l(ka, kb) + c tau A2 K_l(kb, ka)^T ],
+//   K_l(k', k) = sum_n m_n(k', k) G^n_l,
+// so K is built once per distinct (k', k, l) and shared by every pair (all mu) that uses it.
+// Functions unused at slot 0 give zero rows/columns.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ bool used_fn(int kappa, int slot, int type)
 {
     return slot != 0 || (type == 0 ? kappa == -1 : kappa == 1);
 }
 
-__global__ void k_assemble64(OpView A, const double* G, double* W, float* W32)
+// K[key][e] = sum_n m_n(key) G^n_l[e]  (l = key_l[key]), e over one band
+__global__ void k_build_K(OpView A, int block_elems, const double* G, double* K)
+{
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= block_elems) return;
+    for (int key = blockIdx.y; key < A.nkeys; key += gridDim.y) {
+        const double* m = A.key_mono + (int64_t)key * 4;
+        const double* Gl = G + (int64_t)A.key_l[key] * 4 * block_elems + e;
+        double v = m[0] * Gl[0];
+        v = fma(m[1], Gl[block_elems], v);
+        v = fma(m[2], Gl[2 * (int64_t)block_elems], v);
+        v = fma(m[3], Gl[3 * (int64_t)block_elems], v);
+        K[(int64_t)key * block_elems + e] = v;
+    }
+}
+
+// W_ab[r][d] = sum_terms cA K_l(ka,kb)[r][d] + cB K_l(kb,ka)[r'][2h-d]^T,  r' = r + d - h
+__global__ void k_assemble64(OpView A, const double* K, double* W, float* W32)
 {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
     int nrd = A.n1 * A.bd;
     if (idx >= nrd) return;
-    for (int64_t p = blockIdx.y; p < A.npairs; p += gridDim.y) {
     int r = idx / A.bd, d = idx - r * A.bd, rr = r + d - A.half;
-    double w00 = 0, w01 = 0, w10 = 0, w11 = 0;
-    if (rr >= 0 && rr < A.n1) {
-        int64_t nb = (int64_t)nrd * 4;   // elements of one band matrix
-        for (int q = A.term_start[p]; q < A.term_start[p + 1]; q++) {
-            const double* cf = A.term_coef + (int64_t)q * 8;
-            const double* Gl = G + (int64_t)A.term_l[q] * 4 * nb;
-            for (int n = 0; n < 4; n++) {
-                const double* g = Gl + n * nb + ((int64_t)r * A.bd + d) * 4;
-                const double* gt = Gl + n * nb + ((int64_t)rr * A.bd + (2 * A.half - d)) * 4;
-                double ca = cf[n], cb = cf[4 + n];
-                w00 += ca * g[0] + cb * gt[0];
-                w01 += ca * g[1] + cb * gt[2];
-                w10 += ca * g[2] + cb * gt[1];
-                w11 += ca * g[3] + cb * gt[3];
+    int64_t nb = (int64_t)nrd * 4;   // elements of one band matrix
+    for (int64_t pi = blockIdx.y; pi < A.npairs; pi += gridDim.y) {
+        int64_t p = A.pair_order[pi];
+        double w00 = 0, w01 = 0, w10 = 0, w11 = 0;
+        if (rr >= 0 && rr < A.n1) {
+            for (int q = A.term_start[p]; q < A.term_start[p + 1]; q++) {
+                double ca = A.term_cab[2 * q], cb = A.term_cab[2 * q + 1];
+                const double2* g = reinterpret_cast<const double2*>(K + A.term_kd[q] * nb + ((int64_t)r * A.bd + d) * 4);
+                const double2* gt =
+                    reinterpret_cast<const double2*>(K + A.term_kt[q] * nb + ((int64_t)rr * A.bd + (2 * A.half - d)) * 4);
+                double2 g0 = g[0], g1 = g[1], h0 = gt[0], h1 = gt[1];
+                w00 = fma(ca, g0.x, fma(cb, h0.x, w00));
+                w01 = fma(ca, g0.y, fma(cb, h1.x, w01));
+                w10 = fma(ca, g1.x, fma(cb, h0.y, w10));
+                w11 = fma(ca, g1.y, fma(cb, h1.y, w11));
             }
+            int ka = A.ch_kappa[A.pair_a[p]], kb = A.ch_kappa[A.pair_b[p]];
+            if (!used_fn(ka, r, 0)) w00 = w01 = 0;
+            if (!used_fn(ka, r, 1)) w10 = w11 = 0;
+            if (!used_fn(kb, rr, 0)) w00 = w10 = 0;
+            if (!used_fn(kb, rr, 1)) w01 = w11 = 0;
         }
-        int ka = A.ch_kappa[A.pair_a[p]], kb = A.ch_kappa[A.pair_b[p]];
-        if (!used_fn(ka, r, 0)) w00 = w01 = 0;
-        if (!used_fn(ka, r, 1)) w10 = w11 = 0;
-        if (!used_fn(kb, rr, 0)) w00 = w10 = 0;
-        if (!used_fn(kb, rr, 1)) w01 = w11 = 0;
-    }
-    int64_t o = ((p * A.n1 + r) * A.bd + d) * 4;
-    double2* out = reinterpret_cast<double2*>(W + o);
-    out[0] = make_double2(w00, w01);
-    out[1] = make_double2(w10, w11);
-    if (W32) *reinterpret_cast<float4*>(W32 + o) = make_float4((float)w00, (float)w01, (float)w10, (float)w11);
+        int64_t o = ((p * A.n1 + r) * A.bd + d) * 4;
+        double2* out = reinterpret_cast<double2*>(W + o);
+        out[0] = make_double2(w00, w01);
+        out[1] = make_double2(w10, w11);
+        if (W32) *reinterpret_cast<float4*>(W32 + o) = make_float4((float)w00, (float)w01, (float)w10, (float)w11);
     }
 }
 
 __global__ void k_set_time(double* t_eval, double t) { *t_eval = t; }
+
+__global__ void k_set_step_time(double* t_eval, double t_start, int step, double dt, double t_off)
+{
+    *t_eval = step_time(t_start, step, dt, t_off);
+}
 
 __global__ void k_copy64(int64_t n, const double2* a, double2* b)
 {
@@ -111,6 +135,14 @@ __global__ void k_zero64(int64_t n, double2* a)
 }
 
 // x = c0 a + c1 b + c2 c (real coefficients), for the extrapolated initial guess
+__global__ void k_extrapolate(int64_t n, int nh, const double2* psi, const double2* h1, const double2* h2, double2* x)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 p = psi[i], a = nh >= 1 ? h1[i] : p, b = nh >= 2 ? h2[i] : p;
+    x[i] = make_double2(extrapolate(nh, p.x, a.x, b.x), extrapolate(nh, p.y, a.y, b.y));
+}
+
 __global__ void k_lincomb64(int64_t n, double c0, const double2* a, double c1, const double2* b, double c2,
                             const double2* c, double2* x)
 {

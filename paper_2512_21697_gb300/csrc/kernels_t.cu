@@ -40,8 +40,11 @@ __global__ void __launch_bounds__(128) k_apply(OpView A, const T* __restrict__ S
     const int bd = BD > 0 ? BD : A.bd;
     const int half = (bd - 1) / 2;
     const int n1 = A.n1;
-    int ch = blockIdx.y;
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    // tile-major order (all channels of one radial tile, then the next tile): both uses of a
+    // coupling block (W x_b by its lower channel, W^T x_a by its upper one) fall in the same tile
+    // slab of the coupling values, which fits in L2, so the block is read from HBM once
+    int ch = blockIdx.x;
+    int r = blockIdx.y * blockDim.x + threadIdx.x;
     c2<T> y0 = mk<T>(0, 0), y1 = mk<T>(0, 0);
     bool act = r < n1;
     if (act) {
@@ -62,12 +65,14 @@ __global__ void __launch_bounds__(128) k_apply(OpView A, const T* __restrict__ S
             y1.x += s10 * x0.x + s11 * x1.x - (h10 * x0.y + h11 * x1.y);
             y1.y += s10 * x0.y + s11 * x1.y + (h10 * x0.x + h11 * x1.x);
         }
+        // coupling: direct (W x) and transposed (W^T x) sums kept apart so every stored value costs
+        // exactly two FMAs per use; the signs are applied once at the end
+        c2<T> d0 = mk<T>(0, 0), d1 = mk<T>(0, 0), t0 = mk<T>(0, 0), t1 = mk<T>(0, 0);
         for (int e = A.adj_start[ch]; e < A.adj_start[ch + 1]; e++) {
             int64_t p = A.adj_pair[e];
             const c2<T>* xb = x + (int64_t)A.adj_nbr[e] * 2 * n1;
             const T* Wp = W + p * n1 * bd * 4;
             if (!A.adj_tr[e]) {
-                T cs = (T)(-sign);
                 const T* Wr = Wp + (int64_t)r * bd * 4;
 #pragma unroll
                 for (int d = 0; d < bd; d++) {
@@ -76,13 +81,12 @@ __global__ void __launch_bounds__(128) k_apply(OpView A, const T* __restrict__ S
                     c2<T> x0 = xb[2 * rr], x1 = xb[2 * rr + 1];
                     c2<T> wa = *reinterpret_cast<const c2<T>*>(Wr + d * 4);
                     c2<T> wb = *reinterpret_cast<const c2<T>*>(Wr + d * 4 + 2);
-                    y0.x += cs * (wa.x * x0.x + wa.y * x1.x);
-                    y0.y += cs * (wa.x * x0.y + wa.y * x1.y);
-                    y1.x += cs * (wb.x * x0.x + wb.y * x1.x);
-                    y1.y += cs * (wb.x * x0.y + wb.y * x1.y);
+                    d0.x = fma(wa.x, x0.x, d0.x); d0.x = fma(wa.y, x1.x, d0.x);
+                    d0.y = fma(wa.x, x0.y, d0.y); d0.y = fma(wa.y, x1.y, d0.y);
+                    d1.x = fma(wb.x, x0.x, d1.x); d1.x = fma(wb.y, x1.x, d1.x);
+                    d1.y = fma(wb.x, x0.y, d1.y); d1.y = fma(wb.y, x1.y, d1.y);
                 }
             } else {
-                T cs = (T)sign;
 #pragma unroll
                 for (int d = 0; d < bd; d++) {
                     int rr = r + d - half;
@@ -92,13 +96,17 @@ __global__ void __launch_bounds__(128) k_apply(OpView A, const T* __restrict__ S
                     c2<T> wa = *reinterpret_cast<const c2<T>*>(Wt);
                     c2<T> wb = *reinterpret_cast<const c2<T>*>(Wt + 2);
                     // (W^T)[t][u] = W[u][t]
-                    y0.x += cs * (wa.x * x0.x + wb.x * x1.x);
-                    y0.y += cs * (wa.x * x0.y + wb.x * x1.y);
-                    y1.x += cs * (wa.y * x0.x + wb.y * x1.x);
-                    y1.y += cs * (wa.y * x0.y + wb.y * x1.y);
+                    t0.x = fma(wa.x, x0.x, t0.x); t0.x = fma(wb.x, x1.x, t0.x);
+                    t0.y = fma(wa.x, x0.y, t0.y); t0.y = fma(wb.x, x1.y, t0.y);
+                    t1.x = fma(wa.y, x0.x, t1.x); t1.x = fma(wb.y, x1.x, t1.x);
+                    t1.y = fma(wa.y, x0.y, t1.y); t1.y = fma(wb.y, x1.y, t1.y);
                 }
             }
         }
+        // y += sign (sum W^T x - sum W x)
+        T sg = (T)sign;
+        y0.x = fma(sg, t0.x - d0.x, y0.x); y0.y = fma(sg, t0.y - d0.y, y0.y);
+        y1.x = fma(sg, t1.x - d1.x, y1.x); y1.y = fma(sg, t1.y - d1.y, y1.y);
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
         if (bsub) {
             c2<T> b0 = bsub[o], b1 = bsub[o + 1];
@@ -146,33 +154,51 @@ template void launch_apply_t<float>(dim3, cudaStream_t, const OpView&, const flo
                                     const float*, void*, const void*, const void*, double2*, double*, const KState*);
 
 // ---------------------------------------------------------------------------------------------
-// Preconditioner z = M^-1 v (Eq. matrixM), block diagonal over channels, one LU per kappa.
-// One thread per channel: forward substitution with the recorded row interchanges, then back
-// substitution.  Fused prologues (BiCGSTAB):
-//   mode 0: v = r;   mode 1: p = r + beta (p - omega v) (stored in io);
-//   mode 2: s = r - alpha v (stored in io, partial ||s||^2 in double).
+// Preconditioner z = M^-1 v (Eq. matrixM), block diagonal over channels, one banded LU per kappa.
+// One warp per channel (channels sorted by kappa, so neighbouring warps share factors):
+//  - prologue, lanes over the vector:  mode 0: v = r;  mode 1: p = r + beta (p - omega v) (kept in
+//    io);  mode 2: s = r - alpha v (kept in io; partial ||s||^2 summed in double);
+//  - forward substitution column by column: lanes 0..kb hold z[j..j+kb]; the recorded row
+//    interchange of column j swaps lane 0 with lane piv[j]-j, lanes 1..kb subtract L[j] z[j],
+//    then the window slides by one;
+//  - back substitution column by column: lane k accumulates U[i-k][k] x[i] for row i-k, so row i
+//    is complete when it reaches lane 1 and no per-row reduction is needed.  Ucol[i][k] = U[i-k][k].
 // ---------------------------------------------------------------------------------------------
 template <class T>
-__global__ void k_precond(OpView A, const c2<T>* __restrict__ U, const c2<T>* __restrict__ L, int mode,
-                          const KState* st, const c2<T>* __restrict__ r, const c2<T>* __restrict__ v,
-                          c2<T>* __restrict__ io, c2<T>* __restrict__ z, double* part_nrm)
+__device__ __forceinline__ c2<T> shfl2(c2<T> v, int src)
 {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    return mk<T>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+template <class T>
+__device__ __forceinline__ c2<T> shfl2_down(c2<T> v, int d)
+{
+    return mk<T>(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+template <class T>
+__global__ void __launch_bounds__(128) k_precond(OpView A, const c2<T>* __restrict__ Ucol,
+                                                 const c2<T>* __restrict__ L, const c2<T>* __restrict__ Dinv,
+                                                 int mode, const KState* st,
+                                                 const c2<T>* __restrict__ r, const c2<T>* __restrict__ v,
+                                                 c2<T>* __restrict__ io, c2<T>* __restrict__ z, double* part_nrm)
+{
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
     double nsum = 0;
-    if (idx < A.nch && !(st && st->done)) {
-        int ch = A.prec_order[idx];
-        int n = 2 * A.n1, kb = A.kb, wu = 2 * kb;
+    if (warp < A.nch && !(st && st->done)) {
+        int ch = A.prec_order[warp];
+        const int n = 2 * A.n1, kb = A.kb, wu = 2 * kb;
         int ks = A.ch_kslot[ch];
-        const c2<T>* Uk = U + (int64_t)ks * n * (wu + 1);
+        const c2<T>* Uk = Ucol + (int64_t)ks * n * (wu + 1);
         const c2<T>* Lk = L + (int64_t)ks * n * kb;
+        const c2<T>* Dk = Dinv + (int64_t)ks * n;
         const int* P = A.luP + (int64_t)ks * n;
         int64_t o = (int64_t)ch * n;
         c2<T>* zc = z + o;
         if (mode == 0) {
-            for (int i = 0; i < n; i++) zc[i] = r[o + i];
+            for (int i = lane; i < n; i += 32) zc[i] = r[o + i];
         } else if (mode == 1) {
             c2<T> beta = from_d<T>(st->beta), omega = from_d<T>(st->omega);
-            for (int i = 0; i < n; i++) {
+            for (int i = lane; i < n; i += 32) {
                 c2<T> pv = io[o + i], vv = v[o + i], rv = r[o + i];
                 c2<T> t = cm<T>(omega, vv);
                 c2<T> q = cm<T>(beta, mk<T>(pv.x - t.x, pv.y - t.y));
@@ -182,7 +208,7 @@ __global__ void k_precond(OpView A, const c2<T>* __restrict__ U, const c2<T>* __
             }
         } else {
             c2<T> alpha = from_d<T>(st->alpha);
-            for (int i = 0; i < n; i++) {
+            for (int i = lane; i < n; i += 32) {
                 c2<T> t = cm<T>(alpha, v[o + i]);
                 c2<T> rv = r[o + i];
                 c2<T> sv = mk<T>(rv.x - t.x, rv.y - t.y);
@@ -191,42 +217,213 @@ __global__ void k_precond(OpView A, const c2<T>* __restrict__ U, const c2<T>* __
                 nsum += (double)sv.x * sv.x + (double)sv.y * sv.y;
             }
         }
+        __syncwarp();
+        // forward: window lane l = z[j + l], l = 0..kb; row j + 1 of L and its pivot loaded ahead
+        c2<T> w = (lane <= kb && lane < n) ? zc[lane] : mk<T>(0, 0);
+        c2<T> lnext = (lane >= 1 && lane <= kb) ? Lk[lane - 1] : mk<T>(0, 0);
+        int pnext = P[0];
         for (int j = 0; j < n; j++) {
-            int pj = P[j];
-            if (pj != j) { c2<T> t = zc[j]; zc[j] = zc[pj]; zc[pj] = t; }
-            c2<T> zj = zc[j];
-            int lim = min(kb, n - 1 - j);
-            for (int i = 1; i <= lim; i++) {
-                c2<T> m = cm<T>(Lk[(int64_t)j * kb + i - 1], zj);
-                zc[j + i].x -= m.x;
-                zc[j + i].y -= m.y;
+            c2<T> lcur = lnext;
+            int pj = pnext - j;
+            if (j + 1 < n) {
+                lnext = (lane >= 1 && lane <= kb) ? Lk[(int64_t)(j + 1) * kb + lane - 1] : mk<T>(0, 0);
+                pnext = P[j + 1];
+            }
+            c2<T> w0 = shfl2<T>(w, 0), wp = shfl2<T>(w, pj);
+            if (lane == 0) w = wp;
+            else if (lane == pj) w = w0;
+            c2<T> zj = shfl2<T>(w, 0);
+            if (lane >= 1 && lane <= kb && j + lane < n) {
+                w.x -= lcur.x * zj.x - lcur.y * zj.y;
+                w.y -= lcur.x * zj.y + lcur.y * zj.x;
+            }
+            if (lane == 0) zc[j] = zj;
+            w = shfl2_down<T>(w, 1);
+            if (lane == kb) w = (j + kb + 1 < n) ? zc[j + kb + 1] : mk<T>(0, 0);
+        }
+        __syncwarp();
+        // backward: lane k (1..wu) holds the partial sum of row i - k; the row of U for the next
+        // step is loaded one step ahead
+        c2<T> acc = mk<T>(0, 0);
+        c2<T> unext = (lane >= 1 && lane <= wu && n - 1 - lane >= 0) ? Uk[(int64_t)(n - 1) * (wu + 1) + lane]
+                                                                      : mk<T>(0, 0);
+        for (int i = n - 1; i >= 0; i--) {
+            c2<T> ucur = unext;
+            if (i > 0) unext = (lane >= 1 && lane <= wu && i - 1 - lane >= 0) ? Uk[(int64_t)(i - 1) * (wu + 1) + lane]
+                                                                              : mk<T>(0, 0);
+            // row i is complete in lane 1; lane 0 finishes it with the reciprocal diagonal
+            c2<T> a0 = shfl2<T>(acc, 1);
+            c2<T> xi = mk<T>(0, 0);
+            if (lane == 0) {
+                c2<T> zi = zc[i];
+                xi = cm<T>(mk<T>(zi.x - a0.x, zi.y - a0.y), Dk[i]);
+                zc[i] = xi;
+            }
+            xi = shfl2<T>(xi, 0);
+            // slide: lane k takes the sum of row (i-1) - k from lane k + 1, then adds U[i-k][k] x[i]
+            acc = shfl2_down<T>(acc, 1);
+            if (lane == wu) acc = mk<T>(0, 0);
+            if (lane >= 1 && lane <= wu) {
+                acc.x += ucur.x * xi.x - ucur.y * xi.y;
+                acc.y += ucur.x * xi.y + ucur.y * xi.x;
             }
         }
-        for (int i = n - 1; i >= 0; i--) {
-            c2<T> s = zc[i];
-            int lim = min(wu, n - 1 - i);
-            const c2<T>* Ui = Uk + (int64_t)i * (wu + 1);
-            for (int k = 1; k <= lim; k++) {
-                c2<T> m = cm<T>(Ui[k], zc[i + k]);
-                s.x -= m.x;
-                s.y -= m.y;
+    }
+    if (part_nrm) {
+        // per-block partial of ||s||^2 (one value per block in a fixed order)
+        block_reduce_store(make_double2(0, 0), nsum, nullptr, part_nrm, blockIdx.x);
+    }
+}
+
+// Lane-per-channel variant for band width 13 (order-7 B-splines): one warp per group of <= 32
+// channels of the same kappa (warp_ks, warp_first, warp_count), so factor loads are broadcasts
+// and the recorded interchanges are warp-uniform.  Each lane runs the whole substitution of its
+// channel with the windows in registers: forward z[j..j+13], backward x[i+1..i+26]; the diagonal
+// of U is applied as a precomputed reciprocal.  Urow[i][k] = U[i][i+k].
+template <class T, int KB>
+__global__ void __launch_bounds__(32) k_precond_lanes(OpView A, const c2<T>* __restrict__ Urow,
+                                                      const c2<T>* __restrict__ L, const c2<T>* __restrict__ Dinv,
+                                                      const int* __restrict__ warp_ks, const int* __restrict__ warp_first,
+                                                      const int* __restrict__ warp_count, int mode, const KState* st,
+                                                      const c2<T>* __restrict__ r, const c2<T>* __restrict__ v,
+                                                      c2<T>* __restrict__ io, c2<T>* __restrict__ z, double* part_nrm)
+{
+    constexpr int WU = 2 * KB;
+    int w = blockIdx.x, lane = threadIdx.x;
+    double nsum = 0;
+    if (!(st && st->done)) {
+        const int n = 2 * A.n1;
+        int ks = warp_ks[w], first = warp_first[w], cnt = warp_count[w];
+        // prologue, coalesced: lanes over the entries of each channel of the group
+        for (int c = 0; c < cnt; c++) {
+            int64_t o = (int64_t)A.prec_order[first + c] * n;
+            if (mode == 0) {
+                for (int i = lane; i < n; i += 32) z[o + i] = r[o + i];
+            } else if (mode == 1) {
+                c2<T> beta = from_d<T>(st->beta), omega = from_d<T>(st->omega);
+                for (int i = lane; i < n; i += 32) {
+                    c2<T> pv = io[o + i], vv = v[o + i], rv = r[o + i];
+                    c2<T> t = cm<T>(omega, vv);
+                    c2<T> q = cm<T>(beta, mk<T>(pv.x - t.x, pv.y - t.y));
+                    c2<T> pn = mk<T>(rv.x + q.x, rv.y + q.y);
+                    io[o + i] = pn;
+                    z[o + i] = pn;
+                }
+            } else {
+                c2<T> alpha = from_d<T>(st->alpha);
+                for (int i = lane; i < n; i += 32) {
+                    c2<T> t = cm<T>(alpha, v[o + i]);
+                    c2<T> rv = r[o + i];
+                    c2<T> sv = mk<T>(rv.x - t.x, rv.y - t.y);
+                    io[o + i] = sv;
+                    z[o + i] = sv;
+                    nsum += (double)sv.x * sv.x + (double)sv.y * sv.y;
+                }
             }
-            zc[i] = cdv<T>(s, Ui[0]);
+        }
+        __syncwarp();
+        // factor rows are staged through shared memory CH rows at a time (one coalesced load per
+        // chunk, then broadcast reads); the rows are the same for every lane (same kappa)
+        constexpr int CH = 32;
+        __shared__ c2<T> sF[CH * (WU + 1)];
+        __shared__ c2<T> sD[CH];
+        __shared__ int sP[CH];
+        const bool mine = lane < cnt;
+        int64_t o = mine ? (int64_t)A.prec_order[first + lane] * n : 0;
+        c2<T>* zc = z + o;
+        const c2<T>* Lk = L + (int64_t)ks * n * KB;
+        const c2<T>* Uk = Urow + (int64_t)ks * n * (WU + 1);
+        const c2<T>* Dk = Dinv + (int64_t)ks * n;
+        const int* P = A.luP + (int64_t)ks * n;
+        c2<T> win[KB + 1];
+#pragma unroll
+        for (int i = 0; i <= KB; i++) win[i] = (mine && i < n) ? zc[i] : mk<T>(0, 0);
+        for (int j0 = 0; j0 < n; j0 += CH) {
+            int rows = min(CH, n - j0);
+            __syncwarp();
+            for (int e = lane; e < rows * KB; e += 32) sF[e] = Lk[(int64_t)j0 * KB + e];
+            if (lane < rows) sP[lane] = P[j0 + lane];
+            __syncwarp();
+            if (mine)
+                for (int jj = 0; jj < rows; jj++) {
+                    int j = j0 + jj;
+                    int pj = sP[jj] - j;
+#pragma unroll
+                    for (int i = 1; i <= KB; i++)
+                        if (pj == i) { c2<T> t = win[0]; win[0] = win[i]; win[i] = t; }
+                    c2<T> zj = win[0];
+                    zc[j] = zj;
+#pragma unroll
+                    for (int i = 1; i <= KB; i++) {
+                        c2<T> l = sF[jj * KB + i - 1];   // zero beyond the last row
+                        win[i].x -= l.x * zj.x - l.y * zj.y;
+                        win[i].y -= l.x * zj.y + l.y * zj.x;
+                    }
+#pragma unroll
+                    for (int i = 0; i < KB; i++) win[i] = win[i + 1];
+                    win[KB] = (j + KB + 1 < n) ? zc[j + KB + 1] : mk<T>(0, 0);
+                }
+        }
+        c2<T> xw[WU];
+#pragma unroll
+        for (int k = 0; k < WU; k++) xw[k] = mk<T>(0, 0);
+        c2<T> znext = mine ? zc[n - 1] : mk<T>(0, 0);
+        for (int i1 = n - 1; i1 >= 0; i1 -= CH) {
+            int rows = min(CH, i1 + 1);   // rows i1 - rows + 1 .. i1
+            int i0 = i1 - rows + 1;
+            __syncwarp();
+            for (int e = lane; e < rows * (WU + 1); e += 32) sF[e] = Uk[(int64_t)i0 * (WU + 1) + e];
+            if (lane < rows) sD[lane] = Dk[i0 + lane];
+            __syncwarp();
+            if (mine)
+                for (int ii = rows - 1; ii >= 0; ii--) {
+                    int i = i0 + ii;
+                    c2<T> s = znext;
+                    if (i > 0) znext = zc[i - 1];
+                    const c2<T>* Ui = sF + ii * (WU + 1);
+#pragma unroll
+                    for (int k = 1; k <= WU; k++) {
+                        c2<T> u = Ui[k];       // zero beyond the last column
+                        s.x -= u.x * xw[k - 1].x - u.y * xw[k - 1].y;
+                        s.y -= u.x * xw[k - 1].y + u.y * xw[k - 1].x;
+                    }
+                    c2<T> xi = cm<T>(s, sD[ii]);
+                    zc[i] = xi;
+#pragma unroll
+                    for (int k = WU - 1; k > 0; k--) xw[k] = xw[k - 1];
+                    xw[0] = xi;
+                }
         }
     }
     if (part_nrm) block_reduce_store(make_double2(0, 0), nsum, nullptr, part_nrm, blockIdx.x);
 }
 
 template <class T>
-void launch_precond_t(int blocks, cudaStream_t st, const OpView& A, const void* U, const void* L, int mode,
-                      const KState* ks, const void* r, const void* v, void* io, void* z, double* pn)
+void launch_precond_lanes_t(int nwarps, cudaStream_t st, const OpView& A, const void* Urow, const void* L,
+                            const void* Dinv, const int* wks, const int* wfirst, const int* wcnt, int mode,
+                            const KState* ks, const void* r, const void* v, void* io, void* z, double* pn)
 {
-    k_precond<T><<<blocks, 32, 0, st>>>(A, (const c2<T>*)U, (const c2<T>*)L, mode, ks, (const c2<T>*)r,
-                                        (const c2<T>*)v, (c2<T>*)io, (c2<T>*)z, pn);
+    k_precond_lanes<T, 13><<<nwarps, 32, 0, st>>>(A, (const c2<T>*)Urow, (const c2<T>*)L, (const c2<T>*)Dinv, wks,
+                                                  wfirst, wcnt, mode, ks, (const c2<T>*)r, (const c2<T>*)v,
+                                                  (c2<T>*)io, (c2<T>*)z, pn);
 }
-template void launch_precond_t<double>(int, cudaStream_t, const OpView&, const void*, const void*, int,
+template void launch_precond_lanes_t<double>(int, cudaStream_t, const OpView&, const void*, const void*,
+                                             const void*, const int*, const int*, const int*, int, const KState*,
+                                             const void*, const void*, void*, void*, double*);
+template void launch_precond_lanes_t<float>(int, cudaStream_t, const OpView&, const void*, const void*, const void*,
+                                            const int*, const int*, const int*, int, const KState*, const void*,
+                                            const void*, void*, void*, double*);
+
+template <class T>
+void launch_precond_t(int blocks, cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv,
+                      int mode, const KState* ks, const void* r, const void* v, void* io, void* z, double* pn)
+{
+    k_precond<T><<<blocks, 128, 0, st>>>(A, (const c2<T>*)U, (const c2<T>*)L, (const c2<T>*)Dinv, mode, ks,
+                                         (const c2<T>*)r, (const c2<T>*)v, (c2<T>*)io, (c2<T>*)z, pn);
+}
+template void launch_precond_t<double>(int, cudaStream_t, const OpView&, const void*, const void*, const void*, int,
                                        const KState*, const void*, const void*, void*, void*, double*);
-template void launch_precond_t<float>(int, cudaStream_t, const OpView&, const void*, const void*, int,
+template void launch_precond_t<float>(int, cudaStream_t, const OpView&, const void*, const void*, const void*, int,
                                       const KState*, const void*, const void*, void*, void*, double*);
 
 // ---------------------------------------------------------------------------------------------

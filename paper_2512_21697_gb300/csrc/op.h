@@ -1,0 +1,96 @@
+// op.h -- the device operator (dirac_op) and the launch helpers shared by the C ABI
+// implementation (capi.cu) and the CUDA-graph step driver (graph.cu).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "device.h"
+#include "internal.h"
+
+namespace dg {
+
+// Krylov workspace in one working precision (prec 0: complex128, 1: complex64): the vectors
+// of BiCGSTAB, its scalar state and the operator data it multiplies with.
+struct Krylov {
+    int prec = 0;
+    void *b = nullptr, *x = nullptr, *r = nullptr, *rh = nullptr, *p = nullptr, *v = nullptr, *ph = nullptr,
+         *sv = nullptr, *sh = nullptr, *t = nullptr;
+    KState* ks = nullptr;
+    const void *S = nullptr, *H = nullptr, *W = nullptr, *U = nullptr, *L = nullptr;
+    const void *Urow = nullptr, *Dinv = nullptr;   // lane-per-channel preconditioner data
+};
+
+struct GraphDriver;   // graph.cu
+
+}  // namespace dg
+
+struct dirac_op {
+    dg::Basis B;                 // host copy of the basis data the operator needs
+    dirac_pulse pulse{};
+    dirac_solver_opts opts{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    int64_t n = 0, npairs = 0;
+    int nparts_apply = 0, nparts_vec = 0, nparts_prec = 0, nparts_prec32 = 0;
+    int prec_warps = 0;          // same-kappa channel groups (lane-per-channel preconditioner)
+    int *wks = nullptr, *wfirst = nullptr, *wcnt = nullptr;
+    std::vector<void*> allocs;
+    size_t bytes = 0;
+    dg::OpView ov{};
+    dg::PulseView pv{};
+    double* G = nullptr;         // G^n_l(t) bands
+    double* s = nullptr;         // time factors
+    double* t_eval = nullptr;
+    double* K = nullptr;         // combined radial bands K_l(k', k)(t)
+    double* W = nullptr;         // coupling values, FP64 (precision 0 and 1)
+    // precision 2: double-float operator data (hi/lo float pairs)
+    float2 *Gdf = nullptr, *Kdf = nullptr, *Sdf = nullptr, *Htdf = nullptr;
+    float *Wh = nullptr, *Wl = nullptr;   // coupling hi words (also the FP32 values) and lo words
+    float4* cab_df = nullptr;
+    float4* xsplit = nullptr;    // split input vector; u = psi + x in the fused residual
+    float4* vsplit = nullptr;    // v = psi - x in the fused residual
+    float* W32 = nullptr;        // their FP32 rounding (mixed precision only)
+    dg::Krylov k64, k32;         // FP64 solve (outer loop in mixed precision), FP32 inner solve
+    double2* part_d = nullptr;
+    double* part_n = nullptr;
+    double* part_n2 = nullptr;
+    double2* part_d2 = nullptr;
+    double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
+    int ground_ch = -1;
+    // kernel-phase timers (CUDA events on the op's stream) and the launch counter
+    bool profiling = false;
+    int64_t launches = 0;
+    double phase_ms[DIRAC_NPHASE] = {0};
+    int64_t phase_n[DIRAC_NPHASE] = {0};
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    std::vector<cudaEvent_t> event_pool;
+    dg::GraphDriver* graph = nullptr;   // captured multi-step driver (dirac_run), built on first use
+};
+
+namespace dg {
+
+int grid_for(int64_t n, int bs);
+void collect_phases(dirac_op* op);
+dirac_status check_launch(const char* what);
+void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
+                    const void* dv, double2* pdot, double* pnrm, const KState* skip);
+void launch_assemble(dirac_op* op);
+void apply_accurate(dirac_op* op, int sign, const void* x, void* y, const void* bsub, double* pnrm);
+void rhs_accurate(dirac_op* op, const void* psi);
+void residual_accurate(dirac_op* op, const void* psi);
+void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks, const void* r, const void* v,
+                      void* io, void* z, double* pn);
+void finish(dirac_op* op, KState* ks, int what, int np, const double2* pd, const double* pn, int max_iter);
+void vcopy(dirac_op* op, const Krylov& K, const void* a, void* b);
+void vzero(dirac_op* op, const Krylov& K, void* a);
+dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs);
+dirac_status bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter, bool mid_check);
+void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start = false);
+void set_error(const std::string& msg);
+void graph_free(dirac_op* op);
+
+}  // namespace dg

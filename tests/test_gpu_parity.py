@@ -6,8 +6,11 @@ Tolerances (double precision everywhere):
  - preconditioner: relative 2-norm 1e-10 -- two LU factorisations of a matrix with condition
    number up to ~1e4 (dense vs banded, different pivot order) agree to cond * eps.
  - CN step / run: wavefunction relative L2 <= 1e-10, observables <= 1e-9 (the stated parity bar);
-   the GPU solves to its configured tolerance, the oracle to 1e-14.
+   the oracle solves to 1e-14.  A solve to relative residual tol leaves an error up to
+   cond(A_+) tol; random states carry high-energy components where cond(A_+) reaches ~1e3, so the
+   random-state step checks solve to 1e-13 (the physical-state full run uses the workload's 1e-12).
 """
+STEP_TOL = 1e-13
 import math
 
 import numpy as np
@@ -50,7 +53,7 @@ class Case:
 @pytest.fixture(scope="module", params=["tiny", "small", "slice"])
 def case(request, oracle_mod):
     cfg = W.WORKLOADS[request.param]
-    return Case(cfg, oracle_mod, tol=cfg["tol"], max_iter=1000)
+    return Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000)
 
 
 def test_apply_matches_oracle(case):
@@ -89,7 +92,7 @@ def test_step_matches_oracle(case):
         ref, _, _ = case.orc.step(ref, t0 + s * case.cfg["dt"], tol=1e-14)
     got = case.from_dev(psid)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
-    assert np.all(res <= case.cfg["tol"])
+    assert np.all(res <= STEP_TOL)
     assert np.all(got[~case.orc.active_mask()] == 0)
 
 
@@ -144,7 +147,7 @@ def test_mixed_precision_step_matches_oracle(oracle_mod, name):
     # complex64 BiCGSTAB inside double-precision refinement: the refinement stops on the FP64 true
     # residual, so the result meets the same parity bar as the FP64 path
     cfg = W.WORKLOADS[name]
-    c = Case(cfg, oracle_mod, tol=cfg["tol"], max_iter=1000, precision=1, tol_inner=1e-5, max_outer=30)
+    c = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=1, tol_inner=1e-5, max_outer=30)
     psi0 = c.random(11)
     t0 = 0.5 * c.T()
     n = 3
@@ -154,5 +157,39 @@ def test_mixed_precision_step_matches_oracle(oracle_mod, name):
     for s in range(n):
         ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
     got = c.from_dev(psid)
-    assert np.all(res <= cfg["tol"])
+    assert np.all(res <= STEP_TOL)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "slice"])
+def test_double_float_apply_matches_oracle(oracle_mod, name):
+    # precision 2 applies A_+- in double-float (FP32 hi/lo pairs with error-free transforms):
+    # ~2^-44 relative per operation, so the bar is 1e-11 of max|y| instead of 1e-12
+    cfg = W.WORKLOADS[name]
+    c = Case(cfg, oracle_mod, tol=STEP_TOL, precision=2, tol_inner=1e-5, max_outer=30)
+    x = c.random(13)
+    xd = c.to_dev(x)
+    yd = c.torch.empty_like(xd)
+    for sign in (+1, -1):
+        t = 0.43 * c.T()
+        c.op.apply(sign, t, xd, yd)
+        y = c.from_dev(yd)
+        ref = c.orc.apply(t, sign, x)
+        assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max(), sign
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "slice"])
+def test_double_float_step_matches_oracle(oracle_mod, name):
+    cfg = W.WORKLOADS[name]
+    c = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
+    psi0 = c.random(17)
+    t0 = 0.5 * c.T()
+    n = 3
+    psid = c.to_dev(psi0)
+    its, res, _ = c.op.step(psid, n, t0)
+    ref = psi0.copy()
+    for s in range(n):
+        ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+    got = c.from_dev(psid)
+    assert np.all(res <= STEP_TOL)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
