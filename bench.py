@@ -7,7 +7,7 @@ dt = 0.005, BiCGSTAB to relative residual 1e-10.  Every step runs the whole hot 
 factors, coupling assembly, A_- psi, BiCGSTAB (operator applies, preconditioner, updates).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-       [--precision 0|1] [--t0 T] [--workload production|slice|small]
+       [--precision 0|1|2] [--t0 T] [--workload production|slice|small] [--no-fp64-compare]
 Prints one JSON line (rank 0).  N > 1 (torchrun) runs N independent replicas, one per GPU,
 with no data-path communication; the value is the total steps/s over all ranks.
 """
@@ -34,8 +34,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="production")
-    ap.add_argument("--precision", type=int, default=0,
+    ap.add_argument("--precision", type=int, default=2,
                     help="0 FP64, 1 c64 in FP64 refinement, 2 c64 in double-float refinement")
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip timing the plain FP64 solver on the same steps")
     ap.add_argument("--t0", type=float, default=None, help="start time (default: 0, the pulse start)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
@@ -140,6 +142,29 @@ def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
     else:
         out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS hbm_gbs)"})
+    return out
+
+
+def fp64_compare(bas, cfg, psi0_h, t0, args, stream, dev):
+    """Plain FP64 BiCGSTAB on the same steps from the same state, to the same tolerance."""
+    import numpy as np
+    import torch
+    from paper_2512_21697_gb300 import binding as B
+    op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=0, max_iter=1000)
+    with torch.cuda.stream(stream):
+        psi = torch.from_numpy(psi0_h).to(dev)
+        hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev)
+    _, _, nh = op.step(psi, args.warmup, t0, hist=hist, n_hist=0)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    its, res, _ = op.step(psi, args.steps, t0 + args.warmup * cfg["dt"], hist=hist, n_hist=nh)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    out = {"value": args.steps / (ms / 1000.0), "unit": "steps/s", "ms_per_step": ms / args.steps,
+           "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)), "dtype": "f64"}
+    del op
     return out
 
 
@@ -276,13 +301,18 @@ def main():
     with torch.cuda.stream(stream):
         psi_e = torch.empty_like(psi)
     e2e_steps = max(2, min(args.steps, 5))
+    with torch.cuda.stream(stream):
+        hist_e = torch.zeros_like(hist)
+    nh_e = 0
     torch.cuda.synchronize()
     ee0.record(stream)
     te = tcur
     for s in range(e2e_steps):
+        # one user call per step: the state goes in from pinned host memory, comes back out, and the
+        # solver's own history (device-resident between calls) feeds the extrapolated guess
         with torch.cuda.stream(stream):
             psi_e.copy_(psi_h if s == 0 else out_h, non_blocking=True)
-        op.step(psi_e, 1, te)
+        _, _, nh_e = op.step(psi_e, 1, te, hist=hist_e, n_hist=nh_e)
         with torch.cuda.stream(stream):
             out_h.copy_(psi_e, non_blocking=True)
         te += cfg["dt"]
@@ -301,6 +331,9 @@ def main():
             dist.destroy_process_group()
         return
     obs = op.observables(psi)
+    fp64 = None
+    if args.precision != 0 and not args.no_fp64_compare:
+        fp64 = fp64_compare(bas, cfg, psi0_h, t0, args, stream, dev)
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -322,6 +355,9 @@ def main():
         "clocks": ck,
         "observables": obs,
     }
+    if fp64:
+        line["fp64_baseline"] = fp64
+        line["speedup_vs_fp64"] = value / (fp64["value"] * world)
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(cfg, float(np.mean(its)), args.cpu_seconds)

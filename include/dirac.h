@@ -140,7 +140,14 @@ dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist,
                        double t_start, int* iters_out, double* resid_out);
 
 /* Observables of a state (Sec. 4.3): out[0] = psi^H S psi, out[1] = psi^H H0 psi,
- * out[2] = |v_1s^T S psi_{kappa=-1, mu=+1/2}|^2 (ground-state population).  n_out <= 3. */
+ * out[2] = |v_1s^T S psi_{kappa=-1, mu=+1/2}|^2 (ground-state population),
+ * out[3] = sum over channels (kappa, mu) and bound states b of |v_b^T S_kappa psi_{kappa mu}|^2, the
+ * bound-state population, v_b the eigenvectors of H0_kappa v = E S_kappa v with -c^2 < E < 0,
+ * v^T S v = 1.  n_out <= 4.  The first call with n_out = 4 computes those eigenvectors (one dense
+ * generalised eigensolve per kappa on the GPU, cuSOLVER; seconds at N = 1000) and keeps them with
+ * the op (2 n1 doubles per bound state); it allocates, so it must not run inside a stream capture.
+ * Synchronises the op's stream.  Errors: DIRAC_E_ARG (bad argument), DIRAC_E_NUMERIC (the
+ * eigensolver failed), DIRAC_E_CUDA. */
 dirac_status dirac_observables(dirac_op* op, const void* psi_dev, double* out, int n_out);
 
 /* y = A_sign x with the coupling values assembled by the most recent dirac_apply or dirac_step
@@ -167,7 +174,8 @@ dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_
  * callers that cannot allocate GPU memory at that point: code running while a stream is captured
  * into a CUDA graph, real-time or monitoring threads that must not hit the implicit device
  * synchronisation of cudaMalloc/cudaFree, processes whose device footprint is fixed after setup).
- * Same arguments, outputs and errors as dirac_observables.  Its scratch (block partials and the
+ * Same arguments, outputs and errors as dirac_observables, except n_out <= 3 (the bound-state
+ * population needs its eigenvectors set up, which allocates).  Its scratch (block partials and the
  * final sums) is a library-static device array of 2 DIRAC_STATIC_MAX_PARTIALS + 2 complex128
  * values (about 2 MB), held by every GPU that loads the library until the process exits; it
  * supports systems with channels x ceil((N+1)/128) <= DIRAC_STATIC_MAX_PARTIALS and returns

@@ -247,10 +247,16 @@ class Operator:
         _check(st, "dirac_run")
         return it[:n_steps], res[:n_steps], nh.value
 
-    def observables(self, psi):
-        out = np.zeros(3)
-        _check(lib().dirac_observables(self._h, _ptr(psi), _dp(out), 3), "dirac_observables")
-        return dict(norm=out[0], energy=out[1], p_ground=out[2])
+    def observables(self, psi, bound=False):
+        """norm, energy, ground-state population; with bound=True also the bound-state population
+        (its eigenvectors are computed on the first such call)."""
+        k = 4 if bound else 3
+        out = np.zeros(k)
+        _check(lib().dirac_observables(self._h, _ptr(psi), _dp(out), k), "dirac_observables")
+        d = dict(norm=out[0], energy=out[1], p_ground=out[2])
+        if bound:
+            d["p_bound"] = out[3]
+        return d
 
     def observables_static(self, psi):
         """dirac_observables_static: the same observables with library-static scratch."""

@@ -121,6 +121,9 @@ void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void
     if (K.prec == 0)
         launch_apply_t<double>(grid, op->st, op->ov, (const double*)K.S, (const double*)K.H, sign, x,
                                (const double*)K.W, y, bsub, dv, pdot, pnrm, skip);
+    else if (op->part_own)
+        launch_apply_own32(op->st, op->ov, (const float*)K.S, (const float*)K.H, sign, x, (const float*)K.W, y,
+                           op->part_own, bsub, dv, pdot, pnrm, skip, op->dev_err);
     else
         launch_apply_t<float>(grid, op->st, op->ov, (const float*)K.S, (const float*)K.H, sign, x,
                               (const float*)K.W, y, bsub, dv, pdot, pnrm, skip);
@@ -135,9 +138,10 @@ void launch_assemble(dirac_op* op)
         k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->Gdf);
         if (op->npairs) {
             k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, op->st>>>(
-                op->ov, be, op->Gdf, op->Kdf);
-            launch_assemble_df(dim3(grid_for(op->ov.n1, 128), (unsigned)std::min<int64_t>(op->npairs, 65535)), op->st,
-                               op->ov, op->Kdf, op->cab_df, op->Wh, op->Wl);
+                op->ov, be, op->Gdf, op->Kdf, op->KTdf);
+            launch_assemble_df(dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
+                                    (unsigned)std::min<int64_t>(op->npairs, 65535)),
+                               op->st, op->ov, op->Kdf, op->KTdf, op->cab_df, op->Wh, op->Wl);
         }
         return;
     }
@@ -170,7 +174,13 @@ void apply_accurate(dirac_op* op, int sign, const void* x, void* y, const void* 
 // both the residual and ||b||^2 from the fused residual kernel, so nothing happens here.
 void rhs_accurate(dirac_op* op, const void* psi)
 {
-    if (op->opts.precision == 2) return;
+    if (op->opts.precision == 2) {
+        if (op->part_rdf) {
+            k_set_int<<<1, 1, 0, op->st>>>(op->need_b, 1);
+            op->launches++;
+        }
+        return;
+    }
     Krylov& K = op->k64;
     apply_accurate(op, -1, psi, K.b, nullptr, op->part_n);
     finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
@@ -184,6 +194,23 @@ void residual_accurate(dirac_op* op, const void* psi)
     Krylov& K = op->k64;
     if (op->opts.precision != 2) {
         apply_accurate(op, +1, K.x, K.r, K.b, op->part_n);
+        finish(op, K.ks, 1, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
+        return;
+    }
+    if (op->part_rdf) {
+        // owner/gather form: each coupling block read once
+        {
+            PhaseScope ps(op, DIRAC_PHASE_APPLY, 3);
+            k_split_uv3<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)psi, (const double2*)K.x,
+                                                           op->xsplit, op->vsplit, op->psi32);
+            launch_residual_own_df(op->st, op->ov, op->Sdf, op->Htdf, op->xsplit, op->vsplit, op->psi32, op->Wh,
+                                   op->Wl, (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b,
+                                   op->part_n, op->part_n2, op->dev_err);
+        }
+        {
+            PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
+            k_bnorm_if<<<1, 1024, 0, op->st>>>(K.ks, op->need_b, op->nparts_apply, op->part_n2);
+        }
         finish(op, K.ks, 1, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
         return;
     }
@@ -292,6 +319,18 @@ void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start)
     vcopy(op, K, K.r, K.rh);
     vzero(op, K, K.p);
     vzero(op, K, K.v);
+}
+
+// the error word of kernels with bounded waits (synchronises the stream); cleared after reading
+dirac_status check_dev_err(dirac_op* op, const char* what)
+{
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    if (!h) return DIRAC_OK;
+    CUDA_TRY(cudaMemsetAsync(op->dev_err, 0, sizeof(int), op->st));
+    set_error(std::string(what) + ": a kernel's bulk-copy wait ran out of time (results invalid)");
+    return DIRAC_E_CUDA;
 }
 
 dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs)
@@ -472,6 +511,23 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         at.insert(at.end(), adjt[a].begin(), adjt[a].end());
         as.push_back((int)ap.size());
     }
+    // owner lists (pairs a channel is the lower channel of) and in-lists (upper channel of), for the
+    // apply that reads each coupling block once
+    std::vector<int> ows(1, 0), owp, own, ins(1, 0), inp;
+    for (int a = 0; a < B.nch; a++) {
+        for (size_t k = 0; k < adjp[a].size(); k++) {
+            if (adjt[a][k] == 0) { owp.push_back(adjp[a][k]); own.push_back(adjn[a][k]); }
+            else inp.push_back(adjp[a][k]);
+        }
+        ows.push_back((int)owp.size());
+        ins.push_back((int)inp.size());
+    }
+    int *dows, *dowp, *down, *dins, *dinp;
+    TRY(upload(op, &dows, ows));
+    TRY(upload(op, &dowp, owp));
+    TRY(upload(op, &down, own));
+    TRY(upload(op, &dins, ins));
+    TRY(upload(op, &dinp, inp));
     int *das, *dap, *dan, *dat, *dpa, *dpb, *dts, *dtl;
     TRY(upload(op, &das, as));
     TRY(upload(op, &dap, ap));
@@ -622,6 +678,7 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         TRY(upload(op, &op->cab_df, cdf));
         TRY(dev_alloc(op, &op->Gdf, (size_t)P.L * 4 * be));
         TRY(dev_alloc(op, &op->Kdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
+        TRY(dev_alloc(op, &op->KTdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
         TRY(dev_alloc(op, &op->Wh, (size_t)std::max<int64_t>(op->npairs, 1) * be));
         TRY(dev_alloc(op, &op->Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be));
         TRY(dev_alloc(op, &op->xsplit, (size_t)op->n));
@@ -653,6 +710,30 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         op->k32.Urow = fdUr; op->k32.Dinv = fdDi;
         op->k32.S = fdS; op->k32.H = fdH; op->k32.W = dfloat ? (const void*)op->Wh : (const void*)op->W32;
         op->k32.U = fdU; op->k32.L = fdL;
+        if (bd == 13 && op->npairs) {
+            // partial transposed products of the owner/gather apply
+            int ntile = grid_for(n1, apply_own_tile());
+            size_t nslot = (size_t)op->npairs * ntile * apply_own_nout();
+            TRY(dev_alloc(op, &op->part_own, nslot));
+            if (dfloat) {
+                TRY(dev_alloc(op, &op->part_rdf, 2 * nslot));
+                TRY(dev_alloc(op, &op->part_bdf, nslot));
+                TRY(dev_alloc(op, &op->psi32, (size_t)op->n));
+                TRY(dev_alloc(op, &op->b32, (size_t)op->n));
+                TRY(dev_alloc(op, &op->need_b, 1));
+                if (cudaMemsetAsync(op->need_b, 0, sizeof(int), op->st) != cudaSuccess) {
+                    set_error("dirac_operator_setup: cudaMemsetAsync failed");
+                    dirac_op_free(op);
+                    return DIRAC_E_CUDA;
+                }
+            }
+            cudaError_t ce = apply_own32_prepare();
+            if (ce != cudaSuccess) {
+                set_error(std::string("dirac_operator_setup: ") + cudaGetErrorString(ce));
+                dirac_op_free(op);
+                return DIRAC_E_CUDA;
+            }
+        }
     }
     op->nparts_apply = grid_for(n1, 128) * B.nch;
     op->nparts_vec = grid_for(op->n, 256);
@@ -663,6 +744,12 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     TRY(dev_alloc(op, &op->part_d2, (size_t)np));
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
     TRY(dev_alloc(op, &op->part_n2, (size_t)np));
+    TRY(dev_alloc(op, &op->dev_err, 1));
+    if (cudaMemsetAsync(op->dev_err, 0, sizeof(int), op->st) != cudaSuccess) {
+        set_error("dirac_operator_setup: cudaMemsetAsync failed");
+        dirac_op_free(op);
+        return DIRAC_E_CUDA;
+    }
     // ground state of the kappa = -1, mu = +1/2 channel for the observables
     for (int a = 0; a < B.nch; a++)
         if (B.kap[a] == -1 && B.tmu[a] == 1) op->ground_ch = a;
@@ -677,6 +764,7 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     o.n1 = n1; o.bd = bd; o.half = half; o.nch = B.nch; o.npairs = op->npairs; o.tau = tau; o.c = B.p.c;
     o.ch_kslot = dks; o.ch_kappa = dkap; o.S = dS; o.H = dH;
     o.adj_start = das; o.adj_pair = dap; o.adj_nbr = dan; o.adj_tr = dat;
+    o.own_start = dows; o.own_pair = dowp; o.own_nbr = down; o.in_start = dins; o.in_pair = dinp;
     o.pair_a = dpa; o.pair_b = dpb; o.term_start = dts; o.term_l = dtl; o.term_coef = dtc;
     o.nkeys = (int)keyl.size(); o.key_l = dkl; o.key_mono = dkm; o.term_kd = dkd; o.term_kt = dkt;
     o.term_cab = dcab; o.pair_order = dpo;
@@ -807,6 +895,8 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
     if (n_hist) *n_hist = nh;
     CUDA_TRY(cudaStreamSynchronize(op->st));
     collect_phases(op);
+    dirac_status de = check_dev_err(op, "dirac_step");
+    if (de) return de;
     return result;
 }
 
@@ -851,7 +941,7 @@ __global__ void k_observe(OpView A, const double2* __restrict__ x, const double2
 
 extern "C" dirac_status dirac_observables(dirac_op* op, const void* psi_dev, double* out, int n_out)
 {
-    if (!op || !psi_dev || !out || n_out < 1 || n_out > 3) { set_error("dirac_observables: bad argument"); return DIRAC_E_ARG; }
+    if (!op || !psi_dev || !out || n_out < 1 || n_out > 4) { set_error("dirac_observables: bad argument"); return DIRAC_E_ARG; }
     dim3 grid(grid_for(op->ov.n1, 128), op->ov.nch);
     k_observe<<<grid, 128, 0, op->st>>>(op->ov, (const double2*)psi_dev, op->psi0_g, op->ground_ch, op->part_d,
                                          op->part_d2);
@@ -865,7 +955,11 @@ extern "C" dirac_status dirac_observables(dirac_op* op, const void* psi_dev, dou
     CUDA_TRY(cudaStreamSynchronize(op->st));
     double ns = 0, nh = 0, gx = 0, gy = 0;
     for (int i = 0; i < np; i++) { ns += a[i].x; nh += a[i].y; gx += c[i].x; gy += c[i].y; }
-    double vals[3] = {ns, nh, gx * gx + gy * gy};
+    double vals[4] = {ns, nh, gx * gx + gy * gy, 0.0};
+    if (n_out >= 4) {
+        e = bound_population(op, (const double2*)psi_dev, &vals[3]);
+        if (e) return e;
+    }
     for (int i = 0; i < n_out; i++) out[i] = vals[i];
     return DIRAC_OK;
 }

@@ -26,6 +26,11 @@ struct OpView {
     const int* adj_pair;      // pair of each adjacency entry
     const int* adj_nbr;       // neighbour channel
     const int* adj_tr;        // 0: channel is the pair's lower channel (W x), 1: upper (W^T x)
+    const int* own_start;     // [nch + 1] pairs a channel owns (is the lower channel of), in order
+    const int* own_pair;
+    const int* own_nbr;       // the pair's upper channel
+    const int* in_start;      // [nch + 1] pairs a channel is the upper channel of
+    const int* in_pair;
     const int* pair_a;        // [npairs]
     const int* pair_b;
     const int* term_start;    // [npairs + 1]

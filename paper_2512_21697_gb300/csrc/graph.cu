@@ -418,6 +418,8 @@ extern "C" dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, i
         if (resid_out) resid_out[s] = res[s];
     }
     if (n_hist) *n_hist = c.hist_n;
+    dirac_status de = check_dev_err(op, "dirac_run");
+    if (de) return de;
     if (c.status) {
         set_error("dirac_run: step " + std::to_string(c.step - 1) + " failed with status " + std::to_string(c.status));
         return (dirac_status)c.status;

@@ -60,6 +60,8 @@ int kappa_slot(int kappa);   // 0..2 kappa_max-1
 // Radial blocks of one kappa: S, H0 as bands, unused functions replaced by the identity in S
 // and zero in H0.
 void radial_blocks(const Basis& B, int kappa, Band& S, Band& H);
+// scalar entry (i, j) of a Band, i = 2 slot + type (zero outside the band)
+double band_entry(const Band& M, int i, int j);
 
 // Pulse: the three carriers of the sin^2 envelope and the projected multipole matrices
 // g[l][carrier][n] (Band), n = 0..3 the kappa-polynomial component of int P_i g Q_j dr.

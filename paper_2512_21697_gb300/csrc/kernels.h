@@ -59,9 +59,10 @@ __global__ void k_copy32(int64_t n, const float2* a, float2* b);
 // double-float path (precision 2)
 __global__ void k_split_vec(int64_t n, const double2* __restrict__ x, float4* __restrict__ xd);
 __global__ void k_field_combine_df(PulseView P, int block_elems, const double* s, float2* G);
-__global__ void k_build_K_df(OpView A, int block_elems, const float2* G, float2* K);
-void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* K, const float4* cab, float* Wh,
+__global__ void k_build_K_df(OpView A, int block_elems, const float2* G, float2* K, float2* KT);
+void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* K, const float2* KT, const float4* cab, float* Wh,
                         float* Wl);
+__global__ void k_split_uv3(int64_t n, const double2* psi, const double2* x, float4* u, float4* v, float2* psi32);
 __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
                            float4* __restrict__ u, float4* __restrict__ v);
 void launch_residual_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
@@ -76,6 +77,8 @@ __global__ void k_lincomb64(int64_t n, double c0, const double2* a, double c1, c
 __global__ void k_finish64(int what, KState* st, int np, const double2* pd, const double* pn, const double2* pd2,
                            const double* pn2, int max_iter);
 __global__ void k_set_time(double* t_eval, double t);
+__global__ void k_bnorm_if(KState* st, int* flag, int np, const double* pn);
+__global__ void k_set_int(int* p, int v);
 __global__ void k_set_step_time(double* t_eval, double t_start, int step, double dt, double t_off);
 // evaluation time of step `step`: (t_start + step dt) + t_off, each operation rounded separately
 // (no contraction), so the host-driven and the graph-driven loops agree to the last bit
@@ -93,5 +96,20 @@ __device__ __forceinline__ double extrapolate(int nh, double p, double a, double
     return p;
 }
 __global__ void k_extrapolate(int64_t n, int nh, const double2* psi, const double2* h1, const double2* h2, double2* x);
+
+// complex64 apply with each coupling block read once (owner pass + gather pass, bd = 13)
+size_t apply_own32_smem();
+int apply_own_tile();
+int apply_own_nout();
+bool apply_own_supported(const OpView& A);
+cudaError_t apply_own32_prepare();
+size_t residual_own_df_smem();
+void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
+                            const float4* v, const float2* psi32, const float* Wh, const float* Wl, double2* r,
+                            float2* b, double2* part_r, float4* part_b, const int* need_b, double* pn_r,
+                            double* pn_b, int* err);
+void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const float* H, int sign, const void* x,
+                        const float* W, void* y, float4* part, const void* bsub, const void* dv, double2* pdot,
+                        double* pnrm, const KState* skip, int* err);
 
 }  // namespace dg

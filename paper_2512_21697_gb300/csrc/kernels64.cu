@@ -184,6 +184,21 @@ __device__ __forceinline__ bool finite2(double2 a) { return isfinite(a.x) && isf
 //       rho = ||r||^2), resets the per-start counters;  8 = as 1 with bnorm2 = ||r||^2;  2 = alpha = rho / <rh, v>;
 //       3 = ||s||^2 check;  6 = omega = <t, s> / <t, t> from pd = sum <s, t>, pn = sum ||t||^2;
 //       5 = end of iteration: rho = <rh, r>, ||r||^2, beta.
+// ||b||^2 of a step's first refinement pass (flag set): bnorm2 = sum of the partials, flag cleared
+__global__ void k_bnorm_if(KState* st, int* flag, int np, const double* pn)
+{
+    __shared__ double2 d1;
+    __shared__ double n1;
+    if (!*flag) return;   // uniform over the block
+    block_sum_fixed(np, nullptr, pn, &d1, &n1);
+    __syncthreads();
+    if (threadIdx.x) return;
+    st->bnorm2 = n1;
+    *flag = 0;
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
 __global__ void k_finish64(int what, KState* st, int np, const double2* pd, const double* pn, const double2* pd2,
                            const double* pn2, int max_iter)
 {

@@ -37,82 +37,96 @@ __global__ void k_field_combine_df(PulseView P, int block_elems, const double* s
     G[(int64_t)ln * block_elems + e] = df_split(v);
 }
 
-// K[key][e] = sum_n m_n G^n_l[e]; the monomials 1, k', k, k'k are integers, exact in FP32
-__global__ void k_build_K_df(OpView A, int block_elems, const float2* G, float2* K)
+// K[key][e] = sum_n m_n G^n_l[e] and its block transpose KT[key][r][d][t][u] = K[key][r'][2h-d][u][t]
+// (r' = r + d - h; zero where r' leaves the box), so that the assembly reads both the direct and the
+// transposed term of a pair at the same coalesced position.  The monomials 1, k', k, k'k are
+// integers, exact in FP32; G is a few MB and stays in L2, which serves the scattered reads of KT.
+__global__ void k_build_K_df(OpView A, int block_elems, const float2* __restrict__ G, float2* __restrict__ K,
+                             float2* __restrict__ KT)
 {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= block_elems) return;
+    int bd4 = A.bd * 4;
+    int r = e / bd4, rem = e - r * bd4, d = rem >> 2, t = (rem >> 1) & 1, u = rem & 1;
+    int rr = r + d - A.half;
+    bool inb = rr >= 0 && rr < A.n1;
+    int et = inb ? ((rr * A.bd + (2 * A.half - d)) * 2 + u) * 2 + t : 0;
     for (int key = blockIdx.y; key < A.nkeys; key += gridDim.y) {
         const double* m = A.key_mono + (int64_t)key * 4;
-        const float2* Gl = G + (int64_t)A.key_l[key] * 4 * block_elems + e;
-        DfAcc acc;
+        const float2* Gl = G + (int64_t)A.key_l[key] * 4 * block_elems;
+        DfAcc acc, act;
         df_zero(acc);
+        df_zero(act);
         for (int n = 0; n < 4; n++) {
-            float2 g = Gl[(int64_t)n * block_elems];
-            df_fma(acc, (float)m[n], 0.f, g.x, g.y);
+            float mn = (float)m[n];
+            float2 g = Gl[(int64_t)n * block_elems + e];
+            df_fma(acc, mn, 0.f, g.x, g.y);
+            if (inb) {
+                float2 gt = Gl[(int64_t)n * block_elems + et];
+                df_fma(act, mn, 0.f, gt.x, gt.y);
+            }
         }
-        float h = acc.s + acc.c;
+        float h = acc.s + acc.c, ht = act.s + act.c;
         K[(int64_t)key * block_elems + e] = make_float2(h, (acc.s - h) + acc.c);
+        KT[(int64_t)key * block_elems + e] = make_float2(ht, (act.s - ht) + act.c);
     }
 }
 
-// W_ab = sum_terms cA K_l(ka,kb) + cB K_l(kb,ka)^T in double-float; hi words to Wh (also the FP32
-// coupling values of the inner solve), lo words to Wl.  One thread per (pair, radial row): the
-// term list is read once and the 13 block diagonals of the row give independent work.
+// W_ab[r][d] = sum_terms cA K_l(ka,kb)[r][d] + cB KT_l(kb,ka)[r][d] in double-float; hi words to Wh
+// (also the FP32 coupling values of the inner solve), lo words to Wl.  One thread per (radial row,
+// block diagonal) of a pair: consecutive threads read and write consecutive 32-byte blocks.  Pairs
+// sharing their kappa pair (all mu) are adjacent in the pair order, so their K bands come from L2.
 template <int BD>
 __global__ void __launch_bounds__(128) k_assemble_df(OpView A, const float2* __restrict__ K,
-                                                     const float4* __restrict__ cab, float* __restrict__ Wh,
-                                                     float* __restrict__ Wl)
+                                                     const float2* __restrict__ KT, const float4* __restrict__ cab,
+                                                     float* __restrict__ Wh, float* __restrict__ Wl)
 {
     const int bd = BD > 0 ? BD : A.bd;
     const int half = (bd - 1) / 2;
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= A.n1) return;
-    int64_t nb = (int64_t)A.n1 * bd * 4;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    int nrd = A.n1 * bd;
+    if (idx >= nrd) return;
+    int r = idx / bd, d = idx - r * bd, rr = r + d - half;
+    bool inb = rr >= 0 && rr < A.n1;
+    int64_t nb = (int64_t)nrd * 4;
     for (int64_t pi = blockIdx.y; pi < A.npairs; pi += gridDim.y) {
         int64_t p = A.pair_order[pi];
-        int ka = A.ch_kappa[A.pair_a[p]], kb = A.ch_kappa[A.pair_b[p]];
-        int q0 = A.term_start[p], q1 = A.term_start[p + 1];
-#pragma unroll 1
-        for (int d = 0; d < bd; d++) {
-            int rr = r + d - half;
-            DfAcc w[4];
-            for (int k = 0; k < 4; k++) df_zero(w[k]);
-            if (rr >= 0 && rr < A.n1) {
-                for (int q = q0; q < q1; q++) {
-                    float4 cf = cab[q];   // (cA hi, cA lo, cB hi, cB lo)
-                    const float4* g = reinterpret_cast<const float4*>(K + A.term_kd[q] * nb + ((int64_t)r * bd + d) * 4);
-                    const float4* gt =
-                        reinterpret_cast<const float4*>(K + A.term_kt[q] * nb + ((int64_t)rr * bd + (2 * half - d)) * 4);
-                    float4 g01 = g[0], g23 = g[1], h01 = gt[0], h23 = gt[1];
-                    // direct block g[t][u] (t = row type); transposed block gt[u][t]
-                    df_fma(w[0], cf.x, cf.y, g01.x, g01.y); df_fma(w[0], cf.z, cf.w, h01.x, h01.y);
-                    df_fma(w[1], cf.x, cf.y, g01.z, g01.w); df_fma(w[1], cf.z, cf.w, h23.x, h23.y);
-                    df_fma(w[2], cf.x, cf.y, g23.x, g23.y); df_fma(w[2], cf.z, cf.w, h01.z, h01.w);
-                    df_fma(w[3], cf.x, cf.y, g23.z, g23.w); df_fma(w[3], cf.z, cf.w, h23.z, h23.w);
-                }
-                for (int k = 0; k < 4; k++) {
-                    int t = k / 2, u = k % 2;
-                    if (!used_fn_df(ka, r, t) || !used_fn_df(kb, rr, u)) df_zero(w[k]);
-                }
+        DfAcc w[4];
+        for (int k = 0; k < 4; k++) df_zero(w[k]);
+        if (inb) {
+            int q0 = A.term_start[p], q1 = A.term_start[p + 1];
+            for (int q = q0; q < q1; q++) {
+                float4 cf = cab[q];   // (cA hi, cA lo, cB hi, cB lo)
+                const float4* g = reinterpret_cast<const float4*>(K + A.term_kd[q] * nb + (int64_t)idx * 4);
+                const float4* gt = reinterpret_cast<const float4*>(KT + A.term_kt[q] * nb + (int64_t)idx * 4);
+                float4 g01 = g[0], g23 = g[1], h01 = gt[0], h23 = gt[1];
+                df_fma(w[0], cf.x, cf.y, g01.x, g01.y); df_fma(w[0], cf.z, cf.w, h01.x, h01.y);
+                df_fma(w[1], cf.x, cf.y, g01.z, g01.w); df_fma(w[1], cf.z, cf.w, h01.z, h01.w);
+                df_fma(w[2], cf.x, cf.y, g23.x, g23.y); df_fma(w[2], cf.z, cf.w, h23.x, h23.y);
+                df_fma(w[3], cf.x, cf.y, g23.z, g23.w); df_fma(w[3], cf.z, cf.w, h23.z, h23.w);
             }
-            int64_t o = ((p * A.n1 + r) * bd + d) * 4;
-            float hh[4], ll[4];
+            int ka = A.ch_kappa[A.pair_a[p]], kb = A.ch_kappa[A.pair_b[p]];
             for (int k = 0; k < 4; k++) {
-                hh[k] = w[k].s + w[k].c;
-                ll[k] = (w[k].s - hh[k]) + w[k].c;
+                int t = k / 2, u = k % 2;
+                if (!used_fn_df(ka, r, t) || !used_fn_df(kb, rr, u)) df_zero(w[k]);
             }
-            *reinterpret_cast<float4*>(Wh + o) = make_float4(hh[0], hh[1], hh[2], hh[3]);
-            *reinterpret_cast<float4*>(Wl + o) = make_float4(ll[0], ll[1], ll[2], ll[3]);
         }
+        int64_t o = (p * nrd + idx) * 4;
+        float hh[4], ll[4];
+        for (int k = 0; k < 4; k++) {
+            hh[k] = w[k].s + w[k].c;
+            ll[k] = (w[k].s - hh[k]) + w[k].c;
+        }
+        *reinterpret_cast<float4*>(Wh + o) = make_float4(hh[0], hh[1], hh[2], hh[3]);
+        *reinterpret_cast<float4*>(Wl + o) = make_float4(ll[0], ll[1], ll[2], ll[3]);
     }
 }
 
-void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* K, const float4* cab, float* Wh,
-                        float* Wl)
+void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* K, const float2* KT,
+                        const float4* cab, float* Wh, float* Wl)
 {
-    if (A.bd == 13) k_assemble_df<13><<<grid, 128, 0, st>>>(A, K, cab, Wh, Wl);
-    else k_assemble_df<0><<<grid, 128, 0, st>>>(A, K, cab, Wh, Wl);
+    if (A.bd == 13) k_assemble_df<13><<<grid, 128, 0, st>>>(A, K, KT, cab, Wh, Wl);
+    else k_assemble_df<0><<<grid, 128, 0, st>>>(A, K, KT, cab, Wh, Wl);
 }
 
 // u = psi + x, v = psi - x in double, each split into (re_hi, re_lo, im_hi, im_lo)
@@ -125,6 +139,19 @@ __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const dou
     float2 a = df_split(p.x + q.x), b = df_split(p.y + q.y), c = df_split(p.x - q.x), d = df_split(p.y - q.y);
     u[i] = make_float4(a.x, a.y, b.x, b.y);
     v[i] = make_float4(c.x, c.y, d.x, d.y);
+}
+
+// u = psi + x, v = psi - x (split) and psi rounded to FP32
+__global__ void k_split_uv3(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
+                            float4* __restrict__ u, float4* __restrict__ v, float2* __restrict__ psi32)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double2 p = psi[i], q = x[i];
+    float2 a = df_split(p.x + q.x), b = df_split(p.y + q.y), c = df_split(p.x - q.x), d = df_split(p.y - q.y);
+    u[i] = make_float4(a.x, a.y, b.x, b.y);
+    v[i] = make_float4(c.x, c.y, d.x, d.y);
+    psi32[i] = make_float2((float)p.x, (float)p.y);
 }
 
 // Refinement residual r = A_- psi - A_+ x in double-float through one coupling product:

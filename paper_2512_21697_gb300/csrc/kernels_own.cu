@@ -1,0 +1,545 @@
+// kernels_own.cu -- the complex64 operator apply A_+- x of the inner solve (Eq. solPsi with the
+// coupling of Eq. fullH) with every stored coupling block read from HBM once.
+//
+// A coupling block W_ab (pair a < b) is used twice: W_ab x_b in the rows of channel a and W_ab^T x_a
+// in the rows of channel b.  Two passes:
+//   k_apply_own32:    block = (channel a, tile of TR radial rows).  For each pair the channel owns,
+//                     the TR rows of W_ab are copied into shared memory by the bulk-copy engine
+//                     (cp.async.bulk, an NST-deep ring completed by mbarriers); threads 0..TR-1
+//                     accumulate W_ab x_b for their row, threads TR..2TR-1 form the transposed
+//                     product W_ab^T x_a restricted to those rows (TR + 2h output rows) and store it
+//                     in the pair's partial slot.  y_a = D x_a - sign sum W_ab x_b is written.
+//   k_apply_gather32: block = (channel b, tile).  y_b += sign sum of the partials of the pairs b is
+//                     the upper channel of (own tile, and the halo rows of the two neighbouring
+//                     tiles), in a fixed order, then the BiCGSTAB epilogues (y <- bsub - y, <dv, y>,
+//                     ||y||^2).
+// HBM traffic per apply: the coupling values once, plus 2 x 16 B per (pair, row) of partials, i.e.
+// 8 % of the values' bytes at bd = 13.  Sums are formed in a fixed order, so results are
+// reproducible run to run.
+//
+// The refinement residual of the mixed-precision step has the same two-pass form in double-float
+// arithmetic (k_residual_own_df / k_residual_gather_df): the ring holds the hi and lo words of the
+// coupling values, partials are stored in double.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "df64.cuh"
+#include "device.h"
+#include "kernels.h"
+
+namespace dg {
+
+namespace {
+
+constexpr int TR = 128;          // radial rows per tile
+constexpr int NST = 3;           // bulk-copy ring depth
+constexpr int BDO = 13;          // block diagonals (order-7 splines)
+constexpr int HO = (BDO - 1) / 2;
+constexpr int ROWF = BDO * 4;    // floats per stored row of one pair
+constexpr int NOUT = TR + 2 * HO;
+constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bulk-copy wait limit
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for a ring stage; false after the time limit (the caller records the failure)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+{
+    long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    return true;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(2 * TR) k_apply_own32(OpView A, const float* __restrict__ S,
+                                                        const float* __restrict__ H, int sign,
+                                                        const float2* __restrict__ x, const float* __restrict__ W,
+                                                        float2* __restrict__ y, float4* __restrict__ part,
+                                                        const KState* skip, int* err)
+{
+    if (skip && skip->done) return;   // uniform over the grid: the solve already finished
+    extern __shared__ __align__(128) float wring[];   // [NST][TR * ROWF]
+    __shared__ float4 xs[TR];                        // x_a rows of the tile: (x0.re, x0.im, x1.re, x1.im)
+    __shared__ uint64_t bar[NST];
+    const int n1 = A.n1, ntile = gridDim.y;
+    const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
+    const int rows = min(TR, n1 - r0);
+    const uint32_t bytes = (uint32_t)rows * ROWF * 4;
+    const int own0 = A.own_start[ch], nown = A.own_start[ch + 1] - own0;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int s = 0; s < NST; s++) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < min(NST, nown); k++) {
+            int64_t p = A.own_pair[own0 + k];
+            mbar_expect_tx(&bar[k], bytes);
+            bulk_load(wring + k * TR * ROWF, W + (p * n1 + r0) * ROWF, bytes, &bar[k]);
+        }
+    const float2* xa = x + (int64_t)ch * 2 * n1;
+    if (tid < TR) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (tid < rows) {
+            float2 a = xa[2 * (r0 + tid)], b = xa[2 * (r0 + tid) + 1];
+            v = make_float4(a.x, a.y, b.x, b.y);
+        }
+        xs[tid] = v;
+    }
+    // diagonal block (S + sign i tau H0) x_a for the direct threads' row
+    const int r = r0 + tid;
+    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+    if (tid < TR && r < n1) {
+        int ks = A.ch_kslot[ch];
+        const float* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
+        const float* Hk = H + ((int64_t)ks * n1 + r) * ROWF;
+        float st = (float)(sign * A.tau);
+#pragma unroll
+        for (int d = 0; d < BDO; d++) {
+            int rr = r + d - HO;
+            if (rr < 0 || rr >= n1) continue;
+            float4 xv = *reinterpret_cast<const float4*>(xa + 2 * rr);
+            float4 sv = *reinterpret_cast<const float4*>(Sk + d * 4);
+            float4 hv = *reinterpret_cast<const float4*>(Hk + d * 4);
+            float h00 = st * hv.x, h01 = st * hv.y, h10 = st * hv.z, h11 = st * hv.w;
+            y0.x += sv.x * xv.x + sv.y * xv.z - (h00 * xv.y + h01 * xv.w);
+            y0.y += sv.x * xv.y + sv.y * xv.w + (h00 * xv.x + h01 * xv.z);
+            y1.x += sv.z * xv.x + sv.w * xv.z - (h10 * xv.y + h11 * xv.w);
+            y1.y += sv.z * xv.y + sv.w * xv.w + (h10 * xv.x + h11 * xv.z);
+        }
+    }
+    __syncthreads();   // xs ready
+    float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
+    int kfail = -1;   // block-uniform: first ring stage whose copy did not arrive in time
+    for (int k = 0; k < nown; k++) {
+        const int s = k % NST;
+        const bool arrived = mbar_wait(&bar[s], (uint32_t)((k / NST) & 1));
+        const int e = own0 + k;
+        const int64_t p = A.own_pair[e];
+        const float* Ws = wring + s * TR * ROWF;
+        if (arrived) {
+            if (tid < TR) {
+                // direct: row r of W_ab against x_b
+                if (r < n1) {
+                    const float2* xb = x + (int64_t)A.own_nbr[e] * 2 * n1;
+#pragma unroll
+                    for (int d = 0; d < BDO; d++) {
+                        int rr = r + d - HO;
+                        if (rr < 0 || rr >= n1) continue;
+                        float4 xv = *reinterpret_cast<const float4*>(xb + 2 * rr);
+                        float4 w = *reinterpret_cast<const float4*>(Ws + tid * ROWF + d * 4);
+                        d0.x = fmaf(w.x, xv.x, d0.x); d0.x = fmaf(w.y, xv.z, d0.x);
+                        d0.y = fmaf(w.x, xv.y, d0.y); d0.y = fmaf(w.y, xv.w, d0.y);
+                        d1.x = fmaf(w.z, xv.x, d1.x); d1.x = fmaf(w.w, xv.z, d1.x);
+                        d1.y = fmaf(w.z, xv.y, d1.y); d1.y = fmaf(w.w, xv.w, d1.y);
+                    }
+                }
+            } else {
+                // transposed: output rows rb = r0 - h + j of channel b from the tile's rows of W_ab
+                float4* pp = part + ((int64_t)p * ntile + tile) * NOUT;
+                for (int j = tid - TR; j < NOUT; j += TR) {
+                    float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < BDO; d++) {
+                        int lr = j - d;   // W row r0 + lr couples to column rb through diagonal d
+                        if (lr < 0 || lr >= rows) continue;
+                        float4 w = *reinterpret_cast<const float4*>(Ws + lr * ROWF + d * 4);
+                        float4 xv = xs[lr];
+                        // (W^T)[t][u] = W[u][t]
+                        t0.x = fmaf(w.x, xv.x, t0.x); t0.x = fmaf(w.z, xv.z, t0.x);
+                        t0.y = fmaf(w.x, xv.y, t0.y); t0.y = fmaf(w.z, xv.w, t0.y);
+                        t1.x = fmaf(w.y, xv.x, t1.x); t1.x = fmaf(w.w, xv.z, t1.x);
+                        t1.y = fmaf(w.y, xv.y, t1.y); t1.y = fmaf(w.w, xv.w, t1.y);
+                    }
+                    pp[j] = make_float4(t0.x, t0.y, t1.x, t1.y);
+                }
+            }
+        }
+        // every thread is done with stage s (and agrees whether its copy arrived)
+        if (!__syncthreads_and(arrived)) { kfail = k; break; }
+        if (tid == 0 && k + NST < nown) {
+            int64_t pn = A.own_pair[own0 + k + NST];
+            fence_proxy_async();
+            mbar_expect_tx(&bar[s], bytes);
+            bulk_load(wring + s * TR * ROWF, W + (pn * n1 + r0) * ROWF, bytes, &bar[s]);
+        }
+    }
+    if (kfail >= 0) {
+        if (tid == 0) atomicExch(err, 1);
+        // copies issued for stages kfail .. kfail + NST - 1 may still be in flight: give each the
+        // same time limit before the block's shared memory is released
+        for (int k = kfail; k < min(nown, kfail + NST); k++) mbar_wait(&bar[k % NST], (uint32_t)((k / NST) & 1));
+        return;
+    }
+    if (tid < TR && r < n1) {
+        float sg = (float)sign;
+        y0.x = fmaf(-sg, d0.x, y0.x); y0.y = fmaf(-sg, d0.y, y0.y);
+        y1.x = fmaf(-sg, d1.x, y1.x); y1.y = fmaf(-sg, d1.y, y1.y);
+        int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
+        *reinterpret_cast<float4*>(y + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
+    }
+}
+
+__global__ void __launch_bounds__(TR) k_apply_gather32(OpView A, int sign, float2* __restrict__ y,
+                                                       const float4* __restrict__ part,
+                                                       const float2* __restrict__ bsub,
+                                                       const float2* __restrict__ dv, double2* part_dot,
+                                                       double* part_nrm, const KState* skip)
+{
+    if (skip && skip->done) return;
+    const int n1 = A.n1, ntile = gridDim.y;
+    const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR, tid = threadIdx.x;
+    const int r = r0 + tid;
+    const bool act = r < n1;
+    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
+    if (act) {
+        int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
+        float4 yv = *reinterpret_cast<const float4*>(y + o);
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = A.in_start[ch]; e < A.in_start[ch + 1]; e++) {
+            const float4* pp = part + (int64_t)A.in_pair[e] * ntile * NOUT;
+            float4 v = pp[(int64_t)tile * NOUT + tid + HO];
+            if (tid < HO && tile > 0) {
+                float4 u = pp[(int64_t)(tile - 1) * NOUT + TR + HO + tid];
+                v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+            }
+            if (tid >= TR - HO && tile + 1 < ntile) {
+                float4 u = pp[(int64_t)(tile + 1) * NOUT + tid - TR + HO];
+                v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+            }
+            t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
+        }
+        float sg = (float)sign;
+        y0 = make_float2(fmaf(sg, t.x, yv.x), fmaf(sg, t.y, yv.y));
+        y1 = make_float2(fmaf(sg, t.z, yv.z), fmaf(sg, t.w, yv.w));
+        if (bsub) {
+            float4 b = *reinterpret_cast<const float4*>(bsub + o);
+            y0 = make_float2(b.x - y0.x, b.y - y0.y);
+            y1 = make_float2(b.z - y1.x, b.w - y1.y);
+        }
+        *reinterpret_cast<float4*>(y + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
+    }
+    if (part_dot || part_nrm) {
+        double2 dsum = make_double2(0, 0);
+        double nsum = 0;
+        if (act) {
+            int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
+            if (dv) {
+                float4 a = *reinterpret_cast<const float4*>(dv + o);
+                dsum.x = (double)a.x * y0.x + (double)a.y * y0.y + (double)a.z * y1.x + (double)a.w * y1.y;
+                dsum.y = (double)a.x * y0.y - (double)a.y * y0.x + (double)a.z * y1.y - (double)a.w * y1.x;
+            }
+            nsum = (double)y0.x * y0.x + (double)y0.y * y0.y + (double)y1.x * y1.x + (double)y1.y * y1.y;
+        }
+        block_reduce_store(dsum, nsum, part_dot, part_nrm, (int64_t)blockIdx.y * gridDim.x + blockIdx.x);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Refinement residual r = A_- psi - A_+ x = S (psi - x) - i tau H0 (psi + x) + (W - W^T)(psi + x)
+// in double-float, from u = psi + x and v = psi - x split into (re hi, re lo, im hi, im lo), and,
+// when *need_b is set (the first pass of a step), b = A_- psi in FP32 products for the tolerance
+// scale ||b||.  Owner pass: r_a (diagonal + direct coupling) to r_out, b_a to b_out; partials of the
+// transposed products to part_r (double, 2 per row) and part_b.
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr int NSTD = 2;          // ring depth of the double-float pass (hi + lo words per stage)
+}
+
+__global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const float2* __restrict__ S,
+                                                            const float2* __restrict__ Ht,
+                                                            const float4* __restrict__ u,
+                                                            const float4* __restrict__ v,
+                                                            const float2* __restrict__ psi32,
+                                                            const float* __restrict__ Wh, const float* __restrict__ Wl,
+                                                            double2* __restrict__ r_out, float2* __restrict__ b_out,
+                                                            double2* __restrict__ part_r, float4* __restrict__ part_b,
+                                                            const int* need_b_flag, int* err)
+{
+    extern __shared__ __align__(128) float wring[];   // [NSTD][2][TR * ROWF]: hi words, lo words
+    __shared__ float4 us[2 * TR];                    // u_a rows: (type 0, type 1) split complex
+    __shared__ float4 ps[TR];                        // psi_a rows in FP32: (p0.re, p0.im, p1.re, p1.im)
+    __shared__ uint64_t bar[NSTD];
+    const bool need_b = *need_b_flag != 0;
+    const int n1 = A.n1, ntile = gridDim.y;
+    const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
+    const int rows = min(TR, n1 - r0);
+    const uint32_t bytes = (uint32_t)rows * ROWF * 4;
+    const int own0 = A.own_start[ch], nown = A.own_start[ch + 1] - own0;
+    const int tid = threadIdx.x;
+    const int stage_f = 2 * TR * ROWF;
+    if (tid == 0) {
+        for (int s = 0; s < NSTD; s++) mbar_init(&bar[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < min(NSTD, nown); k++) {
+            int64_t p = A.own_pair[own0 + k];
+            mbar_expect_tx(&bar[k], 2 * bytes);
+            bulk_load(wring + k * stage_f, Wh + (p * n1 + r0) * ROWF, bytes, &bar[k]);
+            bulk_load(wring + k * stage_f + TR * ROWF, Wl + (p * n1 + r0) * ROWF, bytes, &bar[k]);
+        }
+    const float4* ua = u + (int64_t)ch * 2 * n1;
+    const float4* va = v + (int64_t)ch * 2 * n1;
+    const float2* pa = psi32 + (int64_t)ch * 2 * n1;
+    if (tid < TR) {
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool in = tid < rows;
+        us[2 * tid] = in ? ua[2 * (r0 + tid)] : z;
+        us[2 * tid + 1] = in ? ua[2 * (r0 + tid) + 1] : z;
+        ps[tid] = in ? *reinterpret_cast<const float4*>(pa + 2 * (r0 + tid)) : z;
+    }
+    const int r = r0 + tid;
+    DfAcc yv[4];   // (type 0 re, im, type 1 re, im)
+    for (int k = 0; k < 4; k++) df_zero(yv[k]);
+    float bb[4] = {0.f, 0.f, 0.f, 0.f};
+    if (tid < TR && r < n1) {
+        int ks = A.ch_kslot[ch];
+        const float2* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
+        const float2* Hk = Ht + ((int64_t)ks * n1 + r) * ROWF;
+#pragma unroll
+        for (int d = 0; d < BDO; d++) {
+            int rr = r + d - HO;
+            if (rr < 0 || rr >= n1) continue;
+            float4 u0 = ua[2 * rr], u1 = ua[2 * rr + 1], v0 = va[2 * rr], v1 = va[2 * rr + 1];
+            float4 pv = need_b ? *reinterpret_cast<const float4*>(pa + 2 * rr) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int t = 0; t < 2; t++) {
+                float2 s0 = Sk[d * 4 + 2 * t], s1 = Sk[d * 4 + 2 * t + 1];
+                float2 h0 = Hk[d * 4 + 2 * t], h1 = Hk[d * 4 + 2 * t + 1];
+                // re: S v_re + tau H u_im ;  im: S v_im - tau H u_re
+                df_fma(yv[2 * t], s0.x, s0.y, v0.x, v0.y);
+                df_fma(yv[2 * t], s1.x, s1.y, v1.x, v1.y);
+                df_fma(yv[2 * t], h0.x, h0.y, u0.z, u0.w);
+                df_fma(yv[2 * t], h1.x, h1.y, u1.z, u1.w);
+                df_fma(yv[2 * t + 1], s0.x, s0.y, v0.z, v0.w);
+                df_fma(yv[2 * t + 1], s1.x, s1.y, v1.z, v1.w);
+                df_fma(yv[2 * t + 1], -h0.x, -h0.y, u0.x, u0.y);
+                df_fma(yv[2 * t + 1], -h1.x, -h1.y, u1.x, u1.y);
+                // b = (S - i tau H) psi
+                bb[2 * t] += s0.x * pv.x + s1.x * pv.z + h0.x * pv.y + h1.x * pv.w;
+                bb[2 * t + 1] += s0.x * pv.y + s1.x * pv.w - h0.x * pv.x - h1.x * pv.z;
+            }
+        }
+    }
+    __syncthreads();   // us, ps ready
+    DfAcc dd[4];
+    for (int k = 0; k < 4; k++) df_zero(dd[k]);
+    float db[4] = {0.f, 0.f, 0.f, 0.f};
+    int kfail = -1;
+    for (int k = 0; k < nown; k++) {
+        const int s = k % NSTD;
+        const bool arrived = mbar_wait(&bar[s], (uint32_t)((k / NSTD) & 1));
+        const int e = own0 + k;
+        const int64_t p = A.own_pair[e];
+        const float* Hs = wring + s * stage_f;
+        const float* Ls = Hs + TR * ROWF;
+        if (arrived) {
+            if (tid < TR) {
+                if (r < n1) {
+                    const int nb = A.own_nbr[e];
+                    const float4* ub = u + (int64_t)nb * 2 * n1;
+                    const float2* pb = psi32 + (int64_t)nb * 2 * n1;
+#pragma unroll
+                    for (int d = 0; d < BDO; d++) {
+                        int rr = r + d - HO;
+                        if (rr < 0 || rr >= n1) continue;
+                        float4 x0 = ub[2 * rr], x1 = ub[2 * rr + 1];
+                        float4 wh = *reinterpret_cast<const float4*>(Hs + tid * ROWF + d * 4);
+                        float4 wl = *reinterpret_cast<const float4*>(Ls + tid * ROWF + d * 4);
+                        // W[t][u] = (w.x, w.y ; w.z, w.w)
+                        df_fma(dd[0], wh.x, wl.x, x0.x, x0.y); df_fma(dd[0], wh.y, wl.y, x1.x, x1.y);
+                        df_fma(dd[1], wh.x, wl.x, x0.z, x0.w); df_fma(dd[1], wh.y, wl.y, x1.z, x1.w);
+                        df_fma(dd[2], wh.z, wl.z, x0.x, x0.y); df_fma(dd[2], wh.w, wl.w, x1.x, x1.y);
+                        df_fma(dd[3], wh.z, wl.z, x0.z, x0.w); df_fma(dd[3], wh.w, wl.w, x1.z, x1.w);
+                        if (need_b) {
+                            float4 q = *reinterpret_cast<const float4*>(pb + 2 * rr);
+                            db[0] += wh.x * q.x + wh.y * q.z;
+                            db[1] += wh.x * q.y + wh.y * q.w;
+                            db[2] += wh.z * q.x + wh.w * q.z;
+                            db[3] += wh.z * q.y + wh.w * q.w;
+                        }
+                    }
+                }
+            } else {
+                double2* pr = part_r + (((int64_t)p * ntile + tile) * NOUT) * 2;
+                float4* pbp = part_b + ((int64_t)p * ntile + tile) * NOUT;
+                for (int j = tid - TR; j < NOUT; j += TR) {
+                    DfAcc tt[4];
+                    for (int q = 0; q < 4; q++) df_zero(tt[q]);
+                    float tb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                    for (int d = 0; d < BDO; d++) {
+                        int lr = j - d;
+                        if (lr < 0 || lr >= rows) continue;
+                        float4 wh = *reinterpret_cast<const float4*>(Hs + lr * ROWF + d * 4);
+                        float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
+                        float4 x0 = us[2 * lr], x1 = us[2 * lr + 1];
+                        // (W^T)[t][u] = W[u][t]
+                        df_fma(tt[0], wh.x, wl.x, x0.x, x0.y); df_fma(tt[0], wh.z, wl.z, x1.x, x1.y);
+                        df_fma(tt[1], wh.x, wl.x, x0.z, x0.w); df_fma(tt[1], wh.z, wl.z, x1.z, x1.w);
+                        df_fma(tt[2], wh.y, wl.y, x0.x, x0.y); df_fma(tt[2], wh.w, wl.w, x1.x, x1.y);
+                        df_fma(tt[3], wh.y, wl.y, x0.z, x0.w); df_fma(tt[3], wh.w, wl.w, x1.z, x1.w);
+                        if (need_b) {
+                            float4 q = ps[lr];
+                            tb[0] += wh.x * q.x + wh.z * q.z;
+                            tb[1] += wh.x * q.y + wh.z * q.w;
+                            tb[2] += wh.y * q.x + wh.w * q.z;
+                            tb[3] += wh.y * q.y + wh.w * q.w;
+                        }
+                    }
+                    pr[2 * j] = make_double2(df_value(tt[0]), df_value(tt[1]));
+                    pr[2 * j + 1] = make_double2(df_value(tt[2]), df_value(tt[3]));
+                    if (need_b) pbp[j] = make_float4(tb[0], tb[1], tb[2], tb[3]);
+                }
+            }
+        }
+        if (!__syncthreads_and(arrived)) { kfail = k; break; }
+        if (tid == 0 && k + NSTD < nown) {
+            int64_t pn = A.own_pair[own0 + k + NSTD];
+            fence_proxy_async();
+            mbar_expect_tx(&bar[s], 2 * bytes);
+            bulk_load(wring + s * stage_f, Wh + (pn * n1 + r0) * ROWF, bytes, &bar[s]);
+            bulk_load(wring + s * stage_f + TR * ROWF, Wl + (pn * n1 + r0) * ROWF, bytes, &bar[s]);
+        }
+    }
+    if (kfail >= 0) {
+        if (tid == 0) atomicExch(err, 1);
+        for (int k = kfail; k < min(nown, kfail + NSTD); k++) mbar_wait(&bar[k % NSTD], (uint32_t)((k / NSTD) & 1));
+        return;
+    }
+    if (tid < TR && r < n1) {
+        for (int k = 0; k < 4; k++) df_add(yv[k], dd[k], 1.f);
+        int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
+        r_out[o] = make_double2(df_value(yv[0]), df_value(yv[1]));
+        r_out[o + 1] = make_double2(df_value(yv[2]), df_value(yv[3]));
+        if (need_b)
+            *reinterpret_cast<float4*>(b_out + o) =
+                make_float4(bb[0] + db[0], bb[1] + db[1], bb[2] + db[2], bb[3] + db[3]);
+    }
+}
+
+// r_b -= sum of the transposed partials (own tile and the neighbours' halo rows, fixed order);
+// partials of ||r||^2 and, on a step's first pass, of ||b||^2
+__global__ void __launch_bounds__(TR) k_residual_gather_df(OpView A, double2* __restrict__ r_out,
+                                                           const float2* __restrict__ b_out,
+                                                           const double2* __restrict__ part_r,
+                                                           const float4* __restrict__ part_b,
+                                                           const int* need_b_flag, double* pn_r, double* pn_b)
+{
+    const bool need_b = *need_b_flag != 0;
+    const int n1 = A.n1, ntile = gridDim.y;
+    const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR, tid = threadIdx.x;
+    const int r = r0 + tid;
+    double nr = 0, nb = 0;
+    if (r < n1) {
+        int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
+        double2 y0 = r_out[o], y1 = r_out[o + 1];
+        float4 bv = need_b ? *reinterpret_cast<const float4*>(b_out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int e = A.in_start[ch]; e < A.in_start[ch + 1]; e++) {
+            int64_t p = A.in_pair[e];
+            const double2* pr = part_r + (int64_t)p * ntile * NOUT * 2;
+            const float4* pb = part_b + (int64_t)p * ntile * NOUT;
+            int js[3], ts[3], nj = 0;
+            js[nj] = tid + HO; ts[nj++] = tile;
+            if (tid < HO && tile > 0) { js[nj] = TR + HO + tid; ts[nj++] = tile - 1; }
+            if (tid >= TR - HO && tile + 1 < ntile) { js[nj] = tid - TR + HO; ts[nj++] = tile + 1; }
+            for (int q = 0; q < nj; q++) {
+                int64_t i = (int64_t)ts[q] * NOUT + js[q];
+                double2 a = pr[2 * i], c = pr[2 * i + 1];
+                y0.x -= a.x; y0.y -= a.y; y1.x -= c.x; y1.y -= c.y;
+                if (need_b) {
+                    float4 w = pb[i];
+                    bv.x -= w.x; bv.y -= w.y; bv.z -= w.z; bv.w -= w.w;
+                }
+            }
+        }
+        r_out[o] = y0;
+        r_out[o + 1] = y1;
+        nr = y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y;
+        nb = (double)bv.x * bv.x + (double)bv.y * bv.y + (double)bv.z * bv.z + (double)bv.w * bv.w;
+    }
+    int64_t slot = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    block_reduce_store(make_double2(0, 0), nr, nullptr, pn_r, slot);
+    if (need_b) block_reduce_store(make_double2(0, 0), nb, nullptr, pn_b, slot);
+}
+
+size_t residual_own_df_smem() { return (size_t)NSTD * 2 * TR * ROWF * sizeof(float); }
+
+void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
+                            const float4* v, const float2* psi32, const float* Wh, const float* Wl, double2* r,
+                            float2* b, double2* part_r, float4* part_b, const int* need_b, double* pn_r,
+                            double* pn_b, int* err)
+{
+    dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
+    k_residual_own_df<<<grid, 2 * TR, residual_own_df_smem(), st>>>(A, S, Ht, u, v, psi32, Wh, Wl, r, b, part_r,
+                                                                    part_b, need_b, err);
+    k_residual_gather_df<<<grid, TR, 0, st>>>(A, r, b, part_r, part_b, need_b, pn_r, pn_b);
+}
+
+size_t apply_own32_smem() { return (size_t)NST * TR * ROWF * sizeof(float); }
+int apply_own_tile() { return TR; }
+int apply_own_nout() { return NOUT; }
+bool apply_own_supported(const OpView& A) { return A.bd == BDO; }
+
+// once per process and device before the first launch (and before any stream capture)
+cudaError_t apply_own32_prepare()
+{
+    cudaError_t e =
+        cudaFuncSetAttribute(k_apply_own32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_own32_smem());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_residual_own_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)residual_own_df_smem());
+}
+
+void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const float* H, int sign, const void* x,
+                        const float* W, void* y, float4* part, const void* bsub, const void* dv, double2* pdot,
+                        double* pnrm, const KState* skip, int* err)
+{
+    dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
+    k_apply_own32<<<grid, 2 * TR, apply_own32_smem(), st>>>(A, S, H, sign, (const float2*)x, W, (float2*)y, part,
+                                                            skip, err);
+    k_apply_gather32<<<grid, TR, 0, st>>>(A, sign, (float2*)y, part, (const float2*)bsub, (const float2*)dv, pdot,
+                                          pnrm, skip);
+}
+
+}  // namespace dg

@@ -48,7 +48,7 @@ struct dirac_op {
     double* K = nullptr;         // combined radial bands K_l(k', k)(t)
     double* W = nullptr;         // coupling values, FP64 (precision 0 and 1)
     // precision 2: double-float operator data (hi/lo float pairs)
-    float2 *Gdf = nullptr, *Kdf = nullptr, *Sdf = nullptr, *Htdf = nullptr;
+    float2 *Gdf = nullptr, *Kdf = nullptr, *KTdf = nullptr, *Sdf = nullptr, *Htdf = nullptr;
     float *Wh = nullptr, *Wl = nullptr;   // coupling hi words (also the FP32 values) and lo words
     float4* cab_df = nullptr;
     float4* xsplit = nullptr;    // split input vector; u = psi + x in the fused residual
@@ -58,8 +58,19 @@ struct dirac_op {
     double2* part_d = nullptr;
     double* part_n = nullptr;
     double* part_n2 = nullptr;
+    float4* part_own = nullptr;  // transposed partial products of the complex64 owner/gather apply
+    double2* part_rdf = nullptr; // ... of the double-float refinement residual (2 per row)
+    float4* part_bdf = nullptr;  // ... of b = A_- psi on a step's first refinement pass
+    float2* psi32 = nullptr;     // psi in FP32 and b = A_- psi (tolerance scale) of the residual pass
+    float2* b32 = nullptr;
+    int* need_b = nullptr;       // device flag: the next residual pass also forms ||b||^2
+    int* dev_err = nullptr;      // set by kernels whose bounded waits ran out
     double2* part_d2 = nullptr;
     double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
+    double* bvec = nullptr;      // bound eigenvectors per kappa slot, [vector][2 n1] (built on first use)
+    int* bstart = nullptr;       // first vector of each kappa slot (2 kappa_max + 1)
+    double* part_pb = nullptr;   // per-channel bound populations
+    int nbound = 0;
     int ground_ch = -1;
     // kernel-phase timers (CUDA events on the op's stream) and the launch counter
     bool profiling = false;
@@ -88,9 +99,11 @@ void finish(dirac_op* op, KState* ks, int what, int np, const double2* pd, const
 void vcopy(dirac_op* op, const Krylov& K, const void* a, void* b);
 void vzero(dirac_op* op, const Krylov& K, void* a);
 dirac_status read_state(dirac_op* op, const Krylov& K, KState& hs);
+dirac_status check_dev_err(dirac_op* op, const char* what);
 dirac_status bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter, bool mid_check);
 void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start = false);
 void set_error(const std::string& msg);
 void graph_free(dirac_op* op);
+dirac_status bound_population(dirac_op* op, const double2* psi, double* out);
 
 }  // namespace dg

@@ -519,7 +519,7 @@ template struct BandLU<cd>;
 template struct BandLU<double>;
 
 // scalar index i = 2 slot + type; entry of a Band as a scalar matrix
-static double band_entry(const Band& M, int i, int j)
+double band_entry(const Band& M, int i, int j)
 {
     int r = i / 2, t = i % 2, rr = j / 2, u = j % 2;
     int d = rr - r + M.half;

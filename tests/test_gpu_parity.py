@@ -96,6 +96,24 @@ def test_step_matches_oracle(case):
     assert np.all(got[~case.orc.active_mask()] == 0)
 
 
+def test_bound_population_matches_oracle(case):
+    # bound-state population (cuSOLVER eigenvectors + projection kernel) against the oracle's
+    # Jacobi eigenvectors, on a random state and on the ground state.  The projector on the bound
+    # subspace computed by two eigensolvers differs by ~eps ||H0|| / gap, with ||H0|| ~ 2 c^2 (the
+    # negative-energy branch) and the gap between the highest bound and the lowest box state
+    # ~1e-3: a few 1e-11 here; the bar is the stated observable tolerance 1e-9
+    for seed in (7, 8):
+        x = case.random(seed)
+        got = case.op.observables(case.to_dev(x), bound=True)
+        ref = case.orc.observables(x)
+        for k in ("norm", "energy", "p_ground"):
+            assert abs(got[k] - ref[k]) <= 1e-11 * max(1.0, abs(ref[k])), (k, got[k], ref[k])
+        assert abs(got["p_bound"] - ref["p_bound"]) <= 1e-9, (got["p_bound"], ref["p_bound"])
+    psi0, _ = case.orc.ground_state()
+    got = case.op.observables(case.to_dev(psi0), bound=True)
+    assert abs(got["p_bound"] - 1) <= 1e-11
+
+
 def test_small_full_run_matches_oracle(oracle_mod):
     # the 200-step small workload from the 1s1/2 state, tol 1e-12; oracle at 1e-14
     cfg = W.SMALL
@@ -107,9 +125,9 @@ def test_small_full_run_matches_oracle(oracle_mod):
     ref, _ = c.orc.run(psi0, cfg["steps"], 0.0, tol=1e-14)
     got = c.from_dev(psid)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
-    o_gpu = c.op.observables(psid)
+    o_gpu = c.op.observables(psid, bound=True)
     o_ref = c.orc.observables(ref)
-    for k in ("norm", "energy", "p_ground"):
+    for k in ("norm", "energy", "p_ground", "p_bound"):
         assert abs(o_gpu[k] - o_ref[k]) <= 1e-9 * max(1.0, abs(o_ref[k])), k
     assert nh == 2 and np.all(res <= cfg["tol"])
 

@@ -123,3 +123,28 @@ def test_initial_state_observables(oracle_mod):
     assert abs(obs["energy"] - E) < 1e-12
     assert abs(obs["p_ground"] - 1) < 1e-12
     assert abs(obs["p_bound"] - 1) < 1e-12
+
+
+def test_bound_population_of_eigen_combination(oracle_mod):
+    # psi = sum over channels of sum_e c_e v_e with S-orthonormal eigenvectors v_e of H0_kappa:
+    # the norm is sum |c_e|^2 and the bound population sum over -c^2 < E_e < 0 of |c_e|^2
+    # (Sec. 4.3), whatever the coefficients; a missing S, a wrong energy window or a channel left
+    # out of the sum breaks one of the two
+    o = oracle_mod.Oracle(**W.oracle_params(W.TINY))
+    c2 = o.params.c ** 2
+    rng = np.random.default_rng(3)
+    psi = np.zeros(o.n, np.complex128)
+    exp_b = exp_n = 0.0
+    nbound = 0
+    for ch, kappa in enumerate(o.kappa):
+        E, V = o.eigen(int(kappa))
+        coef = 0.1 * (rng.normal(size=len(E)) + 1j * rng.normal(size=len(E)))
+        psi[ch * o.nb:(ch + 1) * o.nb] = coef @ V
+        bound = (E > -c2) & (E < 0)
+        nbound += int(bound.sum())
+        exp_b += float(np.sum(np.abs(coef[bound]) ** 2))
+        exp_n += float(np.sum(np.abs(coef) ** 2))
+    assert 0 < nbound < o.n // 2
+    obs = o.observables(psi)
+    assert abs(obs["norm"] - exp_n) <= 1e-11 * exp_n
+    assert abs(obs["p_bound"] - exp_b) <= 1e-11 * exp_n
