@@ -40,6 +40,7 @@ typedef enum {
 
 typedef struct dirac_basis dirac_basis; /* host-side basis and operator data                  */
 typedef struct dirac_op dirac_op;       /* device operator, factors, workspaces               */
+typedef struct dirac_guess dirac_guess; /* learned initial-guess network and its training state */
 
 /* Radial and angular discretisation (Sec. 2.2).  n_splines = N B-splines kept for every kappa
  * (B_2 .. B_{N+1}); order = B-spline order k; grid 0 = linear breakpoints on [0, R]; grid 1 =
@@ -67,7 +68,8 @@ typedef struct {
  * BiCGSTAB inside FP64 iterative refinement, 2 = as 1 with the double-precision-accurate parts
  * (coupling assembly, A_- psi, refinement residuals) in double-float arithmetic (FP32 hi/lo pairs,
  * error-free transforms; about 2^-44 relative per operation); tol_inner: inner relative
- * tolerance (precision >= 1); max_outer: refinement cap (precision >= 1); guess: 0 = psi_n, 1 = quadratic extrapolation
+ * tolerance (precision >= 1); max_outer: refinement cap (precision >= 1); guess: 0 = psi_n, 1 = quadratic extrapolation,
+ * 2 = learned (dirac_op_set_guess; falls back to 1 without a network or history)
  * 3 psi_n - 3 psi_{n-1} + psi_{n-2}; time_eval: 0 = H at t + dt/2 (midpoint rule of Sec. 2.4),
  * 1 = H at t + dt (Eq. solPsi as printed); precond: 0 = none, 1 = LU of M = S + i dt/2 H0
  * (Eq. matrixM). */
@@ -139,6 +141,33 @@ dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist
 dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
                        double t_start, int* iters_out, double* resid_out);
 
+/* Batched solve (the multi-instance form of the step, Sec. 2.4 applied to many pulse parameter
+ * sets and radial sizes): advance n_inst independent instances by n_steps each.  ops[i] is an
+ * instance's operator (its own basis, pulse, radial size and, for overlap, its own stream given at
+ * setup; all on the current device, no op twice), psi_dev[i] / hist_dev[i] its state (complex128[n_i])
+ * and history (complex128[2 n_i]) on the device, n_hist[i] (in/out, nullable = all 0) the valid
+ * history entries, t_start[i] its start time.  Each instance runs its captured step driver
+ * (dirac_run) on its own stream, so the instances' kernels overlap on the GPU; window > 0 keeps at
+ * most `window` instances in flight (0: all).  iters_out / resid_out (host, nullable) are
+ * [n_inst][n_steps].  Results equal per-instance dirac_run calls bit for bit.  Synchronises every
+ * instance's stream.  Returns the first failing instance's status (every instance is completed and
+ * its outputs written first); DIRAC_E_ARG on bad arguments before anything runs. */
+dirac_status dirac_solve_batch(dirac_op* const* ops, int n_inst, void* const* psi_dev, void* const* hist_dev,
+                               int* n_hist, int n_steps, const double* t_start, int window, int* iters_out,
+                               double* resid_out);
+
+/* Schedule autotuner of dirac_solve_batch: for each candidate window cand[0..ncand) and each
+ * schedule of the complex64 preconditioner (v = 0: one lane per channel, v = 1: one warp per
+ * channel) it times one step of all instances (host clock around launch and completion) from the
+ * current states, restoring the states and histories afterwards (it allocates 3 n_i complex128
+ * scratch per instance).  The fastest window goes to *best_window and every op keeps the fastest
+ * preconditioner schedule (results are identical up to the solver tolerance across schedules; the
+ * captured drivers are re-captured).  ms_out (host, nullable, 2 ncand) receives each time at
+ * [v ncand + c].  Same argument rules as dirac_solve_batch. */
+dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void* const* psi_dev, void* const* hist_dev,
+                              const int* n_hist, const double* t_start, const int* cand, int ncand,
+                              int* best_window, double* ms_out);
+
 /* Observables of a state (Sec. 4.3): out[0] = psi^H S psi, out[1] = psi^H H0 psi,
  * out[2] = |v_1s^T S psi_{kappa=-1, mu=+1/2}|^2 (ground-state population),
  * out[3] = sum over channels (kappa, mu) and bound states b of |v_b^T S_kappa psi_{kappa mu}|^2, the
@@ -186,6 +215,51 @@ dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_
  * other allocating routine.  The op's device must be current. */
 #define DIRAC_STATIC_MAX_PARTIALS 65536
 dirac_status dirac_observables_static(dirac_op* op, const void* psi_dev, double* out, int n_out);
+
+/* ---- Learned initial guess (no counterpart in the paper: it only changes where BiCGSTAB starts;
+ * the solver's residual test still decides convergence, so the converged step is unchanged) ----
+ * Per position p = (channel, radial slot): D_0..D_3 = backward differences of psi_n .. psi_{n-3}
+ * at p (4 reals each: Re, Im of both DKB types), m_k their rms, s = m_3; features x[p] = [D_k / m_k
+ * (16), clip(log10(m_j / m_3), -30, 30) / 10 for j = 0..2 (3), field factors at t_{n+1} (6: A0 wt_c
+ * sin, cos of w_c (t - t0) for the three carriers of the sin^2 pulse, zero outside the pulse),
+ * kappa / 10, 2 mu / 20, zeros] (32 floats; zero entries where an m is 0); the network a1 = tanh(x W1 + b1), a2 = tanh(a1 W2 + b2),
+ * a3 = tanh(a2 W3 + b3), out = a3 W4 + b4 (W1 32 x 256, W2, W3 256 x 256, W4 256 x 4, weights
+ * rounded to bfloat16 in every product, FP32 accumulation); guess = 3 psi_n - 3 psi_{n-1} + psi_{n-2}
+ * + s out.  Parameters are one float array in the order W1, b1, W2, b2, W3, b3, W4, b4 (row-major
+ * [in][out]); dirac_guess_param_count() gives its length.  Calls run on `stream` (NULL: the legacy
+ * default stream) unless they take an op, whose stream they use. */
+int64_t dirac_guess_param_count(void);
+/* max_batch: largest training batch (sizes the training workspace, 6 max_batch x 256 floats). */
+dirac_status dirac_guess_create(int max_batch, dirac_guess** out);
+void dirac_guess_free(dirac_guess* net);
+/* Copy parameters in (host, count = dirac_guess_param_count(); resets the optimiser) or out. */
+dirac_status dirac_guess_set_params(dirac_guess* net, const float* host, int64_t count);
+dirac_status dirac_guess_get_params(dirac_guess* net, float* host, int64_t count);
+/* Features of every position of the op's system: states[0..3] = psi_n, psi_{n-1}, psi_{n-2},
+ * psi_{n-3} (device complex128[n]); x_dev float[nch n1][32], s_dev float[nch n1] (device). */
+dirac_status dirac_guess_features(dirac_op* op, const void* const* states, double t_next, float* x_dev,
+                                  float* s_dev);
+/* Training targets (psi_{n+1} - x_ext) / s: states[0..2] = psi_n, psi_{n-1}, psi_{n-2}, psi_next =
+ * psi_{n+1}; t_dev float[nch n1][4]. */
+dirac_status dirac_guess_targets(dirac_op* op, const void* const* states, const void* psi_next, const float* s_dev,
+                                 float* t_dev);
+/* out_dev float[M][4] = net(x_dev[M][32]); tensor_cores != 0: bf16 tensor-core kernel, else the
+ * FP32 kernels of training (batches of max_batch). */
+dirac_status dirac_guess_forward(dirac_guess* net, const float* x_dev, int64_t M, float* out_dev, int tensor_cores,
+                                 void* stream);
+/* Mean squared error over B samples (0 < B <= max_batch) and, if grad_host != NULL, its gradient
+ * (host float[param_count], gradient with respect to the rounded weights); synchronises. */
+dirac_status dirac_guess_loss_grad(dirac_guess* net, const float* x_dev, const float* t_dev, int B, double* loss,
+                                   float* grad_host, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr) on the FP32 parameters from
+ * the batch's gradient; loss (nullable) receives the batch loss before the step (synchronises). */
+dirac_status dirac_guess_train_step(dirac_guess* net, const float* x_dev, const float* t_dev, int B, double lr,
+                                    double* loss, void* stream);
+/* Attach a network (not owned; NULL detaches) to an op: dirac_step with solver option guess = 2 then
+ * starts each step from the network's guess once three past states are in the history, which must
+ * then hold 3 n entries (psi_{n-1}, psi_{n-2}, psi_{n-3}; n_hist up to 3); before that, and in
+ * dirac_run / dirac_solve_batch, the extrapolated guess is used. */
+dirac_status dirac_op_set_guess(dirac_op* op, dirac_guess* net);
 
 const char* dirac_last_error(void);
 

@@ -64,6 +64,21 @@ SIGNATURES = {
     "dirac_profile": (C.c_int, [_VP, C.c_int]),
     "dirac_profile_read": (C.c_int, [_VP, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "dirac_observables_static": (C.c_int, [_VP, _VP, _DP, C.c_int]),
+    "dirac_solve_batch": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(_VP), C.POINTER(_VP), _IP, C.c_int, _DP,
+                                    C.c_int, _IP, _DP]),
+    "dirac_batch_tune": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(_VP), C.POINTER(_VP), _IP, _DP, _IP,
+                                   C.c_int, _IP, _DP]),
+    "dirac_guess_param_count": (C.c_int64, []),
+    "dirac_guess_create": (C.c_int, [C.c_int, C.POINTER(_VP)]),
+    "dirac_guess_free": (None, [_VP]),
+    "dirac_guess_set_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int64]),
+    "dirac_guess_get_params": (C.c_int, [_VP, C.POINTER(C.c_float), C.c_int64]),
+    "dirac_guess_features": (C.c_int, [_VP, C.POINTER(_VP), C.c_double, _VP, _VP]),
+    "dirac_guess_targets": (C.c_int, [_VP, C.POINTER(_VP), _VP, _VP, _VP]),
+    "dirac_guess_forward": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int, _VP]),
+    "dirac_guess_loss_grad": (C.c_int, [_VP, _VP, _VP, C.c_int, _DP, C.POINTER(C.c_float), _VP]),
+    "dirac_guess_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_double, _DP, _VP]),
+    "dirac_op_set_guess": (C.c_int, [_VP, _VP]),
     "dirac_last_error": (C.c_char_p, []),
 }
 
@@ -95,6 +110,14 @@ def _dp(a):
 
 def _ip(a):
     return a.ctypes.data_as(_IP)
+
+
+def _fptr(t):
+    """Device pointer of a contiguous float32 CUDA tensor."""
+    import torch
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.float32):
+        raise ValueError("expected a contiguous float32 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
 
 
 def _ptr(t):
@@ -201,6 +224,10 @@ class Operator:
         self._h = h
         self.n = basis.n
 
+    @property
+    def precision(self):
+        return self.opts.precision
+
     def device_bytes(self):
         return lib().dirac_op_device_bytes(self._h)
 
@@ -269,3 +296,109 @@ class Operator:
         if h is not None and _lib is not None:
             _lib.dirac_op_free(h)
             self._h = None
+
+
+def _batch_args(ops, psis, hists, n_hist, t_start):
+    n = len(ops)
+    if not (len(psis) == len(hists) == n):
+        raise ValueError("ops, states and histories differ in number")
+    oa = (_VP * n)(*[o._h for o in ops])
+    pa = (_VP * n)(*[_ptr(p) for p in psis])
+    ha = (_VP * n)(*[_ptr(h) for h in hists])
+    nh = (C.c_int * n)(*([0] * n if n_hist is None else [int(v) for v in n_hist]))
+    ts = (C.c_double * n)(*[float(t) for t in (t_start if np.ndim(t_start) else [t_start] * n)])
+    return n, oa, pa, ha, nh, ts
+
+
+def solve_batch(ops, psis, hists, n_steps, t_start, n_hist=None, window=0):
+    """dirac_solve_batch: advance every instance n_steps; returns (iters [n, n_steps],
+    resid [n, n_steps], n_hist list)."""
+    n, oa, pa, ha, nh, ts = _batch_args(ops, psis, hists, n_hist, t_start)
+    it = np.zeros((n, max(n_steps, 1)), np.int32)
+    res = np.zeros((n, max(n_steps, 1)))
+    st = lib().dirac_solve_batch(oa, n, pa, ha, nh, int(n_steps), ts, int(window), _ip(it), _dp(res))
+    _check(st, "dirac_solve_batch")
+    return it[:, :n_steps], res[:, :n_steps], list(nh)
+
+
+def batch_tune(ops, psis, hists, t_start, candidates, n_hist=None):
+    """dirac_batch_tune: best window over the candidates (the ops keep the best preconditioner
+    schedule); returns (best_window, ms [2, len(candidates)])."""
+    n, oa, pa, ha, nh, ts = _batch_args(ops, psis, hists, n_hist, t_start)
+    cand = (C.c_int * len(candidates))(*[int(c) for c in candidates])
+    best = C.c_int(0)
+    ms = np.zeros(2 * len(candidates))
+    st = lib().dirac_batch_tune(oa, n, pa, ha, nh, ts, cand, len(candidates), C.byref(best), _dp(ms))
+    _check(st, "dirac_batch_tune")
+    return best.value, ms.reshape(2, len(candidates))
+
+
+class GuessNet:
+    """dirac_guess: the learned initial-guess network (parameters as one float32 array in the order
+    W1, b1, W2, b2, W3, b3, W4, b4)."""
+
+    def __init__(self, max_batch, params=None):
+        h = _VP()
+        _check(lib().dirac_guess_create(int(max_batch), C.byref(h)), "dirac_guess_create")
+        self._h = h
+        self.max_batch = int(max_batch)
+        self.nparams = int(lib().dirac_guess_param_count())
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, flat):
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(lib().dirac_guess_set_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size),
+               "dirac_guess_set_params")
+
+    def get_params(self):
+        a = np.zeros(self.nparams, np.float32)
+        _check(lib().dirac_guess_get_params(self._h, a.ctypes.data_as(C.POINTER(C.c_float)), a.size),
+               "dirac_guess_get_params")
+        return a
+
+    def forward(self, x, out, tensor_cores=True, stream=None):
+        _check(lib().dirac_guess_forward(self._h, _fptr(x), x.shape[0], _fptr(out), int(bool(tensor_cores)),
+                                         _VP(_stream_ptr(stream))), "dirac_guess_forward")
+
+    def loss_grad(self, x, t, stream=None):
+        B = x.shape[0]
+        loss = C.c_double(0)
+        g = np.zeros(self.nparams, np.float32)
+        _check(lib().dirac_guess_loss_grad(self._h, _fptr(x), _fptr(t), B, C.byref(loss),
+                                           g.ctypes.data_as(C.POINTER(C.c_float)), _VP(_stream_ptr(stream))),
+               "dirac_guess_loss_grad")
+        return loss.value, g
+
+    def train_step(self, x, t, lr, stream=None):
+        loss = C.c_double(0)
+        _check(lib().dirac_guess_train_step(self._h, _fptr(x), _fptr(t), x.shape[0], float(lr), C.byref(loss),
+                                            _VP(_stream_ptr(stream))), "dirac_guess_train_step")
+        return loss.value
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.dirac_guess_free(h)
+            self._h = None
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def guess_features(op, states, t_next, x, s):
+    arr = (_VP * 4)(*[_ptr(z) for z in states])
+    _check(lib().dirac_guess_features(op._h, arr, float(t_next), _fptr(x), _fptr(s)), "dirac_guess_features")
+
+
+def guess_targets(op, states, psi_next, s, t):
+    arr = (_VP * 3)(*[_ptr(z) for z in states[:3]])
+    _check(lib().dirac_guess_targets(op._h, arr, _ptr(psi_next), _fptr(s), _fptr(t)), "dirac_guess_targets")
+
+
+def set_guess(op, net):
+    op._net = net   # keep the network alive while attached
+    _check(lib().dirac_op_set_guess(op._h, net._h if net is not None else None), "dirac_op_set_guess")

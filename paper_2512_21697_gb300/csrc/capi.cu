@@ -231,7 +231,7 @@ void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks,
     PhaseScope ps(op, DIRAC_PHASE_PRECOND, 1);
     // complex64: one lane per channel (factor rows through shared memory); complex128: one warp per
     // channel, which keeps every SM sub-partition's FP64 pipe busy
-    if (K.prec == 1 && op->prec_warps)
+    if (K.prec == 1 && op->prec_warps && op->prec_lanes)
         launch_precond_lanes_t<float>(op->prec_warps, op->st, op->ov, K.Urow, K.L, K.Dinv, op->wks, op->wfirst,
                                       op->wcnt, mode, ks, r, v, io, z, pn);
     else if (K.prec == 0)
@@ -496,6 +496,7 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     int *dks, *dkap;
     TRY(upload(op, &dks, kslot));
     TRY(upload(op, &dkap, B.kap));
+    TRY(upload(op, &op->ch_two_mu, B.tmu));
 
     // adjacency: per channel, pairs where it is the lower channel (W x) or the upper one (W^T x)
     std::vector<std::vector<int>> adjp(B.nch), adjn(B.nch), adjt(B.nch);
@@ -814,10 +815,13 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
     if (!op || !psi_dev || n_steps < 0) { set_error("dirac_step: bad argument"); return DIRAC_E_ARG; }
     int64_t n = op->n;
     double2* psi = (double2*)psi_dev;
+    const dirac_solver_opts& o = op->opts;
+    const bool learned = o.guess == 2 && op->net;
+    const int hmax = learned ? 3 : 2;   // history entries kept (the network reads three past states)
     double2* h1 = hist_dev ? (double2*)hist_dev : nullptr;
     double2* h2 = hist_dev ? (double2*)hist_dev + n : nullptr;
-    int nh = (hist_dev && n_hist) ? std::max(0, std::min(2, *n_hist)) : 0;
-    const dirac_solver_opts& o = op->opts;
+    double2* h3 = (hist_dev && learned) ? (double2*)hist_dev + 2 * n : nullptr;
+    int nh = (hist_dev && n_hist) ? std::max(0, std::min(hmax, *n_hist)) : 0;
     int npv = op->nparts_vec;
     Krylov& K = op->k64;
     dirac_status result = DIRAC_OK;
@@ -836,7 +840,13 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
         {
             PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
             double2* x = (double2*)K.x;
-            k_extrapolate<<<npv, 256, 0, op->st>>>(n, o.guess == 1 ? nh : 0, psi, h1, h2, x);
+            if (learned && nh >= 3) {
+                double t_next = t_start + (double)(step + 1) * o.dt;
+                dirac_status ge = guess_into(op, psi, h1, h2, h3, t_next, x);
+                if (ge) return ge;
+            } else {
+                k_extrapolate<<<npv, 256, 0, op->st>>>(n, o.guess >= 1 ? std::min(nh, 2) : 0, psi, h1, h2, x);
+            }
         }
         KState hs{};
         int total_it = 0;
@@ -875,11 +885,13 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
         if (resid_out) resid_out[step] = res;
         // history shift and accept the iterate (also on failure, as documented)
         {
-            PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1 + (h1 ? 1 : 0) + (h2 && nh >= 1 ? 1 : 0));
+            PhaseScope ps(op, DIRAC_PHASE_VECTOR,
+                          1 + (h1 ? 1 : 0) + (h2 && nh >= 1 ? 1 : 0) + (h3 && nh >= 2 ? 1 : 0));
             if (h1) {
+                if (h3 && nh >= 2) k_copy64<<<npv, 256, 0, op->st>>>(n, h2, h3);
                 if (h2 && nh >= 1) k_copy64<<<npv, 256, 0, op->st>>>(n, h1, h2);
                 k_copy64<<<npv, 256, 0, op->st>>>(n, psi, h1);
-                nh = std::min(2, nh + 1);
+                nh = std::min(hmax, nh + 1);
             }
             k_copy64<<<npv, 256, 0, op->st>>>(n, (const double2*)K.x, psi);
         }

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -38,7 +39,13 @@ struct GraphDriver {
     double* res = nullptr;
     int cap = 0;                 // capacity of its/res
     cudaStream_t cap_stream = nullptr;
+    int gen = -1;                // op->config_gen the graph was captured with
+    StepCtl* h_ctl = nullptr;    // pinned host copies of the results (asynchronous read-back)
+    int* h_its = nullptr;
+    double* h_res = nullptr;
 };
+
+__global__ void k_set_ctl(StepCtl* c, StepCtl v) { *c = v; }
 
 __global__ void k_ctl_begin_step(StepCtl* c, double* t_eval, cudaGraphConditionalHandle h_solve)
 {
@@ -324,7 +331,7 @@ static dirac_status build_graph(dirac_op* op, GraphDriver* gd, double2* psi, dou
                 rhs_accurate(op, psi);
             }
             int npv = op->nparts_vec;
-            k_guess<<<npv, 256, 0, s1>>>(gd->ctl, o.guess == 1, op->n, psi, h1, h2, (double2*)K.x);
+            k_guess<<<npv, 256, 0, s1>>>(gd->ctl, o.guess >= 1, op->n, psi, h1, h2, (double2*)K.x);
             cudaGraph_t solve_body;
             e1 = add_cond(s1, h_solve, cudaGraphCondTypeWhile, &solve_body);
             if (e1) return e1;
@@ -357,8 +364,88 @@ void graph_free(dirac_op* op)
     cudaFree(gd->ctl);
     cudaFree(gd->its);
     cudaFree(gd->res);
+    cudaFreeHost(gd->h_ctl);
+    cudaFreeHost(gd->h_its);
+    cudaFreeHost(gd->h_res);
     delete gd;
     op->graph = nullptr;
+}
+
+
+// Enqueue n_steps of the captured driver on the op's stream (graph built or rebuilt as needed) and
+// the asynchronous read-back of its results into pinned host memory.  Nothing waits for the GPU.
+dirac_status run_launch(dirac_op* op, double2* psi, double2* h1, int n_hist, int n_steps, double t_start)
+{
+    if (!op->graph) op->graph = new GraphDriver();
+    GraphDriver* gd = op->graph;
+    double2* h2 = h1 + op->n;
+    bool rebuild = !gd->exec || gd->psi != psi || gd->hist != h1 || gd->gen != op->config_gen;
+    if (!gd->ctl) G_TRY(cudaMalloc(&gd->ctl, sizeof(StepCtl)));
+    if (!gd->h_ctl) G_TRY(cudaMallocHost(&gd->h_ctl, sizeof(StepCtl)));
+    if (gd->cap < n_steps) {
+        cudaFree(gd->its);
+        cudaFree(gd->res);
+        cudaFreeHost(gd->h_its);
+        cudaFreeHost(gd->h_res);
+        gd->its = nullptr;
+        gd->res = nullptr;
+        gd->h_its = nullptr;
+        gd->h_res = nullptr;
+        int cap = std::max(n_steps, 256);
+        G_TRY(cudaMalloc(&gd->its, sizeof(int) * cap));
+        G_TRY(cudaMalloc(&gd->res, sizeof(double) * cap));
+        G_TRY(cudaMallocHost(&gd->h_its, sizeof(int) * cap));
+        G_TRY(cudaMallocHost(&gd->h_res, sizeof(double) * cap));
+        gd->cap = cap;
+        rebuild = true;
+    }
+    if (rebuild) {
+        dirac_status st = build_graph(op, gd, psi, h1, h2);
+        if (st) return st;
+        gd->gen = op->config_gen;
+    }
+    const dirac_solver_opts& o = op->opts;
+    StepCtl c{};
+    c.t_start = t_start;
+    c.dt = o.dt;
+    c.t_off = o.time_eval ? o.dt : 0.5 * o.dt;
+    c.n_steps = n_steps;
+    c.hist_n = std::max(0, std::min(2, n_hist));
+    c.max_restarts = 8;
+    c.max_outer = o.max_outer;
+    k_set_ctl<<<1, 1, 0, op->st>>>(gd->ctl, c);
+    G_TRY(cudaGetLastError());
+    G_TRY(cudaGraphLaunch(gd->exec, op->st));
+    G_TRY(cudaMemcpyAsync(gd->h_ctl, gd->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, op->st));
+    G_TRY(cudaMemcpyAsync(gd->h_its, gd->its, sizeof(int) * n_steps, cudaMemcpyDeviceToHost, op->st));
+    G_TRY(cudaMemcpyAsync(gd->h_res, gd->res, sizeof(double) * n_steps, cudaMemcpyDeviceToHost, op->st));
+    op->launches += 2;   // the control upload and one graph launch (its kernels are not counted)
+    return DIRAC_OK;
+}
+
+// Wait for the op's stream and report the results of the last run_launch.
+dirac_status run_collect(dirac_op* op, int n_steps, int* n_hist, int* iters_out, double* resid_out, const char* who)
+{
+    GraphDriver* gd = op->graph;
+    cudaError_t e = cudaStreamSynchronize(op->st);
+    if (e != cudaSuccess) {
+        set_error(std::string(who) + ": " + cudaGetErrorString(e));
+        return DIRAC_E_CUDA;
+    }
+    const StepCtl& c = *gd->h_ctl;
+    for (int s = 0; s < c.step && s < n_steps; s++) {
+        if (iters_out) iters_out[s] = gd->h_its[s];
+        if (resid_out) resid_out[s] = gd->h_res[s];
+    }
+    if (n_hist) *n_hist = c.hist_n;
+    dirac_status de = check_dev_err(op, who);
+    if (de) return de;
+    if (c.status) {
+        set_error(std::string(who) + ": step " + std::to_string(c.step - 1) + " failed with status " +
+                  std::to_string(c.status));
+        return (dirac_status)c.status;
+    }
+    return DIRAC_OK;
 }
 
 }  // namespace dg
@@ -373,56 +460,142 @@ extern "C" dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, i
         return DIRAC_E_ARG;
     }
     if (n_steps == 0) return DIRAC_OK;
-    if (!op->graph) op->graph = new GraphDriver();
-    GraphDriver* gd = op->graph;
-    double2* psi = (double2*)psi_dev;
-    double2* h1 = (double2*)hist_dev;
-    double2* h2 = h1 + op->n;
-    bool rebuild = !gd->exec || gd->psi != psi || gd->hist != h1;
-    if (!gd->ctl) G_TRY(cudaMalloc(&gd->ctl, sizeof(StepCtl)));
-    if (gd->cap < n_steps) {
-        cudaFree(gd->its);
-        cudaFree(gd->res);
-        gd->its = nullptr;
-        gd->res = nullptr;
-        int cap = std::max(n_steps, 256);
-        G_TRY(cudaMalloc(&gd->its, sizeof(int) * cap));
-        G_TRY(cudaMalloc(&gd->res, sizeof(double) * cap));
-        gd->cap = cap;
-        rebuild = true;
+    dirac_status st = run_launch(op, (double2*)psi_dev, (double2*)hist_dev, n_hist ? *n_hist : 0, n_steps, t_start);
+    if (st) return st;
+    return run_collect(op, n_steps, n_hist, iters_out, resid_out, "dirac_run");
+}
+
+// Many independent instances (their own basis, pulse and radial size), each advanced by its own
+// captured driver on its own stream, so their kernels overlap on the GPU: the small, latency-bound
+// parts of one instance (preconditioner sweeps, reductions, control) fill the gaps of the others.
+// window > 0 keeps at most `window` instances in flight (instance i starts when i - window is done).
+extern "C" dirac_status dirac_solve_batch(dirac_op* const* ops, int n_inst, void* const* psi_dev,
+                                          void* const* hist_dev, int* n_hist, int n_steps, const double* t_start,
+                                          int window, int* iters_out, double* resid_out)
+{
+    if (!ops || !psi_dev || !hist_dev || !t_start || n_inst < 0 || n_steps < 0 || window < 0) {
+        set_error("dirac_solve_batch: bad argument");
+        return DIRAC_E_ARG;
     }
-    if (rebuild) {
-        dirac_status st = build_graph(op, gd, psi, h1, h2);
-        if (st) return st;
+    for (int i = 0; i < n_inst; i++) {
+        if (!ops[i] || !psi_dev[i] || !hist_dev[i]) {
+            set_error("dirac_solve_batch: instance " + std::to_string(i) + " has a NULL op, state or history");
+            return DIRAC_E_ARG;
+        }
+        if (ops[i]->device != ops[0]->device) {
+            set_error("dirac_solve_batch: instances on different devices");
+            return DIRAC_E_ARG;
+        }
+        for (int j = 0; j < i; j++)
+            if (ops[j] == ops[i]) {
+                set_error("dirac_solve_batch: the same op appears twice");
+                return DIRAC_E_ARG;
+            }
     }
-    const dirac_solver_opts& o = op->opts;
-    StepCtl c{};
-    c.t_start = t_start;
-    c.dt = o.dt;
-    c.t_off = o.time_eval ? o.dt : 0.5 * o.dt;
-    c.n_steps = n_steps;
-    c.hist_n = n_hist ? std::max(0, std::min(2, *n_hist)) : 0;
-    c.max_restarts = 8;
-    c.max_outer = o.max_outer;
-    G_TRY(cudaMemcpyAsync(gd->ctl, &c, sizeof(c), cudaMemcpyHostToDevice, op->st));
-    G_TRY(cudaGraphLaunch(gd->exec, op->st));
-    std::vector<int> its(n_steps);
-    std::vector<double> res(n_steps);
-    G_TRY(cudaMemcpyAsync(&c, gd->ctl, sizeof(c), cudaMemcpyDeviceToHost, op->st));
-    G_TRY(cudaMemcpyAsync(its.data(), gd->its, sizeof(int) * n_steps, cudaMemcpyDeviceToHost, op->st));
-    G_TRY(cudaMemcpyAsync(res.data(), gd->res, sizeof(double) * n_steps, cudaMemcpyDeviceToHost, op->st));
-    G_TRY(cudaStreamSynchronize(op->st));
-    op->launches += 1;   // one graph launch (its kernels are not counted individually)
-    for (int s = 0; s < c.step && s < n_steps; s++) {
-        if (iters_out) iters_out[s] = its[s];
-        if (resid_out) resid_out[s] = res[s];
+    if (n_inst == 0 || n_steps == 0) return DIRAC_OK;
+    std::vector<cudaEvent_t> ev(n_inst, nullptr);
+    dirac_status first = DIRAC_OK;
+    int launched = 0;
+    for (int i = 0; i < n_inst; i++) {
+        dirac_op* op = ops[i];
+        if (window > 0 && i >= window) {
+            if (cudaStreamWaitEvent(op->st, ev[i - window], 0) != cudaSuccess) {
+                set_error("dirac_solve_batch: cudaStreamWaitEvent failed");
+                first = DIRAC_E_CUDA;
+                break;
+            }
+        }
+        dirac_status st = run_launch(op, (double2*)psi_dev[i], (double2*)hist_dev[i], n_hist ? n_hist[i] : 0, n_steps,
+                                     t_start[i]);
+        if (st) { first = st; break; }
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventRecord(ev[i], op->st) != cudaSuccess) {
+            set_error("dirac_solve_batch: event record failed");
+            first = DIRAC_E_CUDA;
+            launched = i + 1;
+            break;
+        }
+        launched = i + 1;
     }
-    if (n_hist) *n_hist = c.hist_n;
-    dirac_status de = check_dev_err(op, "dirac_run");
-    if (de) return de;
-    if (c.status) {
-        set_error("dirac_run: step " + std::to_string(c.step - 1) + " failed with status " + std::to_string(c.status));
-        return (dirac_status)c.status;
+    std::string msg = first ? dirac_last_error() : std::string();
+    for (int i = 0; i < launched; i++) {
+        dirac_status st = run_collect(ops[i], n_steps, n_hist ? &n_hist[i] : nullptr,
+                                      iters_out ? iters_out + (size_t)i * n_steps : nullptr,
+                                      resid_out ? resid_out + (size_t)i * n_steps : nullptr, "dirac_solve_batch");
+        if (st && !first) {
+            first = st;
+            msg = "instance " + std::to_string(i) + ": " + dirac_last_error();
+        }
     }
-    return DIRAC_OK;
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    if (first) set_error(msg);
+    return first;
+}
+
+// Schedule autotuner of the batch: times one step of every instance for each candidate window
+// (instances in flight) and each inner-preconditioner schedule (one lane or one warp per channel),
+// on saved copies of the states, restores the states and histories, and leaves every op on the
+// fastest preconditioner schedule.  Returns the best window and, per tried configuration, the
+// milliseconds (ms_out[v * ncand + c], v = 0 lanes, 1 warps), when ms_out is given.
+extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void* const* psi_dev, void* const* hist_dev,
+                                         const int* n_hist, const double* t_start, const int* cand, int ncand,
+                                         int* best_window, double* ms_out)
+{
+    if (!ops || !psi_dev || !hist_dev || !t_start || !cand || ncand <= 0 || n_inst <= 0 || !best_window) {
+        set_error("dirac_batch_tune: bad argument");
+        return DIRAC_E_ARG;
+    }
+    for (int c = 0; c < ncand; c++)
+        if (cand[c] < 0) { set_error("dirac_batch_tune: negative window"); return DIRAC_E_ARG; }
+    std::vector<void*> save(n_inst, nullptr);
+    std::vector<int> nh(n_inst), nh0(n_inst);
+    dirac_status first = DIRAC_OK;
+    for (int i = 0; i < n_inst && !first; i++) {
+        if (!ops[i] || !psi_dev[i] || !hist_dev[i]) { set_error("dirac_batch_tune: NULL instance"); first = DIRAC_E_ARG; break; }
+        size_t b = sizeof(double2) * 3 * (size_t)ops[i]->n;
+        if (cudaMalloc(&save[i], b) != cudaSuccess) { set_error("dirac_batch_tune: cudaMalloc failed"); first = DIRAC_E_NOMEM; break; }
+        size_t bn = sizeof(double2) * (size_t)ops[i]->n;
+        cudaMemcpyAsync(save[i], psi_dev[i], bn, cudaMemcpyDeviceToDevice, ops[i]->st);
+        cudaMemcpyAsync((char*)save[i] + bn, hist_dev[i], 2 * bn, cudaMemcpyDeviceToDevice, ops[i]->st);
+        nh0[i] = n_hist ? n_hist[i] : 0;
+    }
+    auto restore = [&]() {
+        for (int i = 0; i < n_inst; i++) {
+            size_t bn = sizeof(double2) * (size_t)ops[i]->n;
+            cudaMemcpyAsync(psi_dev[i], save[i], bn, cudaMemcpyDeviceToDevice, ops[i]->st);
+            cudaMemcpyAsync(hist_dev[i], (char*)save[i] + bn, 2 * bn, cudaMemcpyDeviceToDevice, ops[i]->st);
+            nh[i] = nh0[i];
+        }
+    };
+    double best = 1e300;
+    int bw = cand[0], bv = 0;
+    for (int v = 0; v < 2 && !first; v++) {
+        for (int i = 0; i < n_inst; i++) {
+            ops[i]->prec_lanes = v == 0;
+            ops[i]->config_gen++;
+        }
+        restore();
+        first = dirac_solve_batch(ops, n_inst, psi_dev, hist_dev, nh.data(), 1, t_start, 0, nullptr, nullptr);   // warm-up
+        for (int c = 0; c < ncand && !first; c++) {
+            restore();
+            for (int i = 0; i < n_inst; i++) cudaStreamSynchronize(ops[i]->st);
+            auto t0 = std::chrono::steady_clock::now();
+            first = dirac_solve_batch(ops, n_inst, psi_dev, hist_dev, nh.data(), 1, t_start, cand[c], nullptr, nullptr);
+            double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            if (ms_out) ms_out[v * ncand + c] = ms;
+            if (!first && ms < best) { best = ms; bw = cand[c]; bv = v; }
+        }
+    }
+    if (n_inst > 0 && save[0]) restore();
+    for (int i = 0; i < n_inst; i++) {
+        if (ops[i]) {
+            ops[i]->prec_lanes = bv == 0;
+            ops[i]->config_gen++;
+            if (ops[i]->st) cudaStreamSynchronize(ops[i]->st);
+        }
+        if (save[i]) cudaFree(save[i]);
+    }
+    *best_window = bw;
+    return first;
 }

@@ -3,12 +3,13 @@
 //
 // A coupling block W_ab (pair a < b) is used twice: W_ab x_b in the rows of channel a and W_ab^T x_a
 // in the rows of channel b.  Two passes:
-//   k_apply_own32:    block = (channel a, tile of TR radial rows).  For each pair the channel owns,
-//                     the TR rows of W_ab are copied into shared memory by the bulk-copy engine
-//                     (cp.async.bulk, an NST-deep ring completed by mbarriers); threads 0..TR-1
-//                     accumulate W_ab x_b for their row, threads TR..2TR-1 form the transposed
-//                     product W_ab^T x_a restricted to those rows (TR + 2h output rows) and store it
-//                     in the pair's partial slot.  y_a = D x_a - sign sum W_ab x_b is written.
+//   k_apply_own32:    block = (channel a, tile of TR = 116 radial rows), 2 x 128 threads.  For each
+//                     pair the channel owns, the TR rows of W_ab are copied into shared memory by the
+//                     bulk-copy engine (cp.async.bulk, an NST-deep ring completed by mbarriers);
+//                     threads 0..TR-1 accumulate W_ab x_b for their row, threads 128..255 form the
+//                     transposed product W_ab^T x_a restricted to those rows (TR + 2h = 128 output
+//                     rows, one per thread) and store it in the pair's partial slot.
+//                     y_a = D x_a - sign sum W_ab x_b is written.
 //   k_apply_gather32: block = (channel b, tile).  y_b += sign sum of the partials of the pairs b is
 //                     the upper channel of (own tile, and the halo rows of the two neighbouring
 //                     tiles), in a fixed order, then the BiCGSTAB epilogues (y <- bsub - y, <dv, y>,
@@ -32,12 +33,14 @@ namespace dg {
 
 namespace {
 
-constexpr int TR = 128;          // radial rows per tile
+constexpr int NT = 128;          // threads per role: NT direct-product threads, NT transposed ones
+constexpr int TR = 116;          // radial rows per tile: TR + 2h = NT transposed output rows
 constexpr int NST = 3;           // bulk-copy ring depth
 constexpr int BDO = 13;          // block diagonals (order-7 splines)
 constexpr int HO = (BDO - 1) / 2;
 constexpr int ROWF = BDO * 4;    // floats per stored row of one pair
 constexpr int NOUT = TR + 2 * HO;
+static_assert(NOUT == NT, "one transposed output row per thread");
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bulk-copy wait limit
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -89,7 +92,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 
 }  // namespace
 
-__global__ void __launch_bounds__(2 * TR) k_apply_own32(OpView A, const float* __restrict__ S,
+__global__ void __launch_bounds__(2 * NT) k_apply_own32(OpView A, const float* __restrict__ S,
                                                         const float* __restrict__ H, int sign,
                                                         const float2* __restrict__ x, const float* __restrict__ W,
                                                         float2* __restrict__ y, float4* __restrict__ part,
@@ -157,9 +160,9 @@ __global__ void __launch_bounds__(2 * TR) k_apply_own32(OpView A, const float* _
         const int64_t p = A.own_pair[e];
         const float* Ws = wring + s * TR * ROWF;
         if (arrived) {
-            if (tid < TR) {
+            if (tid < NT) {
                 // direct: row r of W_ab against x_b
-                if (r < n1) {
+                if (tid < TR && r < n1) {
                     const float2* xb = x + (int64_t)A.own_nbr[e] * 2 * n1;
 #pragma unroll
                     for (int d = 0; d < BDO; d++) {
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(2 * TR) k_apply_own32(OpView A, const float* _
             } else {
                 // transposed: output rows rb = r0 - h + j of channel b from the tile's rows of W_ab
                 float4* pp = part + ((int64_t)p * ntile + tile) * NOUT;
-                for (int j = tid - TR; j < NOUT; j += TR) {
+                for (int j = tid - NT; j < NOUT; j += NT) {
                     float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
 #pragma unroll
                     for (int d = 0; d < BDO; d++) {
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(2 * TR) k_apply_own32(OpView A, const float* _
     }
 }
 
-__global__ void __launch_bounds__(TR) k_apply_gather32(OpView A, int sign, float2* __restrict__ y,
+__global__ void __launch_bounds__(NT) k_apply_gather32(OpView A, int sign, float2* __restrict__ y,
                                                        const float4* __restrict__ part,
                                                        const float2* __restrict__ bsub,
                                                        const float2* __restrict__ dv, double2* part_dot,
@@ -229,7 +232,7 @@ __global__ void __launch_bounds__(TR) k_apply_gather32(OpView A, int sign, float
     const int n1 = A.n1, ntile = gridDim.y;
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR, tid = threadIdx.x;
     const int r = r0 + tid;
-    const bool act = r < n1;
+    const bool act = tid < TR && r < n1;
     float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
     if (act) {
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(TR) k_apply_gather32(OpView A, int sign, float
                 float4 u = pp[(int64_t)(tile - 1) * NOUT + TR + HO + tid];
                 v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
             }
-            if (tid >= TR - HO && tile + 1 < ntile) {
+            if (tid >= TR - HO && tile + 1 < ntile) {   // tid < TR here
                 float4 u = pp[(int64_t)(tile + 1) * NOUT + tid - TR + HO];
                 v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
             }
@@ -282,10 +285,11 @@ __global__ void __launch_bounds__(TR) k_apply_gather32(OpView A, int sign, float
 // transposed products to part_r (double, 2 per row) and part_b.
 // ---------------------------------------------------------------------------------------------
 namespace {
-constexpr int NSTD = 2;          // ring depth of the double-float pass (hi + lo words per stage)
+constexpr int NSTD = 2;          // ring depth of the double-float pass
+constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8;   // floats: hi and lo words, u_b row window
 }
 
-__global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const float2* __restrict__ S,
+__global__ void __launch_bounds__(2 * NT) k_residual_own_df(OpView A, const float2* __restrict__ S,
                                                             const float2* __restrict__ Ht,
                                                             const float4* __restrict__ u,
                                                             const float4* __restrict__ v,
@@ -295,7 +299,8 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
                                                             double2* __restrict__ part_r, float4* __restrict__ part_b,
                                                             const int* need_b_flag, int* err)
 {
-    extern __shared__ __align__(128) float wring[];   // [NSTD][2][TR * ROWF]: hi words, lo words
+    // ring stage: hi words, lo words of the TR coupling rows, then u_b rows r0 - h .. r0 + TR + h
+    extern __shared__ __align__(128) float wring[];
     __shared__ float4 us[2 * TR];                    // u_a rows: (type 0, type 1) split complex
     __shared__ float4 ps[TR];                        // psi_a rows in FP32: (p0.re, p0.im, p1.re, p1.im)
     __shared__ uint64_t bar[NSTD];
@@ -306,19 +311,27 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
     const uint32_t bytes = (uint32_t)rows * ROWF * 4;
     const int own0 = A.own_start[ch], nown = A.own_start[ch + 1] - own0;
     const int tid = threadIdx.x;
-    const int stage_f = 2 * TR * ROWF;
+    const int stage_f = STAGE_DF;
+    // u_b window: rows [lo, hi) land at window index lo - (r0 - h)
+    const int lo = max(0, r0 - HO), hi = min(n1, r0 + TR + HO);
+    const uint32_t ubytes = (uint32_t)(hi - lo) * 32;
+    const int uoff = (lo - (r0 - HO)) * 8;   // floats
+    auto issue = [&](int k, int slot) {
+        int64_t p = A.own_pair[own0 + k];
+        int nb = A.own_nbr[own0 + k];
+        float* st = wring + slot * stage_f;
+        mbar_expect_tx(&bar[slot], 2 * bytes + ubytes);
+        bulk_load(st, Wh + (p * n1 + r0) * ROWF, bytes, &bar[slot]);
+        bulk_load(st + TR * ROWF, Wl + (p * n1 + r0) * ROWF, bytes, &bar[slot]);
+        bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nb * n1 + lo) * 2, ubytes, &bar[slot]);
+    };
     if (tid == 0) {
         for (int s = 0; s < NSTD; s++) mbar_init(&bar[s], 1);
         mbar_fence_init();
     }
     __syncthreads();
     if (tid == 0)
-        for (int k = 0; k < min(NSTD, nown); k++) {
-            int64_t p = A.own_pair[own0 + k];
-            mbar_expect_tx(&bar[k], 2 * bytes);
-            bulk_load(wring + k * stage_f, Wh + (p * n1 + r0) * ROWF, bytes, &bar[k]);
-            bulk_load(wring + k * stage_f + TR * ROWF, Wl + (p * n1 + r0) * ROWF, bytes, &bar[k]);
-        }
+        for (int k = 0; k < min(NSTD, nown); k++) issue(k, k);
     const float4* ua = u + (int64_t)ch * 2 * n1;
     const float4* va = v + (int64_t)ch * 2 * n1;
     const float2* pa = psi32 + (int64_t)ch * 2 * n1;
@@ -337,7 +350,7 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
         int ks = A.ch_kslot[ch];
         const float2* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
         const float2* Hk = Ht + ((int64_t)ks * n1 + r) * ROWF;
-#pragma unroll
+#pragma unroll 1   // keeps the double-float loop bodies within the instruction cache
         for (int d = 0; d < BDO; d++) {
             int rr = r + d - HO;
             if (rr < 0 || rr >= n1) continue;
@@ -373,17 +386,18 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
         const int64_t p = A.own_pair[e];
         const float* Hs = wring + s * stage_f;
         const float* Ls = Hs + TR * ROWF;
+        const float4* Us = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window][2]
         if (arrived) {
-            if (tid < TR) {
-                if (r < n1) {
+            if (tid < NT) {
+                if (tid < TR && r < n1) {
                     const int nb = A.own_nbr[e];
-                    const float4* ub = u + (int64_t)nb * 2 * n1;
                     const float2* pb = psi32 + (int64_t)nb * 2 * n1;
-#pragma unroll
+#pragma unroll 1   // keeps the double-float loop bodies within the instruction cache
                     for (int d = 0; d < BDO; d++) {
                         int rr = r + d - HO;
                         if (rr < 0 || rr >= n1) continue;
-                        float4 x0 = ub[2 * rr], x1 = ub[2 * rr + 1];
+                        // window index of row rr: rr - (r0 - h) = tid + d
+                        float4 x0 = Us[2 * (tid + d)], x1 = Us[2 * (tid + d) + 1];
                         float4 wh = *reinterpret_cast<const float4*>(Hs + tid * ROWF + d * 4);
                         float4 wl = *reinterpret_cast<const float4*>(Ls + tid * ROWF + d * 4);
                         // W[t][u] = (w.x, w.y ; w.z, w.w)
@@ -403,11 +417,11 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
             } else {
                 double2* pr = part_r + (((int64_t)p * ntile + tile) * NOUT) * 2;
                 float4* pbp = part_b + ((int64_t)p * ntile + tile) * NOUT;
-                for (int j = tid - TR; j < NOUT; j += TR) {
+                for (int j = tid - NT; j < NOUT; j += NT) {
                     DfAcc tt[4];
                     for (int q = 0; q < 4; q++) df_zero(tt[q]);
                     float tb[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
+#pragma unroll 1   // keeps the double-float loop bodies within the instruction cache
                     for (int d = 0; d < BDO; d++) {
                         int lr = j - d;
                         if (lr < 0 || lr >= rows) continue;
@@ -435,11 +449,8 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
         }
         if (!__syncthreads_and(arrived)) { kfail = k; break; }
         if (tid == 0 && k + NSTD < nown) {
-            int64_t pn = A.own_pair[own0 + k + NSTD];
             fence_proxy_async();
-            mbar_expect_tx(&bar[s], 2 * bytes);
-            bulk_load(wring + s * stage_f, Wh + (pn * n1 + r0) * ROWF, bytes, &bar[s]);
-            bulk_load(wring + s * stage_f + TR * ROWF, Wl + (pn * n1 + r0) * ROWF, bytes, &bar[s]);
+            issue(k + NSTD, s);
         }
     }
     if (kfail >= 0) {
@@ -460,7 +471,7 @@ __global__ void __launch_bounds__(2 * TR) k_residual_own_df(OpView A, const floa
 
 // r_b -= sum of the transposed partials (own tile and the neighbours' halo rows, fixed order);
 // partials of ||r||^2 and, on a step's first pass, of ||b||^2
-__global__ void __launch_bounds__(TR) k_residual_gather_df(OpView A, double2* __restrict__ r_out,
+__global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, double2* __restrict__ r_out,
                                                            const float2* __restrict__ b_out,
                                                            const double2* __restrict__ part_r,
                                                            const float4* __restrict__ part_b,
@@ -471,7 +482,7 @@ __global__ void __launch_bounds__(TR) k_residual_gather_df(OpView A, double2* __
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR, tid = threadIdx.x;
     const int r = r0 + tid;
     double nr = 0, nb = 0;
-    if (r < n1) {
+    if (tid < TR && r < n1) {
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
         double2 y0 = r_out[o], y1 = r_out[o + 1];
         float4 bv = need_b ? *reinterpret_cast<const float4*>(b_out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -503,7 +514,7 @@ __global__ void __launch_bounds__(TR) k_residual_gather_df(OpView A, double2* __
     if (need_b) block_reduce_store(make_double2(0, 0), nb, nullptr, pn_b, slot);
 }
 
-size_t residual_own_df_smem() { return (size_t)NSTD * 2 * TR * ROWF * sizeof(float); }
+size_t residual_own_df_smem() { return (size_t)NSTD * STAGE_DF * sizeof(float); }
 
 void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                             const float4* v, const float2* psi32, const float* Wh, const float* Wl, double2* r,
@@ -511,9 +522,9 @@ void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, c
                             double* pn_b, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_residual_own_df<<<grid, 2 * TR, residual_own_df_smem(), st>>>(A, S, Ht, u, v, psi32, Wh, Wl, r, b, part_r,
+    k_residual_own_df<<<grid, 2 * NT, residual_own_df_smem(), st>>>(A, S, Ht, u, v, psi32, Wh, Wl, r, b, part_r,
                                                                     part_b, need_b, err);
-    k_residual_gather_df<<<grid, TR, 0, st>>>(A, r, b, part_r, part_b, need_b, pn_r, pn_b);
+    k_residual_gather_df<<<grid, NT, 0, st>>>(A, r, b, part_r, part_b, need_b, pn_r, pn_b);
 }
 
 size_t apply_own32_smem() { return (size_t)NST * TR * ROWF * sizeof(float); }
@@ -536,9 +547,9 @@ void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const 
                         double* pnrm, const KState* skip, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_apply_own32<<<grid, 2 * TR, apply_own32_smem(), st>>>(A, S, H, sign, (const float2*)x, W, (float2*)y, part,
+    k_apply_own32<<<grid, 2 * NT, apply_own32_smem(), st>>>(A, S, H, sign, (const float2*)x, W, (float2*)y, part,
                                                             skip, err);
-    k_apply_gather32<<<grid, TR, 0, st>>>(A, sign, (float2*)y, part, (const float2*)bsub, (const float2*)dv, pdot,
+    k_apply_gather32<<<grid, NT, 0, st>>>(A, sign, (float2*)y, part, (const float2*)bsub, (const float2*)dv, pdot,
                                           pnrm, skip);
 }
 

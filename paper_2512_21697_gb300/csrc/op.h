@@ -37,6 +37,8 @@ struct dirac_op {
     int64_t n = 0, npairs = 0;
     int nparts_apply = 0, nparts_vec = 0, nparts_prec = 0, nparts_prec32 = 0;
     int prec_warps = 0;          // same-kappa channel groups (lane-per-channel preconditioner)
+    bool prec_lanes = true;      // complex64 preconditioner schedule: one lane (else one warp) per channel
+    int config_gen = 0;          // bumped when a launch choice changes (captured graphs are rebuilt)
     int *wks = nullptr, *wfirst = nullptr, *wcnt = nullptr;
     std::vector<void*> allocs;
     size_t bytes = 0;
@@ -64,6 +66,9 @@ struct dirac_op {
     float2* psi32 = nullptr;     // psi in FP32 and b = A_- psi (tolerance scale) of the residual pass
     float2* b32 = nullptr;
     int* need_b = nullptr;       // device flag: the next residual pass also forms ||b||^2
+    int* ch_two_mu = nullptr;    // [nch] 2 mu of each channel (learned-guess features)
+    dirac_guess* net = nullptr;  // learned initial guess (guess option 2), not owned
+    float *gx = nullptr, *gs = nullptr, *gout = nullptr;   // its features, scales and outputs
     int* dev_err = nullptr;      // set by kernels whose bounded waits ran out
     double2* part_d2 = nullptr;
     double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
@@ -105,5 +110,7 @@ void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start 
 void set_error(const std::string& msg);
 void graph_free(dirac_op* op);
 dirac_status bound_population(dirac_op* op, const double2* psi, double* out);
+dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, const double2* h2, const double2* h3,
+                        double t_next, double2* x);
 
 }  // namespace dg

@@ -59,18 +59,20 @@ def oracle_params(cfg):
     return {k: cfg[k] for k in keys}
 
 
-def batch_instances(n_inst=64, seed0=0, kappa_max=20, l_max=2):
+def batch_instances(n_inst=64, seed0=0, kappa_max=20, l_max=2, N_lo=400, N_hi=1000, R=300.0):
     """Laser/basis parameter sets for the batched workload: E0 log-uniform in [0.02, 0.2],
-    wavelength uniform in [400, 1600] nm, 2-6 cycles, 400-1000 radial splines, R = 300 a.u."""
+    wavelength uniform in [400, 1600] nm, 2-6 cycles, N_lo..N_hi radial splines (default
+    400-1000), box R (default 300 a.u.), linear-then-geometric grid with half the knot intervals
+    linear up to R/5."""
     out = []
     for i in range(n_inst):
         g = np.random.default_rng(seed0 + i)
         E0 = float(np.exp(g.uniform(np.log(0.02), np.log(0.2))))
         lam = float(g.uniform(400, 1600))
         ncyc = int(g.integers(2, 7))
-        N = int(g.integers(400, 1001))
+        N = int(g.integers(N_lo, N_hi + 1))
         m = N + 5 - 7
-        out.append(_base(R=300.0, N=N, grid=1, r_lin=60.0, n_lin=m // 2, kappa_max=kappa_max,
+        out.append(_base(R=float(R), N=N, grid=1, r_lin=R / 5.0, n_lin=m // 2, kappa_max=kappa_max,
                          two_mu_max=0, l_max=l_max, E0=E0, omega=omega_from_nm(lam),
                          n_cycles=float(ncyc), dt=0.005, steps=2000, tol=1e-10))
     return out
