@@ -113,6 +113,11 @@ void collect_phases(dirac_op* op)
 }
 
 // ---- launch helpers ------------------------------------------------------------------------
+int apply_parts(const dirac_op* op, const Krylov& K)
+{
+    return (K.prec == 1 && op->part_own) ? op->nparts_own : op->nparts_apply;
+}
+
 void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
                            const void* dv, double2* pdot, double* pnrm, const KState* skip)
 {
@@ -209,9 +214,9 @@ void residual_accurate(dirac_op* op, const void* psi)
         }
         {
             PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
-            k_bnorm_if<<<1, 1024, 0, op->st>>>(K.ks, op->need_b, op->nparts_apply, op->part_n2);
+            k_bnorm_if<<<1, 1024, 0, op->st>>>(K.ks, op->need_b, op->nparts_own, op->part_n2);
         }
-        finish(op, K.ks, 1, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
+        finish(op, K.ks, 1, op->nparts_own, nullptr, op->part_n, op->opts.max_iter);
         return;
     }
     {
@@ -275,7 +280,7 @@ dirac_status check_launch(const char* what)
 // nothing more than the final update (large systems, where a host round trip is negligible).
 dirac_status bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter, bool mid_check)
 {
-    int npa = op->nparts_apply, npp = K.prec == 1 ? op->nparts_prec32 : op->nparts_prec, npv = op->nparts_vec;
+    int npa = apply_parts(op, K), npp = K.prec == 1 ? op->nparts_prec32 : op->nparts_prec, npv = op->nparts_vec;
     // p = r + beta (p - omega v); ph = M^-1 p
     k_precond_launch(op, K, 1, K.ks, K.r, K.v, K.p, K.ph, nullptr);
     // v = A ph, <rh, v>
@@ -315,7 +320,7 @@ dirac_status bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter, boo
 void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start)
 {
     k_apply_launch(op, K, +1, K.x, K.r, K.b, nullptr, nullptr, op->part_n, nullptr);
-    finish(op, K.ks, rel_start ? 8 : 1, op->nparts_apply, nullptr, op->part_n, max_iter);
+    finish(op, K.ks, rel_start ? 8 : 1, apply_parts(op, K), nullptr, op->part_n, max_iter);
     vcopy(op, K, K.r, K.rh);
     vzero(op, K, K.p);
     vzero(op, K, K.v);
@@ -424,6 +429,37 @@ extern "C" dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* co
 }
 
 extern "C" int64_t dirac_op_device_bytes(const dirac_op* op) { return op ? (int64_t)op->bytes : -1; }
+
+// Schedule of the complex64 preconditioner, picked by timing: one lane per channel (the channels
+// of one kappa share the factor rows read through shared memory) or one warp per channel (more
+// parallelism along the band).  Which is faster depends on the channel count and radial size, so
+// the operator times one application of each on zeroed vectors (after a warm-up) and keeps the
+// faster; the choice does not change results beyond the inner solve's tolerance.
+static dirac_status tune_precond32(dirac_op* op)
+{
+    Krylov& I = op->k32;
+    if (!op->prec_warps) { op->prec_lanes = false; return DIRAC_OK; }
+    size_t bytes = sizeof(float2) * (size_t)op->n;
+    CUDA_TRY(cudaMemsetAsync(I.r, 0, bytes, op->st));
+    CUDA_TRY(cudaMemsetAsync(I.sh, 0, bytes, op->st));
+    cudaEvent_t e[3];
+    for (auto& ev : e) CUDA_TRY(cudaEventCreate(&ev));
+    float ms[2] = {0, 0};
+    for (int v = 0; v < 2; v++) {
+        op->prec_lanes = v == 0;
+        k_precond_launch(op, I, 0, nullptr, I.r, nullptr, nullptr, I.sh, nullptr);   // warm-up
+        CUDA_TRY(cudaEventRecord(e[0], op->st));
+        k_precond_launch(op, I, 0, nullptr, I.r, nullptr, nullptr, I.sh, nullptr);
+        CUDA_TRY(cudaEventRecord(e[1], op->st));
+        CUDA_TRY(cudaEventSynchronize(e[1]));
+        CUDA_TRY(cudaEventElapsedTime(&ms[v], e[0], e[1]));
+    }
+    for (auto& ev : e) cudaEventDestroy(ev);
+    op->prec_lanes = ms[0] <= ms[1];
+    op->prec_ms[0] = ms[0];
+    op->prec_ms[1] = ms[1];
+    return check_launch("dirac_operator_setup: preconditioner schedule");
+}
 
 static dirac_status alloc_krylov(dirac_op* op, Krylov& K, int prec, double tol)
 {
@@ -737,10 +773,11 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         }
     }
     op->nparts_apply = grid_for(n1, 128) * B.nch;
+    op->nparts_own = grid_for(n1, apply_own_tile()) * B.nch;
     op->nparts_vec = grid_for(op->n, 256);
     op->nparts_prec = grid_for(B.nch, 4);                     // ||s||^2 partials, warp-per-channel kernel
     op->nparts_prec32 = op->prec_warps ? op->prec_warps : grid_for(B.nch, 4);   // lane-per-channel kernel
-    int np = std::max({op->nparts_apply, op->nparts_vec, op->nparts_prec, op->nparts_prec32});
+    int np = std::max({op->nparts_apply, op->nparts_own, op->nparts_vec, op->nparts_prec, op->nparts_prec32});
     TRY(dev_alloc(op, &op->part_d, (size_t)np));
     TRY(dev_alloc(op, &op->part_d2, (size_t)np));
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
@@ -774,6 +811,10 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     pv.L = P.L; pv.T = P.T; pv.amp = P.amp; pv.t0 = pulse->t0; pv.dt = opts->dt;
     for (int c = 0; c < 3; c++) { pv.w[c] = P.w[c]; pv.wt[c] = P.wt[c]; }
     pv.M = dM;
+    if (mixed) {
+        dirac_status ts = tune_precond32(op);
+        if (ts) { dirac_op_free(op); return ts; }
+    }
     *out = op;
 #undef TRY
     return DIRAC_OK;

@@ -560,7 +560,10 @@ extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void*
         cudaMemcpyAsync((char*)save[i] + bn, hist_dev[i], 2 * bn, cudaMemcpyDeviceToDevice, ops[i]->st);
         nh0[i] = n_hist ? n_hist[i] : 0;
     }
+    int nsaved = 0;
+    for (int i = 0; i < n_inst; i++) nsaved += save[i] != nullptr;
     auto restore = [&]() {
+        if (nsaved != n_inst) return;   // a save failed: nothing ran, nothing to restore
         for (int i = 0; i < n_inst; i++) {
             size_t bn = sizeof(double2) * (size_t)ops[i]->n;
             cudaMemcpyAsync(psi_dev[i], save[i], bn, cudaMemcpyDeviceToDevice, ops[i]->st);
@@ -587,7 +590,7 @@ extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void*
             if (!first && ms < best) { best = ms; bw = cand[c]; bv = v; }
         }
     }
-    if (n_inst > 0 && save[0]) restore();
+    restore();
     for (int i = 0; i < n_inst; i++) {
         if (ops[i]) {
             ops[i]->prec_lanes = bv == 0;

@@ -3,13 +3,14 @@
 //
 // A coupling block W_ab (pair a < b) is used twice: W_ab x_b in the rows of channel a and W_ab^T x_a
 // in the rows of channel b.  Two passes:
-//   k_apply_own32:    block = (channel a, tile of TR = 116 radial rows), 2 x 128 threads.  For each
-//                     pair the channel owns, the TR rows of W_ab are copied into shared memory by the
-//                     bulk-copy engine (cp.async.bulk, an NST-deep ring completed by mbarriers);
-//                     threads 0..TR-1 accumulate W_ab x_b for their row, threads 128..255 form the
-//                     transposed product W_ab^T x_a restricted to those rows (TR + 2h = 128 output
-//                     rows, one per thread) and store it in the pair's partial slot.
-//                     y_a = D x_a - sign sum W_ab x_b is written.
+//   k_apply_own32:    block = (channel a, tile of TR = 116 radial rows), 288 threads.  For each
+//                     pair the channel owns, a producer warp copies the TR rows of W_ab and the
+//                     window of x_b the band needs into shared memory with the bulk-copy engine
+//                     (cp.async.bulk into an NST-deep ring: a "full" mbarrier per stage completes on
+//                     the bytes, an "empty" one when the consumers release it); warps 0..3
+//                     accumulate W_ab x_b for their row, warps 4..7 form the transposed product
+//                     W_ab^T x_a restricted to those rows (TR + 2h = 128 output rows, one per thread)
+//                     and store it in the pair's partial slot.  y_a = D x_a - sign sum W_ab x_b.
 //   k_apply_gather32: block = (channel b, tile).  y_b += sign sum of the partials of the pairs b is
 //                     the upper channel of (own tile, and the halo rows of the two neighbouring
 //                     tiles), in a fixed order, then the BiCGSTAB epilogues (y <- bsub - y, <dv, y>,
@@ -35,12 +36,13 @@ namespace {
 
 constexpr int NT = 128;          // threads per role: NT direct-product threads, NT transposed ones
 constexpr int TR = 116;          // radial rows per tile: TR + 2h = NT transposed output rows
-constexpr int NST = 3;           // bulk-copy ring depth
+constexpr int NST = 2;           // bulk-copy ring depth of the complex64 pass
 constexpr int BDO = 13;          // block diagonals (order-7 splines)
 constexpr int HO = (BDO - 1) / 2;
 constexpr int ROWF = BDO * 4;    // floats per stored row of one pair
 constexpr int NOUT = TR + 2 * HO;
 static_assert(NOUT == NT, "one transposed output row per thread");
+constexpr int STAGE32 = TR * ROWF + NOUT * 4;   // floats per complex64 ring stage: coupling rows, x_b row window
 constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bulk-copy wait limit
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -58,6 +60,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
@@ -92,33 +99,38 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
 
 }  // namespace
 
-__global__ void __launch_bounds__(2 * NT) k_apply_own32(OpView A, const float* __restrict__ S,
-                                                        const float* __restrict__ H, int sign,
-                                                        const float2* __restrict__ x, const float* __restrict__ W,
-                                                        float2* __restrict__ y, float4* __restrict__ part,
-                                                        const KState* skip, int* err)
+__global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const float* __restrict__ S,
+                                                             const float* __restrict__ H, int sign,
+                                                             const float2* __restrict__ x, const float* __restrict__ W,
+                                                             float2* __restrict__ y, float4* __restrict__ part,
+                                                             const KState* skip, int* err)
 {
     if (skip && skip->done) return;   // uniform over the grid: the solve already finished
-    extern __shared__ __align__(128) float wring[];   // [NST][TR * ROWF]
+    // ring stage: the TR coupling rows, then x_b rows r0 - h .. r0 + TR + h.  Warps 0..3: direct
+    // products, warps 4..7: transposed products, warp 8: producer of the bulk copies; a stage is
+    // refilled when the eight consumer warps have released it.
+    extern __shared__ __align__(128) float wring[];
     __shared__ float4 xs[TR];                        // x_a rows of the tile: (x0.re, x0.im, x1.re, x1.im)
-    __shared__ uint64_t bar[NST];
+    __shared__ uint64_t full[NST], empty[NST];
+    __shared__ int fail, issued;
     const int n1 = A.n1, ntile = gridDim.y;
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
     const int rows = min(TR, n1 - r0);
     const uint32_t bytes = (uint32_t)rows * ROWF * 4;
     const int own0 = A.own_start[ch], nown = A.own_start[ch + 1] - own0;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lo = max(0, r0 - HO), hi = min(n1, r0 + TR + HO);
+    const uint32_t xbytes = (uint32_t)(hi - lo) * 16;
+    const int xoff = (lo - (r0 - HO)) * 4;   // floats
     if (tid == 0) {
-        for (int s = 0; s < NST; s++) mbar_init(&bar[s], 1);
+        for (int q = 0; q < NST; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 2 * NT / 32);
+        }
+        fail = 0;
+        issued = 0;
         mbar_fence_init();
     }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < min(NST, nown); k++) {
-            int64_t p = A.own_pair[own0 + k];
-            mbar_expect_tx(&bar[k], bytes);
-            bulk_load(wring + k * TR * ROWF, W + (p * n1 + r0) * ROWF, bytes, &bar[k]);
-        }
     const float2* xa = x + (int64_t)ch * 2 * n1;
     if (tid < TR) {
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -130,8 +142,9 @@ __global__ void __launch_bounds__(2 * NT) k_apply_own32(OpView A, const float* _
     }
     // diagonal block (S + sign i tau H0) x_a for the direct threads' row
     const int r = r0 + tid;
+    const bool direct_row = tid < TR && r < n1;
     float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
-    if (tid < TR && r < n1) {
+    if (direct_row) {
         int ks = A.ch_kslot[ch];
         const float* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
         const float* Hk = H + ((int64_t)ks * n1 + r) * ROWF;
@@ -150,25 +163,37 @@ __global__ void __launch_bounds__(2 * NT) k_apply_own32(OpView A, const float* _
             y1.y += sv.z * xv.y + sv.w * xv.w + (h10 * xv.x + h11 * xv.z);
         }
     }
-    __syncthreads();   // xs ready
+    __syncthreads();   // barriers initialised, xs staged
     float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
-    int kfail = -1;   // block-uniform: first ring stage whose copy did not arrive in time
-    for (int k = 0; k < nown; k++) {
-        const int s = k % NST;
-        const bool arrived = mbar_wait(&bar[s], (uint32_t)((k / NST) & 1));
-        const int e = own0 + k;
-        const int64_t p = A.own_pair[e];
-        const float* Ws = wring + s * TR * ROWF;
-        if (arrived) {
+    if (warp == 2 * NT / 32) {
+        if (lane == 0) {
+            for (int k = 0; k < nown; k++) {
+                const int s = k % NST;
+                if (k >= NST && !mbar_wait(&empty[s], (uint32_t)((k / NST - 1) & 1))) { fail = 1; break; }
+                const int64_t p = A.own_pair[own0 + k];
+                const int nb = A.own_nbr[own0 + k];
+                float* st = wring + s * STAGE32;
+                fence_proxy_async();
+                mbar_expect_tx(&full[s], bytes + xbytes);
+                bulk_load(st, W + (p * n1 + r0) * ROWF, bytes, &full[s]);
+                bulk_load(st + TR * ROWF + xoff, x + ((int64_t)nb * n1 + lo) * 2, xbytes, &full[s]);
+                issued = k + 1;
+            }
+        }
+    } else {
+        for (int k = 0; k < nown; k++) {
+            const int s = k % NST;
+            if (!mbar_wait(&full[s], (uint32_t)((k / NST) & 1))) { fail = 1; break; }
+            const int64_t p = A.own_pair[own0 + k];
+            const float* Ws = wring + s * STAGE32;
+            const float4* Xs = reinterpret_cast<const float4*>(Ws + TR * ROWF);   // x_b row window
             if (tid < NT) {
-                // direct: row r of W_ab against x_b
-                if (tid < TR && r < n1) {
-                    const float2* xb = x + (int64_t)A.own_nbr[e] * 2 * n1;
+                if (direct_row) {
 #pragma unroll
                     for (int d = 0; d < BDO; d++) {
                         int rr = r + d - HO;
                         if (rr < 0 || rr >= n1) continue;
-                        float4 xv = *reinterpret_cast<const float4*>(xb + 2 * rr);
+                        float4 xv = Xs[tid + d];   // row rr = r0 - h + (tid + d)
                         float4 w = *reinterpret_cast<const float4*>(Ws + tid * ROWF + d * 4);
                         d0.x = fmaf(w.x, xv.x, d0.x); d0.x = fmaf(w.y, xv.z, d0.x);
                         d0.y = fmaf(w.x, xv.y, d0.y); d0.y = fmaf(w.y, xv.w, d0.y);
@@ -177,43 +202,39 @@ __global__ void __launch_bounds__(2 * NT) k_apply_own32(OpView A, const float* _
                     }
                 }
             } else {
-                // transposed: output rows rb = r0 - h + j of channel b from the tile's rows of W_ab
+                // transposed: output row rb = r0 - h + j of channel b from the tile's rows of W_ab
                 float4* pp = part + ((int64_t)p * ntile + tile) * NOUT;
-                for (int j = tid - NT; j < NOUT; j += NT) {
-                    float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
+                const int j = tid - NT;
+                float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int d = 0; d < BDO; d++) {
-                        int lr = j - d;   // W row r0 + lr couples to column rb through diagonal d
-                        if (lr < 0 || lr >= rows) continue;
-                        float4 w = *reinterpret_cast<const float4*>(Ws + lr * ROWF + d * 4);
-                        float4 xv = xs[lr];
-                        // (W^T)[t][u] = W[u][t]
-                        t0.x = fmaf(w.x, xv.x, t0.x); t0.x = fmaf(w.z, xv.z, t0.x);
-                        t0.y = fmaf(w.x, xv.y, t0.y); t0.y = fmaf(w.z, xv.w, t0.y);
-                        t1.x = fmaf(w.y, xv.x, t1.x); t1.x = fmaf(w.w, xv.z, t1.x);
-                        t1.y = fmaf(w.y, xv.y, t1.y); t1.y = fmaf(w.w, xv.w, t1.y);
-                    }
-                    pp[j] = make_float4(t0.x, t0.y, t1.x, t1.y);
+                for (int d = 0; d < BDO; d++) {
+                    int lr = j - d;   // W row r0 + lr couples to column rb through diagonal d
+                    if (lr < 0 || lr >= rows) continue;
+                    float4 w = *reinterpret_cast<const float4*>(Ws + lr * ROWF + d * 4);
+                    float4 xv = xs[lr];
+                    // (W^T)[t][u] = W[u][t]
+                    t0.x = fmaf(w.x, xv.x, t0.x); t0.x = fmaf(w.z, xv.z, t0.x);
+                    t0.y = fmaf(w.x, xv.y, t0.y); t0.y = fmaf(w.z, xv.w, t0.y);
+                    t1.x = fmaf(w.y, xv.x, t1.x); t1.x = fmaf(w.w, xv.z, t1.x);
+                    t1.y = fmaf(w.y, xv.y, t1.y); t1.y = fmaf(w.w, xv.w, t1.y);
                 }
+                pp[j] = make_float4(t0.x, t0.y, t1.x, t1.y);
             }
-        }
-        // every thread is done with stage s (and agrees whether its copy arrived)
-        if (!__syncthreads_and(arrived)) { kfail = k; break; }
-        if (tid == 0 && k + NST < nown) {
-            int64_t pn = A.own_pair[own0 + k + NST];
-            fence_proxy_async();
-            mbar_expect_tx(&bar[s], bytes);
-            bulk_load(wring + s * TR * ROWF, W + (pn * n1 + r0) * ROWF, bytes, &bar[s]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
         }
     }
-    if (kfail >= 0) {
-        if (tid == 0) atomicExch(err, 1);
-        // copies issued for stages kfail .. kfail + NST - 1 may still be in flight: give each the
-        // same time limit before the block's shared memory is released
-        for (int k = kfail; k < min(nown, kfail + NST); k++) mbar_wait(&bar[k % NST], (uint32_t)((k / NST) & 1));
+    __syncthreads();
+    if (fail) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // copies still in flight target this block's shared memory: give the last ones issued
+            // the same time limit before the block exits
+            for (int k = max(0, issued - NST); k < issued; k++) mbar_wait(&full[k % NST], (uint32_t)((k / NST) & 1));
+        }
         return;
     }
-    if (tid < TR && r < n1) {
+    if (direct_row) {
         float sg = (float)sign;
         y0.x = fmaf(-sg, d0.x, y0.x); y0.y = fmaf(-sg, d0.y, y0.y);
         y1.x = fmaf(-sg, d1.x, y1.x); y1.y = fmaf(-sg, d1.y, y1.y);
@@ -282,56 +303,57 @@ __global__ void __launch_bounds__(NT) k_apply_gather32(OpView A, int sign, float
 // in double-float, from u = psi + x and v = psi - x split into (re hi, re lo, im hi, im lo), and,
 // when *need_b is set (the first pass of a step), b = A_- psi in FP32 products for the tolerance
 // scale ||b||.  Owner pass: r_a (diagonal + direct coupling) to r_out, b_a to b_out; partials of the
-// transposed products to part_r (double, 2 per row) and part_b.
+// transposed products to part_r (the unnormalised double-float accumulators (s, c) of the four
+// components, two float4 per row: no FP64 instruction in this pass) and part_b.
 // ---------------------------------------------------------------------------------------------
 namespace {
 constexpr int NSTD = 2;          // ring depth of the double-float pass
 constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8;   // floats: hi and lo words, u_b row window
 }
 
-__global__ void __launch_bounds__(2 * NT) k_residual_own_df(OpView A, const float2* __restrict__ S,
-                                                            const float2* __restrict__ Ht,
-                                                            const float4* __restrict__ u,
-                                                            const float4* __restrict__ v,
-                                                            const float2* __restrict__ psi32,
-                                                            const float* __restrict__ Wh, const float* __restrict__ Wl,
-                                                            double2* __restrict__ r_out, float2* __restrict__ b_out,
-                                                            double2* __restrict__ part_r, float4* __restrict__ part_b,
-                                                            const int* need_b_flag, int* err)
+// Warp roles: warps 0..3 direct products (row r0 + tid), warps 4..7 transposed products (output row
+// r0 - h + tid - 128), warp 8 the producer that keeps the NSTD-deep ring of bulk copies filled.  A
+// stage is refilled when all eight consumer warps have released it (an "empty" mbarrier), so the two
+// roles drift freely within the ring instead of meeting at a block barrier for every pair.
+constexpr int NTHR_OWN = 2 * NT + 32;
+
+__global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const float2* __restrict__ S,
+                                                             const float2* __restrict__ Ht,
+                                                             const float4* __restrict__ u,
+                                                             const float4* __restrict__ v,
+                                                             const float2* __restrict__ psi32,
+                                                             const float* __restrict__ Wh, const float* __restrict__ Wl,
+                                                             double2* __restrict__ r_out, float2* __restrict__ b_out,
+                                                             float4* __restrict__ part_r, float4* __restrict__ part_b,
+                                                             const int* need_b_flag, int* err)
 {
     // ring stage: hi words, lo words of the TR coupling rows, then u_b rows r0 - h .. r0 + TR + h
     extern __shared__ __align__(128) float wring[];
     __shared__ float4 us[2 * TR];                    // u_a rows: (type 0, type 1) split complex
     __shared__ float4 ps[TR];                        // psi_a rows in FP32: (p0.re, p0.im, p1.re, p1.im)
-    __shared__ uint64_t bar[NSTD];
+    __shared__ uint64_t full[NSTD], empty[NSTD];
+    __shared__ int fail, issued;
     const bool need_b = *need_b_flag != 0;
     const int n1 = A.n1, ntile = gridDim.y;
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
     const int rows = min(TR, n1 - r0);
     const uint32_t bytes = (uint32_t)rows * ROWF * 4;
     const int own0 = A.own_start[ch], nown = A.own_start[ch + 1] - own0;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int stage_f = STAGE_DF;
     // u_b window: rows [lo, hi) land at window index lo - (r0 - h)
     const int lo = max(0, r0 - HO), hi = min(n1, r0 + TR + HO);
     const uint32_t ubytes = (uint32_t)(hi - lo) * 32;
     const int uoff = (lo - (r0 - HO)) * 8;   // floats
-    auto issue = [&](int k, int slot) {
-        int64_t p = A.own_pair[own0 + k];
-        int nb = A.own_nbr[own0 + k];
-        float* st = wring + slot * stage_f;
-        mbar_expect_tx(&bar[slot], 2 * bytes + ubytes);
-        bulk_load(st, Wh + (p * n1 + r0) * ROWF, bytes, &bar[slot]);
-        bulk_load(st + TR * ROWF, Wl + (p * n1 + r0) * ROWF, bytes, &bar[slot]);
-        bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nb * n1 + lo) * 2, ubytes, &bar[slot]);
-    };
     if (tid == 0) {
-        for (int s = 0; s < NSTD; s++) mbar_init(&bar[s], 1);
+        for (int q = 0; q < NSTD; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 2 * NT / 32);
+        }
+        fail = 0;
+        issued = 0;
         mbar_fence_init();
     }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < min(NSTD, nown); k++) issue(k, k);
     const float4* ua = u + (int64_t)ch * 2 * n1;
     const float4* va = v + (int64_t)ch * 2 * n1;
     const float2* pa = psi32 + (int64_t)ch * 2 * n1;
@@ -343,10 +365,11 @@ __global__ void __launch_bounds__(2 * NT) k_residual_own_df(OpView A, const floa
         ps[tid] = in ? *reinterpret_cast<const float4*>(pa + 2 * (r0 + tid)) : z;
     }
     const int r = r0 + tid;
+    const bool direct_row = tid < TR && r < n1;
     DfAcc yv[4];   // (type 0 re, im, type 1 re, im)
     for (int k = 0; k < 4; k++) df_zero(yv[k]);
     float bb[4] = {0.f, 0.f, 0.f, 0.f};
-    if (tid < TR && r < n1) {
+    if (direct_row) {
         int ks = A.ch_kslot[ch];
         const float2* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
         const float2* Hk = Ht + ((int64_t)ks * n1 + r) * ROWF;
@@ -374,25 +397,41 @@ __global__ void __launch_bounds__(2 * NT) k_residual_own_df(OpView A, const floa
             }
         }
     }
-    __syncthreads();   // us, ps ready
+    __syncthreads();   // barriers initialised, us and ps staged
     DfAcc dd[4];
     for (int k = 0; k < 4; k++) df_zero(dd[k]);
     float db[4] = {0.f, 0.f, 0.f, 0.f};
-    int kfail = -1;
-    for (int k = 0; k < nown; k++) {
-        const int s = k % NSTD;
-        const bool arrived = mbar_wait(&bar[s], (uint32_t)((k / NSTD) & 1));
-        const int e = own0 + k;
-        const int64_t p = A.own_pair[e];
-        const float* Hs = wring + s * stage_f;
-        const float* Ls = Hs + TR * ROWF;
-        const float4* Us = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window][2]
-        if (arrived) {
+    if (warp == 2 * NT / 32) {
+        // producer
+        if (lane == 0) {
+            for (int k = 0; k < nown; k++) {
+                const int s = k % NSTD;
+                if (k >= NSTD && !mbar_wait(&empty[s], (uint32_t)((k / NSTD - 1) & 1))) { fail = 1; break; }
+                const int64_t p = A.own_pair[own0 + k];
+                const int nb = A.own_nbr[own0 + k];
+                float* st = wring + s * stage_f;
+                fence_proxy_async();
+                mbar_expect_tx(&full[s], 2 * bytes + ubytes);
+                bulk_load(st, Wh + (p * n1 + r0) * ROWF, bytes, &full[s]);
+                bulk_load(st + TR * ROWF, Wl + (p * n1 + r0) * ROWF, bytes, &full[s]);
+                bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nb * n1 + lo) * 2, ubytes, &full[s]);
+                issued = k + 1;
+            }
+        }
+    } else {
+        for (int k = 0; k < nown; k++) {
+            const int s = k % NSTD;
+            if (!mbar_wait(&full[s], (uint32_t)((k / NSTD) & 1))) { fail = 1; break; }
+            const int e = own0 + k;
+            const int64_t p = A.own_pair[e];
+            const float* Hs = wring + s * stage_f;
+            const float* Ls = Hs + TR * ROWF;
+            const float4* Us = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window][2]
             if (tid < NT) {
-                if (tid < TR && r < n1) {
+                if (direct_row) {
                     const int nb = A.own_nbr[e];
                     const float2* pb = psi32 + (int64_t)nb * 2 * n1;
-#pragma unroll 1   // keeps the double-float loop bodies within the instruction cache
+#pragma unroll 1
                     for (int d = 0; d < BDO; d++) {
                         int rr = r + d - HO;
                         if (rr < 0 || rr >= n1) continue;
@@ -415,50 +454,51 @@ __global__ void __launch_bounds__(2 * NT) k_residual_own_df(OpView A, const floa
                     }
                 }
             } else {
-                double2* pr = part_r + (((int64_t)p * ntile + tile) * NOUT) * 2;
+                float4* pr = part_r + (((int64_t)p * ntile + tile) * NOUT) * 2;
                 float4* pbp = part_b + ((int64_t)p * ntile + tile) * NOUT;
-                for (int j = tid - NT; j < NOUT; j += NT) {
-                    DfAcc tt[4];
-                    for (int q = 0; q < 4; q++) df_zero(tt[q]);
-                    float tb[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll 1   // keeps the double-float loop bodies within the instruction cache
-                    for (int d = 0; d < BDO; d++) {
-                        int lr = j - d;
-                        if (lr < 0 || lr >= rows) continue;
-                        float4 wh = *reinterpret_cast<const float4*>(Hs + lr * ROWF + d * 4);
-                        float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
-                        float4 x0 = us[2 * lr], x1 = us[2 * lr + 1];
-                        // (W^T)[t][u] = W[u][t]
-                        df_fma(tt[0], wh.x, wl.x, x0.x, x0.y); df_fma(tt[0], wh.z, wl.z, x1.x, x1.y);
-                        df_fma(tt[1], wh.x, wl.x, x0.z, x0.w); df_fma(tt[1], wh.z, wl.z, x1.z, x1.w);
-                        df_fma(tt[2], wh.y, wl.y, x0.x, x0.y); df_fma(tt[2], wh.w, wl.w, x1.x, x1.y);
-                        df_fma(tt[3], wh.y, wl.y, x0.z, x0.w); df_fma(tt[3], wh.w, wl.w, x1.z, x1.w);
-                        if (need_b) {
-                            float4 q = ps[lr];
-                            tb[0] += wh.x * q.x + wh.z * q.z;
-                            tb[1] += wh.x * q.y + wh.z * q.w;
-                            tb[2] += wh.y * q.x + wh.w * q.z;
-                            tb[3] += wh.y * q.y + wh.w * q.w;
-                        }
+                const int j = tid - NT;   // one output row per thread (NOUT == NT)
+                DfAcc tt[4];
+                for (int q = 0; q < 4; q++) df_zero(tt[q]);
+                float tb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+                for (int d = 0; d < BDO; d++) {
+                    int lr = j - d;
+                    if (lr < 0 || lr >= rows) continue;
+                    float4 wh = *reinterpret_cast<const float4*>(Hs + lr * ROWF + d * 4);
+                    float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
+                    float4 x0 = us[2 * lr], x1 = us[2 * lr + 1];
+                    // (W^T)[t][u] = W[u][t]
+                    df_fma(tt[0], wh.x, wl.x, x0.x, x0.y); df_fma(tt[0], wh.z, wl.z, x1.x, x1.y);
+                    df_fma(tt[1], wh.x, wl.x, x0.z, x0.w); df_fma(tt[1], wh.z, wl.z, x1.z, x1.w);
+                    df_fma(tt[2], wh.y, wl.y, x0.x, x0.y); df_fma(tt[2], wh.w, wl.w, x1.x, x1.y);
+                    df_fma(tt[3], wh.y, wl.y, x0.z, x0.w); df_fma(tt[3], wh.w, wl.w, x1.z, x1.w);
+                    if (need_b) {
+                        float4 q = ps[lr];
+                        tb[0] += wh.x * q.x + wh.z * q.z;
+                        tb[1] += wh.x * q.y + wh.z * q.w;
+                        tb[2] += wh.y * q.x + wh.w * q.z;
+                        tb[3] += wh.y * q.y + wh.w * q.w;
                     }
-                    pr[2 * j] = make_double2(df_value(tt[0]), df_value(tt[1]));
-                    pr[2 * j + 1] = make_double2(df_value(tt[2]), df_value(tt[3]));
-                    if (need_b) pbp[j] = make_float4(tb[0], tb[1], tb[2], tb[3]);
                 }
+                pr[2 * j] = make_float4(tt[0].s, tt[0].c, tt[1].s, tt[1].c);
+                pr[2 * j + 1] = make_float4(tt[2].s, tt[2].c, tt[3].s, tt[3].c);
+                if (need_b) pbp[j] = make_float4(tb[0], tb[1], tb[2], tb[3]);
             }
-        }
-        if (!__syncthreads_and(arrived)) { kfail = k; break; }
-        if (tid == 0 && k + NSTD < nown) {
-            fence_proxy_async();
-            issue(k + NSTD, s);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
         }
     }
-    if (kfail >= 0) {
-        if (tid == 0) atomicExch(err, 1);
-        for (int k = kfail; k < min(nown, kfail + NSTD); k++) mbar_wait(&bar[k % NSTD], (uint32_t)((k / NSTD) & 1));
+    __syncthreads();
+    if (fail) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // copies still in flight target this block's shared memory: give the last ones issued
+            // the same time limit before the block exits
+            for (int k = max(0, issued - NSTD); k < issued; k++) mbar_wait(&full[k % NSTD], (uint32_t)((k / NSTD) & 1));
+        }
         return;
     }
-    if (tid < TR && r < n1) {
+    if (direct_row) {
         for (int k = 0; k < 4; k++) df_add(yv[k], dd[k], 1.f);
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
         r_out[o] = make_double2(df_value(yv[0]), df_value(yv[1]));
@@ -469,11 +509,11 @@ __global__ void __launch_bounds__(2 * NT) k_residual_own_df(OpView A, const floa
     }
 }
 
-// r_b -= sum of the transposed partials (own tile and the neighbours' halo rows, fixed order);
-// partials of ||r||^2 and, on a step's first pass, of ||b||^2
+// r_b -= sum of the transposed partials (own tile and the neighbours' halo rows, fixed order) in
+// double-float; partials of ||r||^2 and, on a step's first pass, of ||b||^2
 __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, double2* __restrict__ r_out,
                                                            const float2* __restrict__ b_out,
-                                                           const double2* __restrict__ part_r,
+                                                           const float4* __restrict__ part_r,
                                                            const float4* __restrict__ part_b,
                                                            const int* need_b_flag, double* pn_r, double* pn_b)
 {
@@ -485,10 +525,17 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, double2* __
     if (tid < TR && r < n1) {
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
         double2 y0 = r_out[o], y1 = r_out[o + 1];
+        DfAcc acc[4];
+        const double yv[4] = {y0.x, y0.y, y1.x, y1.y};
+        for (int k = 0; k < 4; k++) {
+            float2 h = df_split(yv[k]);
+            acc[k].s = h.x;
+            acc[k].c = h.y;
+        }
         float4 bv = need_b ? *reinterpret_cast<const float4*>(b_out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int e = A.in_start[ch]; e < A.in_start[ch + 1]; e++) {
             int64_t p = A.in_pair[e];
-            const double2* pr = part_r + (int64_t)p * ntile * NOUT * 2;
+            const float4* pr = part_r + (int64_t)p * ntile * NOUT * 2;
             const float4* pb = part_b + (int64_t)p * ntile * NOUT;
             int js[3], ts[3], nj = 0;
             js[nj] = tid + HO; ts[nj++] = tile;
@@ -496,14 +543,20 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, double2* __
             if (tid >= TR - HO && tile + 1 < ntile) { js[nj] = tid - TR + HO; ts[nj++] = tile + 1; }
             for (int q = 0; q < nj; q++) {
                 int64_t i = (int64_t)ts[q] * NOUT + js[q];
-                double2 a = pr[2 * i], c = pr[2 * i + 1];
-                y0.x -= a.x; y0.y -= a.y; y1.x -= c.x; y1.y -= c.y;
+                float4 a = pr[2 * i], c = pr[2 * i + 1];
+                DfAcc t0 = {a.x, a.y}, t1 = {a.z, a.w}, t2 = {c.x, c.y}, t3 = {c.z, c.w};
+                df_add(acc[0], t0, -1.f);
+                df_add(acc[1], t1, -1.f);
+                df_add(acc[2], t2, -1.f);
+                df_add(acc[3], t3, -1.f);
                 if (need_b) {
                     float4 w = pb[i];
                     bv.x -= w.x; bv.y -= w.y; bv.z -= w.z; bv.w -= w.w;
                 }
             }
         }
+        y0 = make_double2(df_value(acc[0]), df_value(acc[1]));
+        y1 = make_double2(df_value(acc[2]), df_value(acc[3]));
         r_out[o] = y0;
         r_out[o + 1] = y1;
         nr = y0.x * y0.x + y0.y * y0.y + y1.x * y1.x + y1.y * y1.y;
@@ -518,16 +571,16 @@ size_t residual_own_df_smem() { return (size_t)NSTD * STAGE_DF * sizeof(float); 
 
 void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                             const float4* v, const float2* psi32, const float* Wh, const float* Wl, double2* r,
-                            float2* b, double2* part_r, float4* part_b, const int* need_b, double* pn_r,
+                            float2* b, float4* part_r, float4* part_b, const int* need_b, double* pn_r,
                             double* pn_b, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_residual_own_df<<<grid, 2 * NT, residual_own_df_smem(), st>>>(A, S, Ht, u, v, psi32, Wh, Wl, r, b, part_r,
+    k_residual_own_df<<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, S, Ht, u, v, psi32, Wh, Wl, r, b, part_r,
                                                                     part_b, need_b, err);
     k_residual_gather_df<<<grid, NT, 0, st>>>(A, r, b, part_r, part_b, need_b, pn_r, pn_b);
 }
 
-size_t apply_own32_smem() { return (size_t)NST * TR * ROWF * sizeof(float); }
+size_t apply_own32_smem() { return (size_t)NST * STAGE32 * sizeof(float); }
 int apply_own_tile() { return TR; }
 int apply_own_nout() { return NOUT; }
 bool apply_own_supported(const OpView& A) { return A.bd == BDO; }
@@ -547,7 +600,7 @@ void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const 
                         double* pnrm, const KState* skip, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_apply_own32<<<grid, 2 * NT, apply_own32_smem(), st>>>(A, S, H, sign, (const float2*)x, W, (float2*)y, part,
+    k_apply_own32<<<grid, 2 * NT + 32, apply_own32_smem(), st>>>(A, S, H, sign, (const float2*)x, W, (float2*)y, part,
                                                             skip, err);
     k_apply_gather32<<<grid, NT, 0, st>>>(A, sign, (float2*)y, part, (const float2*)bsub, (const float2*)dv, pdot,
                                           pnrm, skip);

@@ -35,9 +35,12 @@ struct dirac_op {
     cudaStream_t st = nullptr;
     int device = 0;
     int64_t n = 0, npairs = 0;
-    int nparts_apply = 0, nparts_vec = 0, nparts_prec = 0, nparts_prec32 = 0;
+    // block partials written by each kind of launch (the reductions must read exactly these):
+    // nparts_apply: 128-row tiles (FP64 apply, observables); nparts_own: the owner/gather passes
+    int nparts_apply = 0, nparts_own = 0, nparts_vec = 0, nparts_prec = 0, nparts_prec32 = 0;
     int prec_warps = 0;          // same-kappa channel groups (lane-per-channel preconditioner)
     bool prec_lanes = true;      // complex64 preconditioner schedule: one lane (else one warp) per channel
+    float prec_ms[2] = {0, 0};   // the setup's timing of the two schedules (lane, warp)
     int config_gen = 0;          // bumped when a launch choice changes (captured graphs are rebuilt)
     int *wks = nullptr, *wfirst = nullptr, *wcnt = nullptr;
     std::vector<void*> allocs;
@@ -61,7 +64,7 @@ struct dirac_op {
     double* part_n = nullptr;
     double* part_n2 = nullptr;
     float4* part_own = nullptr;  // transposed partial products of the complex64 owner/gather apply
-    double2* part_rdf = nullptr; // ... of the double-float refinement residual (2 per row)
+    float4* part_rdf = nullptr;  // ... of the double-float refinement residual (2 per row)
     float4* part_bdf = nullptr;  // ... of b = A_- psi on a step's first refinement pass
     float2* psi32 = nullptr;     // psi in FP32 and b = A_- psi (tolerance scale) of the residual pass
     float2* b32 = nullptr;
@@ -92,6 +95,7 @@ namespace dg {
 int grid_for(int64_t n, int bs);
 void collect_phases(dirac_op* op);
 dirac_status check_launch(const char* what);
+int apply_parts(const dirac_op* op, const Krylov& K);   // partials of k_apply_launch on K
 void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
                     const void* dv, double2* pdot, double* pnrm, const KState* skip);
 void launch_assemble(dirac_op* op);

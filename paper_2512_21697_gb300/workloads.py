@@ -49,7 +49,13 @@ SLICE = _base(R=300.0, N=157, grid=1, r_lin=60.0, n_lin=76, kappa_max=5, two_mu_
 MEDIUM = _base(R=300.0, N=600, grid=1, r_lin=60.0, n_lin=299, kappa_max=14, two_mu_max=0, l_max=6,
                E0=0.1, omega=omega_from_nm(800), n_cycles=3.0, dt=0.005, steps=20, tol=1e-10)
 
-WORKLOADS = {"small": SMALL, "production": PRODUCTION, "tiny": TINY, "slice": SLICE, "medium": MEDIUM}
+# Ragged-tail case for the kernels' row tiles: 121 radial slots are one 128-row tile but two
+# 116-row tiles, so every partial count and halo of the tiled passes is exercised.
+TAIL = _base(R=300.0, N=120, grid=1, r_lin=60.0, n_lin=58, kappa_max=4, two_mu_max=0, l_max=4,
+             E0=0.1, omega=omega_from_nm(800), n_cycles=3.0, dt=0.005, steps=20, tol=1e-12)
+
+WORKLOADS = {"small": SMALL, "production": PRODUCTION, "tiny": TINY, "slice": SLICE, "medium": MEDIUM,
+             "tail": TAIL}
 
 
 def oracle_params(cfg):

@@ -160,7 +160,7 @@ def test_production_apply_sampled_rows(oracle_mod):
     assert np.abs(y[rows] - ref).max() <= 1e-12 * scale
 
 
-@pytest.mark.parametrize("name", ["tiny", "small", "slice"])
+@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail"])
 def test_mixed_precision_step_matches_oracle(oracle_mod, name):
     # complex64 BiCGSTAB inside double-precision refinement: the refinement stops on the FP64 true
     # residual, so the result meets the same parity bar as the FP64 path
@@ -179,7 +179,7 @@ def test_mixed_precision_step_matches_oracle(oracle_mod, name):
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("name", ["tiny", "small", "slice"])
+@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail"])
 def test_double_float_apply_matches_oracle(oracle_mod, name):
     # precision 2 applies A_+- in double-float (FP32 hi/lo pairs with error-free transforms):
     # ~2^-44 relative per operation, so the bar is 1e-11 of max|y| instead of 1e-12
@@ -196,7 +196,7 @@ def test_double_float_apply_matches_oracle(oracle_mod, name):
         assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max(), sign
 
 
-@pytest.mark.parametrize("name", ["tiny", "small", "slice"])
+@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail"])
 def test_double_float_step_matches_oracle(oracle_mod, name):
     cfg = W.WORKLOADS[name]
     c = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
