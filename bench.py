@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--batch-n", type=int, default=64, help="instances of --workload batch")
+    ap.add_argument("--overlap", action="store_true",
+                    help="precision 2: assemble the next step during the current solve (same arithmetic)")
     return ap.parse_args()
 
 
@@ -357,6 +359,8 @@ def main():
     stream = torch.cuda.Stream()
     op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=args.precision, max_iter=1000,
                     tol_inner=1e-5, max_outer=20)
+    if args.precision == 2 and args.overlap:
+        op.set_overlap(True)   # next step's assembly overlaps the current solve (same arithmetic)
     dev = torch.device("cuda", local)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)
@@ -439,6 +443,8 @@ def main():
                    "pairs": bas.npairs, "t_start": t0,
                    "precision": ["fp64", "mixed: c64 BiCGSTAB in FP64 refinement",
                                  "mixed: c64 BiCGSTAB in double-float refinement"][args.precision],
+                   "assembly": "overlapped with the previous step's solve" if (args.precision == 2 and
+                                                                               args.overlap) else "in step",
                    "l2": "inputs larger than L2: %.1f GB of coupling values streamed per operator apply" %
                          (8 * coup / 1e9),
                    "parallelism": "replicas x%d (independent instances, no collective)" % world},

@@ -261,6 +261,14 @@ dirac_status dirac_guess_train_step(dirac_guess* net, const float* x_dev, const 
  * dirac_run / dirac_solve_batch, the extrapolated guess is used. */
 dirac_status dirac_op_set_guess(dirac_op* op, dirac_guess* net);
 
+/* Overlapped assembly (precision 2 only; no counterpart in the paper, a scheduling choice): with
+ * enable != 0, dirac_step assembles step s + 1's coupling values (they depend only on the time) on a
+ * second stream into a second buffer set while step s solves, instead of at the start of step s + 1.
+ * Results are identical (same kernels on the same data).  The first call allocates the second set
+ * (the coupling values, K bands and pulse factors again: about the operator's coupling storage)
+ * and a stream.  dirac_run and dirac_solve_batch do not overlap.  DIRAC_E_ARG if precision != 2. */
+dirac_status dirac_op_set_overlap(dirac_op* op, int enable);
+
 const char* dirac_last_error(void);
 
 #ifdef __cplusplus

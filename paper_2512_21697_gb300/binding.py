@@ -79,6 +79,7 @@ SIGNATURES = {
     "dirac_guess_loss_grad": (C.c_int, [_VP, _VP, _VP, C.c_int, _DP, C.POINTER(C.c_float), _VP]),
     "dirac_guess_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_double, _DP, _VP]),
     "dirac_op_set_guess": (C.c_int, [_VP, _VP]),
+    "dirac_op_set_overlap": (C.c_int, [_VP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
 }
 
@@ -227,6 +228,10 @@ class Operator:
     @property
     def precision(self):
         return self.opts.precision
+
+    def set_overlap(self, enable=True):
+        """dirac_op_set_overlap: assemble the next step's coupling values during the current solve."""
+        _check(lib().dirac_op_set_overlap(self._h, int(bool(enable))), "dirac_op_set_overlap")
 
     def device_bytes(self):
         return lib().dirac_op_device_bytes(self._h)

@@ -80,27 +80,35 @@ static cudaEvent_t take_event(dirac_op* op)
 struct PhaseScope {
     dirac_op* op;
     int phase;
+    cudaStream_t st;
     cudaEvent_t a = nullptr;
-    PhaseScope(dirac_op* o, int ph, int nlaunch) : op(o), phase(ph)
+    PhaseScope(dirac_op* o, int ph, int nlaunch, cudaStream_t stream = nullptr)
+        : op(o), phase(ph), st(stream ? stream : o->st)
     {
         op->launches += nlaunch;
         if (op->profiling) {
             a = take_event(op);
-            cudaEventRecord(a, op->st);
+            cudaEventRecord(a, st);
         }
     }
     ~PhaseScope()
     {
         if (!a) return;
         cudaEvent_t b = take_event(op);
-        cudaEventRecord(b, op->st);
+        cudaEventRecord(b, st);
         op->pending.push_back({phase, {a, b}});
     }
 };
 
 void collect_phases(dirac_op* op)
 {
+    // timers on the overlapped assembly stream may still be running: keep those for a later call
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> keep;
     for (auto& pe : op->pending) {
+        if (cudaEventQuery(pe.second.second) == cudaErrorNotReady) {
+            keep.push_back(pe);
+            continue;
+        }
         float ms = 0;
         if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
             op->phase_ms[pe.first] += ms;
@@ -109,7 +117,9 @@ void collect_phases(dirac_op* op)
         op->event_pool.push_back(pe.second.first);
         op->event_pool.push_back(pe.second.second);
     }
-    op->pending.clear();
+    // a not-ready query is not an error of the stream; clear it only if it is what is pending
+    if (!keep.empty() && cudaPeekAtLastError() == cudaErrorNotReady) cudaGetLastError();
+    op->pending.swap(keep);
 }
 
 // ---- launch helpers ------------------------------------------------------------------------
@@ -134,22 +144,32 @@ void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void
                               (const float*)K.W, y, bsub, dv, pdot, pnrm, skip);
 }
 
+// precision 2: pulse factors, combined bands and double-float coupling values of one buffer set,
+// on stream st (the op's stream, or the overlap stream)
+void launch_assemble_set(dirac_op* op, cudaStream_t st, const AsmSet& a)
+{
+    PhaseScope ps(op, DIRAC_PHASE_ASSEMBLE, op->npairs ? 4 : 2, st);
+    k_time_factors<<<1, 128, 0, st>>>(op->pv, a.t_eval, a.s);
+    int be = op->ov.n1 * op->ov.bd * 4;
+    k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, st>>>(op->pv, be, a.s, a.Gdf);
+    if (op->npairs) {
+        k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, st>>>(
+            op->ov, be, a.Gdf, a.Kdf, a.KTdf);
+        launch_assemble_df(dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
+                                (unsigned)std::min<int64_t>(op->npairs, 65535)),
+                           st, op->ov, a.Kdf, a.KTdf, op->cab_df, a.Wh, a.Wl);
+    }
+}
+
 void launch_assemble(dirac_op* op)
 {
+    if (op->opts.precision == 2) {
+        launch_assemble_set(op, op->st, op->aset[op->acur]);
+        return;
+    }
     PhaseScope ps(op, DIRAC_PHASE_ASSEMBLE, op->npairs ? 4 : 2);
     k_time_factors<<<1, 128, 0, op->st>>>(op->pv, op->t_eval, op->s);
     int be = op->ov.n1 * op->ov.bd * 4;
-    if (op->opts.precision == 2) {
-        k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->Gdf);
-        if (op->npairs) {
-            k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, op->st>>>(
-                op->ov, be, op->Gdf, op->Kdf, op->KTdf);
-            launch_assemble_df(dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
-                                    (unsigned)std::min<int64_t>(op->npairs, 65535)),
-                               op->st, op->ov, op->Kdf, op->KTdf, op->cab_df, op->Wh, op->Wl);
-        }
-        return;
-    }
     k_field_combine<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, op->st>>>(op->pv, be, op->s, op->G);
     if (op->npairs) {
         k_build_K<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, op->st>>>(
@@ -397,9 +417,19 @@ extern "C" void dirac_op_free(dirac_op* op)
 {
     if (!op) return;
     cudaStreamSynchronize(op->st);
+    if (op->st_asm) cudaStreamSynchronize(op->st_asm);
     collect_phases(op);
     graph_free(op);
     for (cudaEvent_t e : op->event_pool) cudaEventDestroy(e);
+    for (auto& pe : op->pending) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (int i = 0; i < 2; i++) {
+        if (op->ev_asm[i]) cudaEventDestroy(op->ev_asm[i]);
+        if (op->ev_use[i]) cudaEventDestroy(op->ev_use[i]);
+    }
+    if (op->st_asm) cudaStreamDestroy(op->st_asm);
     for (void* p : op->allocs) cudaFree(p);
     delete op;
 }
@@ -720,6 +750,8 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         TRY(dev_alloc(op, &op->Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be));
         TRY(dev_alloc(op, &op->xsplit, (size_t)op->n));
         TRY(dev_alloc(op, &op->vsplit, (size_t)op->n));
+        op->aset[0] = AsmSet{op->t_eval, op->s, op->Gdf, op->Kdf, op->KTdf, op->Wh, op->Wl};
+        op->acur = 0;
     }
 
     // Krylov workspaces and reduction partials
@@ -850,6 +882,51 @@ extern "C" dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, voi
     return check_launch("dirac_precond_apply");
 }
 
+// make buffer set c the current one (the pointers every precision-2 kernel reads)
+static void select_set(dirac_op* op, int c)
+{
+    if (c == op->acur) return;
+    const AsmSet& a = op->aset[c];
+    op->t_eval = a.t_eval;
+    op->s = a.s;
+    op->Gdf = a.Gdf;
+    op->Kdf = a.Kdf;
+    op->KTdf = a.KTdf;
+    op->Wh = a.Wh;
+    op->Wl = a.Wl;
+    op->k32.W = a.Wh;
+    op->acur = c;
+    op->config_gen++;   // captured graphs hold the old pointers
+}
+
+extern "C" dirac_status dirac_op_set_overlap(dirac_op* op, int enable)
+{
+    if (!op || (enable && op->opts.precision != 2)) {
+        set_error("dirac_op_set_overlap: bad argument (the overlapped assembly needs precision 2)");
+        return DIRAC_E_ARG;
+    }
+    if (enable && !op->aset[1].Wh) {
+        size_t be = (size_t)op->ov.n1 * op->ov.bd * 4;
+        AsmSet a;
+        dirac_status e;
+        if ((e = dev_alloc(op, &a.t_eval, 1)) || (e = dev_alloc(op, &a.s, (size_t)op->pv.L * 3)) ||
+            (e = dev_alloc(op, &a.Gdf, (size_t)op->pv.L * 4 * be)) ||
+            (e = dev_alloc(op, &a.Kdf, (size_t)std::max(op->ov.nkeys, 1) * be)) ||
+            (e = dev_alloc(op, &a.KTdf, (size_t)std::max(op->ov.nkeys, 1) * be)) ||
+            (e = dev_alloc(op, &a.Wh, (size_t)std::max<int64_t>(op->npairs, 1) * be)) ||
+            (e = dev_alloc(op, &a.Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be)))
+            return e;
+        CUDA_TRY(cudaStreamCreateWithFlags(&op->st_asm, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; i++) {
+            CUDA_TRY(cudaEventCreateWithFlags(&op->ev_asm[i], cudaEventDisableTiming));
+            CUDA_TRY(cudaEventCreateWithFlags(&op->ev_use[i], cudaEventDisableTiming));
+        }
+        op->aset[1] = a;
+    }
+    op->overlap = enable != 0;
+    return DIRAC_OK;
+}
+
 extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
                                    double t_start, int* iters_out, double* resid_out)
 {
@@ -866,10 +943,27 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
     int npv = op->nparts_vec;
     Krylov& K = op->k64;
     dirac_status result = DIRAC_OK;
+    // overlapped assembly: step s + 1's coupling values are assembled on st_asm into the other buffer
+    // set while step s solves; ev_asm[c] marks set c assembled, ev_use[c] the end of its last use
+    const bool ovl = op->overlap && o.precision == 2 && op->aset[1].Wh;
+    const double t_off = o.time_eval ? o.dt : 0.5 * o.dt;
     for (int step = 0; step < n_steps; step++) {
-        k_set_step_time<<<1, 1, 0, op->st>>>(op->t_eval, t_start, step, o.dt, o.time_eval ? o.dt : 0.5 * o.dt);
-        op->launches++;
-        launch_assemble(op);
+        if (!ovl || step == 0) {
+            if (ovl) CUDA_TRY(cudaStreamWaitEvent(op->st, op->ev_asm[op->acur], 0));   // a pending fill of this set
+            k_set_step_time<<<1, 1, 0, op->st>>>(op->t_eval, t_start, step, o.dt, t_off);
+            op->launches++;
+            launch_assemble(op);
+        } else {
+            CUDA_TRY(cudaStreamWaitEvent(op->st, op->ev_asm[op->acur], 0));
+        }
+        if (ovl && step + 1 < n_steps) {
+            const int nx = 1 - op->acur;
+            CUDA_TRY(cudaStreamWaitEvent(op->st_asm, op->ev_use[nx], 0));
+            k_set_step_time<<<1, 1, 0, op->st_asm>>>(op->aset[nx].t_eval, t_start, step + 1, o.dt, t_off);
+            op->launches++;
+            launch_assemble_set(op, op->st_asm, op->aset[nx]);
+            CUDA_TRY(cudaEventRecord(op->ev_asm[nx], op->st_asm));
+        }
         // b = A_- psi, ||b||^2 (precision 2 forms them inside the residual passes)
         if (o.precision == 0) {
             apply_accurate(op, -1, psi, K.b, nullptr, op->part_n);
@@ -936,6 +1030,10 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
             }
             k_copy64<<<npv, 256, 0, op->st>>>(n, (const double2*)K.x, psi);
         }
+        if (ovl) {
+            CUDA_TRY(cudaEventRecord(op->ev_use[op->acur], op->st));
+            if (step + 1 < n_steps) select_set(op, 1 - op->acur);
+        }
         e = check_launch("dirac_step");
         if (e) return e;
         if (hs.status) {
@@ -947,6 +1045,7 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
     }
     if (n_hist) *n_hist = nh;
     CUDA_TRY(cudaStreamSynchronize(op->st));
+    if (op->st_asm) CUDA_TRY(cudaStreamSynchronize(op->st_asm));
     collect_phases(op);
     dirac_status de = check_dev_err(op, "dirac_step");
     if (de) return de;

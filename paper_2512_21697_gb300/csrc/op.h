@@ -26,6 +26,16 @@ struct Krylov {
 
 struct GraphDriver;   // graph.cu
 
+// Buffers of one double-float assembly (precision 2): evaluation time, pulse factors, combined
+// bands and the coupling values they produce.  Set 0 is the operator's own; set 1 exists when the
+// next step's assembly overlaps the current step's solve.
+struct AsmSet {
+    double* t_eval = nullptr;
+    double* s = nullptr;
+    float2 *Gdf = nullptr, *Kdf = nullptr, *KTdf = nullptr;
+    float *Wh = nullptr, *Wl = nullptr;
+};
+
 }  // namespace dg
 
 struct dirac_op {
@@ -88,6 +98,13 @@ struct dirac_op {
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
     std::vector<cudaEvent_t> event_pool;
     dg::GraphDriver* graph = nullptr;   // captured multi-step driver (dirac_run), built on first use
+    // overlapped assembly (dirac_op_set_overlap): the next step's coupling values are assembled on
+    // st_asm into the other buffer set while the current step solves
+    bool overlap = false;
+    dg::AsmSet aset[2];
+    int acur = 0;                        // the set op->Wh / op->Wl currently point to
+    cudaStream_t st_asm = nullptr;
+    cudaEvent_t ev_asm[2] = {nullptr, nullptr}, ev_use[2] = {nullptr, nullptr};
 };
 
 namespace dg {
@@ -99,6 +116,7 @@ int apply_parts(const dirac_op* op, const Krylov& K);   // partials of k_apply_l
 void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
                     const void* dv, double2* pdot, double* pnrm, const KState* skip);
 void launch_assemble(dirac_op* op);
+void launch_assemble_set(dirac_op* op, cudaStream_t st, const AsmSet& a);
 void apply_accurate(dirac_op* op, int sign, const void* x, void* y, const void* bsub, double* pnrm);
 void rhs_accurate(dirac_op* op, const void* psi);
 void residual_accurate(dirac_op* op, const void* psi);
