@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--batch-n", type=int, default=64, help="instances of --workload batch")
+    ap.add_argument("--learned", action="store_true",
+                    help="train the learned initial guess on production trajectories, then time guess=2 vs guess=1")
     ap.add_argument("--overlap", action="store_true",
                     help="precision 2: assemble the next step during the current solve (same arithmetic)")
     return ap.parse_args()
@@ -261,6 +263,79 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, per_step=65536, iters=1500):
+    """Learned initial guess at the production size: trajectories of the method itself (extrapolated
+    guess) for seeded pulses on the production basis give (features, target) samples; the network
+    is trained with the library's kernels; then the same K steps at peak field are timed with the
+    extrapolated guess and with the learned one (both solve to the same tolerance)."""
+    import numpy as np
+    import torch
+    from paper_2512_21697_gb300 import binding as B, learned as L, workloads as W
+    dev = torch.device("cuda", local)
+    cfg = dict(W.WORKLOADS[args.workload])
+    cfg["precision"] = args.precision
+    bas = B.Basis(cfg)
+    npos = bas.nch * (cfg["N"] + 1)
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    X, Tg = [], []
+    t_data = time.time()
+    for pc in L.pulse_variants(cfg, range(1000, 1000 + n_train)):
+        tr = L.Trajectory(bas, pc, train_steps, precision=args.precision, tol=cfg["tol"])
+        x, t = L.samples(tr)
+        idx = torch.randint(0, x.shape[0], (min(x.shape[0], per_step * (train_steps - 4)),), device=dev,
+                            generator=g)
+        X.append(x[idx])
+        Tg.append(t[idx])
+        del tr, x, t
+        torch.cuda.empty_cache()
+    X, Tg = torch.cat(X), torch.cat(Tg)
+    n_samples = int(X.shape[0])
+    t_data = time.time() - t_data
+    net = B.GuessNet(8192, W.guess_net_init(7))
+    t_train = time.time()
+    losses = L.train(net, X, Tg, iters, batch=8192, lr=1e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.time() - t_train
+    del X, Tg
+    T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
+    t0 = args.t0 if args.t0 is not None else 0.5 * T
+    psi0, _ = bas.initial_state()
+    res = {}
+    for guess in (1, 2):
+        stream = torch.cuda.Stream()
+        op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=args.precision, max_iter=1000,
+                        tol_inner=1e-5, max_outer=20, guess=guess)
+        if guess == 2:
+            B.set_guess(op, net)
+        with torch.cuda.stream(stream):
+            psi = torch.from_numpy(psi0).to(dev)
+            hist = torch.zeros(3 * bas.n, dtype=torch.complex128, device=dev)
+        _, _, nh = op.step(psi, args.warmup + 3, t0, hist=hist, n_hist=0)   # fills the history
+        tcur = t0 + (args.warmup + 3) * cfg["dt"]
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        its, rr, _ = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        res[guess] = {"value": args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
+                      "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(rr))}
+        del op
+    line = {"metric": METRIC, "value": res[2]["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res[2]["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "c64+f64", "c64+df64"][args.precision],
+            "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, cfg) + "; learned initial guess, start at t=%.2f" % t0,
+                       "training": "%d seeded pulses x %d steps (extrapolated guess), %d samples, %d Adam steps of "
+                                   "8192; data %.1f s, training %.1f s; loss %.3g -> %.3g" %
+                                   (n_train, train_steps, n_samples, iters, t_data, t_train, losses[0], losses[-1])},
+            "learned": res[2], "extrapolated": res[1], "speedup_vs_extrapolated": res[2]["value"] / res[1]["value"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def batch_bench(args, world, rank, local, dist):
     """Batched workload: independent instances (own pulse and radial size) stepped concurrently by
     dirac_solve_batch with the window and preconditioner schedule picked by dirac_batch_tune.
@@ -349,6 +424,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if args.workload == "batch":
         batch_bench(args, world, rank, local, dist)
+        return
+    if args.learned:
+        learned_bench(args, world, rank, local, dist)
         return
     cfg = dict(W.WORKLOADS[args.workload])
     T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]

@@ -269,6 +269,15 @@ dirac_status dirac_op_set_guess(dirac_op* op, dirac_guess* net);
  * and a stream.  dirac_run and dirac_solve_batch do not overlap.  DIRAC_E_ARG if precision != 2. */
 dirac_status dirac_op_set_overlap(dirac_op* op, int enable);
 
+/* Preconditioner schedule of the complex128 (complex64 = 0) or complex64 (complex64 = 1) solve:
+ * 0 one lane per channel (complex64 only; the channels of one kappa share the factor rows),
+ * 1 one warp per channel, 2 one warp per channel with the vector and the factor rows staged
+ * through shared memory.  dirac_operator_setup times the available ones and keeps the fastest;
+ * this call overrides it (DIRAC_E_ARG if the schedule is not available for the op).  Schedules 1
+ * and 2 give identical results; 0 rounds differently (within the solver tolerance). */
+dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched);
+int dirac_op_get_schedule(const dirac_op* op, int complex64);   /* -1 for a NULL op */
+
 const char* dirac_last_error(void);
 
 #ifdef __cplusplus

@@ -80,6 +80,8 @@ SIGNATURES = {
     "dirac_guess_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_double, _DP, _VP]),
     "dirac_op_set_guess": (C.c_int, [_VP, _VP]),
     "dirac_op_set_overlap": (C.c_int, [_VP, C.c_int]),
+    "dirac_op_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "dirac_op_get_schedule": (C.c_int, [_VP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
 }
 
@@ -228,6 +230,13 @@ class Operator:
     @property
     def precision(self):
         return self.opts.precision
+
+    def set_schedule(self, complex64, sched):
+        """dirac_op_set_schedule: 0 lane / 1 warp / 2 staged-warp preconditioner schedule."""
+        _check(lib().dirac_op_set_schedule(self._h, int(bool(complex64)), int(sched)), "dirac_op_set_schedule")
+
+    def schedule(self, complex64):
+        return int(lib().dirac_op_get_schedule(self._h, int(bool(complex64))))
 
     def set_overlap(self, enable=True):
         """dirac_op_set_overlap: assemble the next step's coupling values during the current solve."""

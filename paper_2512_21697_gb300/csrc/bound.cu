@@ -216,8 +216,16 @@ dirac_status bound_population(dirac_op* op, const double2* psi, double* out)
     int ns = 2 * op->ov.n1;
     size_t smem = sizeof(double2) * ns;
     if (smem > 48 * 1024) {
-        cudaError_t ce = cudaFuncSetAttribute(k_pbound, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (ce != cudaSuccess || smem > 227 * 1024) {
+        // the limit is per kernel and shared by every operator: raise it to the device maximum
+        int dev = 0, optin = 0;
+        cudaError_t ce = cudaGetDevice(&dev);
+        if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        if (ce == cudaSuccess) ce = cudaFuncGetAttributes(&fa, k_pbound);
+        int lim = ce == cudaSuccess ? optin - (int)fa.sharedSizeBytes : 0;   // static shared memory included
+        if (ce == cudaSuccess && smem <= (size_t)lim)
+            ce = cudaFuncSetAttribute(k_pbound, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+        if (ce != cudaSuccess || smem > (size_t)lim) {
             set_error("bound states: radial size too large for the projection kernel");
             return DIRAC_E_ARG;
         }

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -254,15 +256,36 @@ void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks,
                              const void* v, void* io, void* z, double* pn)
 {
     PhaseScope ps(op, DIRAC_PHASE_PRECOND, 1);
-    // complex64: one lane per channel (factor rows through shared memory); complex128: one warp per
-    // channel, which keeps every SM sub-partition's FP64 pipe busy
-    if (K.prec == 1 && op->prec_warps && op->prec_lanes)
-        launch_precond_lanes_t<float>(op->prec_warps, op->st, op->ov, K.Urow, K.L, K.Dinv, op->wks, op->wfirst,
-                                      op->wcnt, mode, ks, r, v, io, z, pn);
-    else if (K.prec == 0)
-        launch_precond_t<double>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
-    else
-        launch_precond_t<float>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
+    // schedule picked at setup: one lane per channel (channels of one kappa share the factor rows),
+    // one warp per channel, or one warp per channel with the vector and the factor rows staged
+    // through shared memory
+    if (K.prec == 1) {
+        if (op->prec_sched32 == 0 && op->prec_warps)
+            launch_precond_lanes_t<float>(op->prec_warps, op->st, op->ov, K.Urow, K.L, K.Dinv, op->wks, op->wfirst,
+                                          op->wcnt, mode, ks, r, v, io, z, pn);
+        else if (op->prec_sched32 == 2 && op->prec_sm_ok)
+            launch_precond_sm_t<float>(op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
+        else
+            launch_precond_t<float>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z,
+                                    pn);
+    } else {
+        if (op->prec_sched64 == 2 && op->prec_sm_ok)
+            launch_precond_sm_t<double>(op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
+        else
+            launch_precond_t<double>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z,
+                                     pn);
+    }
+}
+
+int prec_parts(const dirac_op* op, const Krylov& K)
+{
+    if (K.prec == 1) {
+        if (op->prec_sched32 == 0 && op->prec_warps) return op->prec_warps;
+        if (op->prec_sched32 == 2 && op->prec_sm_ok) return precond_sm_blocks<float>(op->ov.nch);
+        return grid_for(op->ov.nch, 4);
+    }
+    if (op->prec_sched64 == 2 && op->prec_sm_ok) return precond_sm_blocks<double>(op->ov.nch);
+    return grid_for(op->ov.nch, 4);
 }
 
 void finish(dirac_op* op, KState* ks, int what, int np, const double2* pd, const double* pn, int max_iter)
@@ -300,7 +323,7 @@ dirac_status check_launch(const char* what)
 // nothing more than the final update (large systems, where a host round trip is negligible).
 dirac_status bicgstab_iteration(dirac_op* op, const Krylov& K, int max_iter, bool mid_check)
 {
-    int npa = apply_parts(op, K), npp = K.prec == 1 ? op->nparts_prec32 : op->nparts_prec, npv = op->nparts_vec;
+    int npa = apply_parts(op, K), npp = prec_parts(op, K), npv = op->nparts_vec;
     // p = r + beta (p - omega v); ph = M^-1 p
     k_precond_launch(op, K, 1, K.ks, K.r, K.v, K.p, K.ph, nullptr);
     // v = A ph, <rh, v>
@@ -460,34 +483,64 @@ extern "C" dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* co
 
 extern "C" int64_t dirac_op_device_bytes(const dirac_op* op) { return op ? (int64_t)op->bytes : -1; }
 
-// Schedule of the complex64 preconditioner, picked by timing: one lane per channel (the channels
-// of one kappa share the factor rows read through shared memory) or one warp per channel (more
-// parallelism along the band).  Which is faster depends on the channel count and radial size, so
-// the operator times one application of each on zeroed vectors (after a warm-up) and keeps the
-// faster; the choice does not change results beyond the inner solve's tolerance.
-static dirac_status tune_precond32(dirac_op* op)
+// Preconditioner schedules, picked by timing: one lane per channel (the channels of one kappa share
+// the factor rows read through shared memory), one warp per channel (more parallelism along the
+// band), or one warp per channel with the vector and factor rows staged through shared memory.
+// Which is fastest depends on the channel count and radial size, so the operator times one
+// application of each on zeroed vectors (after a warm-up) and keeps the fastest, for the complex64
+// inner solve and for the complex128 solve.  The choice does not change results beyond the solver
+// tolerance (lane and warp substitutions round differently; the two warp kernels are identical).
+static dirac_status time_precond(dirac_op* op, Krylov& K, int sched, float* ms)
 {
-    Krylov& I = op->k32;
-    if (!op->prec_warps) { op->prec_lanes = false; return DIRAC_OK; }
-    size_t bytes = sizeof(float2) * (size_t)op->n;
-    CUDA_TRY(cudaMemsetAsync(I.r, 0, bytes, op->st));
-    CUDA_TRY(cudaMemsetAsync(I.sh, 0, bytes, op->st));
-    cudaEvent_t e[3];
+    int& slot = K.prec == 1 ? op->prec_sched32 : op->prec_sched64;
+    slot = sched;
+    cudaEvent_t e[2];
     for (auto& ev : e) CUDA_TRY(cudaEventCreate(&ev));
-    float ms[2] = {0, 0};
-    for (int v = 0; v < 2; v++) {
-        op->prec_lanes = v == 0;
-        k_precond_launch(op, I, 0, nullptr, I.r, nullptr, nullptr, I.sh, nullptr);   // warm-up
-        CUDA_TRY(cudaEventRecord(e[0], op->st));
-        k_precond_launch(op, I, 0, nullptr, I.r, nullptr, nullptr, I.sh, nullptr);
-        CUDA_TRY(cudaEventRecord(e[1], op->st));
-        CUDA_TRY(cudaEventSynchronize(e[1]));
-        CUDA_TRY(cudaEventElapsedTime(&ms[v], e[0], e[1]));
-    }
+    k_precond_launch(op, K, 0, nullptr, K.r, nullptr, nullptr, K.sh, nullptr);   // warm-up
+    CUDA_TRY(cudaEventRecord(e[0], op->st));
+    k_precond_launch(op, K, 0, nullptr, K.r, nullptr, nullptr, K.sh, nullptr);
+    CUDA_TRY(cudaEventRecord(e[1], op->st));
+    CUDA_TRY(cudaEventSynchronize(e[1]));
+    CUDA_TRY(cudaEventElapsedTime(ms, e[0], e[1]));
     for (auto& ev : e) cudaEventDestroy(ev);
-    op->prec_lanes = ms[0] <= ms[1];
-    op->prec_ms[0] = ms[0];
-    op->prec_ms[1] = ms[1];
+    return DIRAC_OK;
+}
+
+// Schedules chosen so far, per shape (radial slots, channels, precision of the solve, staged kernel
+// available): operators of the same shape in one process take the same schedule, so their results
+// agree bit for bit.
+static std::mutex g_sched_mutex;
+static std::map<std::tuple<int, int, int, int>, int> g_sched_cache;
+
+static dirac_status tune_precond(dirac_op* op, Krylov& K)
+{
+    auto key = std::make_tuple(op->ov.n1, op->ov.nch, K.prec, (int)op->prec_sm_ok);
+    {
+        std::lock_guard<std::mutex> lock(g_sched_mutex);
+        auto it = g_sched_cache.find(key);
+        if (it != g_sched_cache.end()) {
+            (K.prec == 1 ? op->prec_sched32 : op->prec_sched64) = it->second;
+            return DIRAC_OK;
+        }
+    }
+    size_t es = K.prec == 1 ? sizeof(float2) : sizeof(double2);
+    CUDA_TRY(cudaMemsetAsync(K.r, 0, es * (size_t)op->n, op->st));
+    CUDA_TRY(cudaMemsetAsync(K.sh, 0, es * (size_t)op->n, op->st));
+    float* ms = K.prec == 1 ? op->prec_ms32 : op->prec_ms64;
+    int best = -1;
+    for (int sched = 0; sched < 3; sched++) {
+        ms[sched] = 0;
+        if (sched == 0 && (K.prec != 1 || !op->prec_warps)) continue;
+        if (sched == 2 && !op->prec_sm_ok) continue;
+        dirac_status e = time_precond(op, K, sched, &ms[sched]);
+        if (e) return e;
+        if (best < 0 || ms[sched] < ms[best]) best = sched;
+    }
+    (K.prec == 1 ? op->prec_sched32 : op->prec_sched64) = best;
+    {
+        std::lock_guard<std::mutex> lock(g_sched_mutex);
+        g_sched_cache.emplace(key, best);
+    }
     return check_launch("dirac_operator_setup: preconditioner schedule");
 }
 
@@ -809,7 +862,8 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     op->nparts_vec = grid_for(op->n, 256);
     op->nparts_prec = grid_for(B.nch, 4);                     // ||s||^2 partials, warp-per-channel kernel
     op->nparts_prec32 = op->prec_warps ? op->prec_warps : grid_for(B.nch, 4);   // lane-per-channel kernel
-    int np = std::max({op->nparts_apply, op->nparts_own, op->nparts_vec, op->nparts_prec, op->nparts_prec32});
+    int np = std::max({op->nparts_apply, op->nparts_own, op->nparts_vec, op->nparts_prec, op->nparts_prec32,
+                       precond_sm_blocks<double>(B.nch), precond_sm_blocks<float>(B.nch)});
     TRY(dev_alloc(op, &op->part_d, (size_t)np));
     TRY(dev_alloc(op, &op->part_d2, (size_t)np));
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
@@ -843,8 +897,11 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     pv.L = P.L; pv.T = P.T; pv.amp = P.amp; pv.t0 = pulse->t0; pv.dt = opts->dt;
     for (int c = 0; c < 3; c++) { pv.w[c] = P.w[c]; pv.wt[c] = P.wt[c]; }
     pv.M = dM;
-    if (mixed) {
-        dirac_status ts = tune_precond32(op);
+    op->prec_sm_ok = precond_sm_prepare<float>(n1) == cudaSuccess && precond_sm_prepare<double>(n1) == cudaSuccess;
+    cudaGetLastError();
+    {
+        dirac_status ts = tune_precond(op, op->k64);
+        if (!ts && mixed) ts = tune_precond(op, op->k32);
         if (ts) { dirac_op_free(op); return ts; }
     }
     *out = op;
@@ -880,6 +937,24 @@ extern "C" dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, voi
     if (!op || !r_dev || !z_dev || r_dev == z_dev) { set_error("dirac_precond_apply: bad argument"); return DIRAC_E_ARG; }
     k_precond_launch(op, op->k64, 0, nullptr, r_dev, nullptr, nullptr, z_dev, nullptr);
     return check_launch("dirac_precond_apply");
+}
+
+extern "C" dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched)
+{
+    if (!op || sched < 0 || sched > 2 || (sched == 0 && (!complex64 || !op->prec_warps)) ||
+        (sched == 2 && !op->prec_sm_ok) || (complex64 && !op->k32.ks)) {
+        set_error("dirac_op_set_schedule: schedule not available for this operator");
+        return DIRAC_E_ARG;
+    }
+    (complex64 ? op->prec_sched32 : op->prec_sched64) = sched;
+    op->config_gen++;   // captured graphs hold the old kernel
+    return DIRAC_OK;
+}
+
+extern "C" int dirac_op_get_schedule(const dirac_op* op, int complex64)
+{
+    if (!op) return -1;
+    return complex64 ? op->prec_sched32 : op->prec_sched64;
 }
 
 // make buffer set c the current one (the pointers every precision-2 kernel reads)

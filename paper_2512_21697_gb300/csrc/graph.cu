@@ -348,7 +348,12 @@ static dirac_status build_graph(dirac_op* op, GraphDriver* gd, double2* psi, dou
     });
     op->profiling = prof;
     op->launches = launches;
-    if (st) return st;
+    if (st) {
+        // a graph whose capture was invalidated part-way through a conditional body is dropped, not
+        // destroyed: it is never launched, and tearing down its half-captured bodies is not relied on
+        gd->graph = nullptr;
+        return st;
+    }
     G_TRY(cudaGraphInstantiate(&gd->exec, gd->graph, 0));
     gd->psi = psi;
     gd->hist = h1;
@@ -575,7 +580,7 @@ extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void*
     int bw = cand[0], bv = 0;
     for (int v = 0; v < 2 && !first; v++) {
         for (int i = 0; i < n_inst; i++) {
-            ops[i]->prec_lanes = v == 0;
+            ops[i]->prec_sched32 = v == 0 ? 0 : 2;
             ops[i]->config_gen++;
         }
         restore();
@@ -593,7 +598,7 @@ extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void*
     restore();
     for (int i = 0; i < n_inst; i++) {
         if (ops[i]) {
-            ops[i]->prec_lanes = bv == 0;
+            ops[i]->prec_sched32 = bv == 0 ? 0 : 2;
             ops[i]->config_gen++;
             if (ops[i]->st) cudaStreamSynchronize(ops[i]->st);
         }

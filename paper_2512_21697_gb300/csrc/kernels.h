@@ -97,6 +97,14 @@ __device__ __forceinline__ double extrapolate(int nh, double p, double a, double
 }
 __global__ void k_extrapolate(int64_t n, int nh, const double2* psi, const double2* h1, const double2* h2, double2* x);
 
+// warp-per-channel preconditioner with shared-memory staging (band width 13)
+template <class T> size_t precond_sm_smem(int n1);
+template <class T> cudaError_t precond_sm_prepare(int n1);
+template <class T> int precond_sm_blocks(int nch);
+template <class T>
+void launch_precond_sm_t(cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv, int mode,
+                         const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
+
 // complex64 apply with each coupling block read once (owner pass + gather pass, bd = 13)
 size_t apply_own32_smem();
 int apply_own_tile();

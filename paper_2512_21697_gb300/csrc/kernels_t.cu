@@ -427,6 +427,248 @@ template void launch_precond_t<float>(int, cudaStream_t, const OpView&, const vo
                                       const KState*, const void*, const void*, void*, void*, double*);
 
 // ---------------------------------------------------------------------------------------------
+// Warp-per-channel preconditioner with the channel's vector in shared memory and the factor rows
+// staged through shared memory in chunks of CH rows by asynchronous copies (cp.async), one chunk
+// ahead.  The substitution is the same as k_precond (same operations in the same order, so the
+// results are identical); what changes is where the operands come from: every row of the sweeps
+// reads shared memory instead of waiting on an L2 load.  Band width KB = 13 (order-7 splines).
+// ---------------------------------------------------------------------------------------------
+namespace {
+constexpr int PCH = 16;   // factor rows per staged chunk
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// copy `bytes` (a multiple of 16, both addresses 16-byte aligned) with the warp's lanes
+__device__ __forceinline__ void warp_copy16(void* dst, const void* src, int bytes, int lane)
+{
+    for (int e = lane; e < bytes / 16; e += 32)
+        cp_async16(static_cast<char*>(dst) + 16 * e, static_cast<const char*>(src) + 16 * e);
+}
+}  // namespace
+
+template <class T>
+constexpr int prec_sm_warps() { return sizeof(T) == 4 ? 4 : 2; }
+
+// per-warp shared memory: the vector (n entries) and the factor chunk buffers
+template <class T, int KB>
+__host__ __device__ constexpr size_t prec_sm_fbytes()
+{
+    // forward: L[2][PCH][KB] + P[2][PCH] (ints); backward: Ucol[2][PCH][2 KB + 1] + Dinv[2][PCH]
+    return sizeof(c2<T>) * (2 * PCH * (2 * KB + 1) + 2 * PCH) > sizeof(c2<T>) * 2 * PCH * KB + 2 * PCH * 4
+               ? sizeof(c2<T>) * (2 * PCH * (2 * KB + 1) + 2 * PCH)
+               : sizeof(c2<T>) * 2 * PCH * KB + 2 * PCH * 4;
+}
+template <class T, int KB>
+size_t prec_sm_warp_bytes(int n)
+{
+    return ((sizeof(c2<T>) * (size_t)n + 15) / 16) * 16 + prec_sm_fbytes<T, KB>();
+}
+
+template <class T, int KB>
+__global__ void k_precond_sm(OpView A, const c2<T>* __restrict__ Ucol, const c2<T>* __restrict__ L,
+                             const c2<T>* __restrict__ Dinv, int mode, const KState* st,
+                             const c2<T>* __restrict__ r, const c2<T>* __restrict__ v, c2<T>* __restrict__ io,
+                             c2<T>* __restrict__ z, double* part_nrm, int warp_bytes)
+{
+    constexpr int WU = 2 * KB;
+    extern __shared__ __align__(16) unsigned char prec_smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int n = 2 * A.n1;
+    unsigned char* base = prec_smem + (size_t)wib * warp_bytes;
+    c2<T>* zs = reinterpret_cast<c2<T>*>(base);
+    unsigned char* fb = base + ((sizeof(c2<T>) * (size_t)n + 15) / 16) * 16;
+    c2<T>* Lb = reinterpret_cast<c2<T>*>(fb);                          // [2][PCH * KB]
+    int* Pb = reinterpret_cast<int*>(fb + sizeof(c2<T>) * 2 * PCH * KB);  // [2][PCH]
+    c2<T>* Ub = reinterpret_cast<c2<T>*>(fb);                          // [2][PCH * (WU + 1)]
+    c2<T>* Db = Ub + 2 * PCH * (WU + 1);                               // [2][PCH]
+    double nsum = 0;
+    if (warp < A.nch && !(st && st->done)) {
+        const int ch = A.prec_order[warp];
+        const int ks = A.ch_kslot[ch];
+        const c2<T>* Uk = Ucol + (int64_t)ks * n * (WU + 1);
+        const c2<T>* Lk = L + (int64_t)ks * n * KB;
+        const c2<T>* Dk = Dinv + (int64_t)ks * n;
+        const int* P = A.luP + (int64_t)ks * n;
+        const int64_t o = (int64_t)ch * n;
+        // forward factor chunk c into buffer b: rows [c PCH, c PCH + rows)
+        auto issue_fwd = [&](int c, int b) {
+            int j0 = c * PCH, rows = min(PCH, n - j0);
+            warp_copy16(Lb + b * PCH * KB, Lk + (int64_t)j0 * KB, rows * KB * (int)sizeof(c2<T>), lane);
+            for (int e = lane; e < rows; e += 32) cp_async4(Pb + b * PCH + e, P + j0 + e);
+            cp_async_commit();
+        };
+        issue_fwd(0, 0);
+        // prologue into the shared copy of the vector
+        if (mode == 0) {
+            for (int i = lane; i < n; i += 32) zs[i] = r[o + i];
+        } else if (mode == 1) {
+            c2<T> beta = from_d<T>(st->beta), omega = from_d<T>(st->omega);
+            for (int i = lane; i < n; i += 32) {
+                c2<T> pv = io[o + i], vv = v[o + i], rv = r[o + i];
+                c2<T> t = cm<T>(omega, vv);
+                c2<T> q = cm<T>(beta, mk<T>(pv.x - t.x, pv.y - t.y));
+                c2<T> pn = mk<T>(rv.x + q.x, rv.y + q.y);
+                io[o + i] = pn;
+                zs[i] = pn;
+            }
+        } else {
+            c2<T> alpha = from_d<T>(st->alpha);
+            for (int i = lane; i < n; i += 32) {
+                c2<T> t = cm<T>(alpha, v[o + i]);
+                c2<T> rv = r[o + i];
+                c2<T> sv = mk<T>(rv.x - t.x, rv.y - t.y);
+                io[o + i] = sv;
+                zs[i] = sv;
+                nsum += (double)sv.x * sv.x + (double)sv.y * sv.y;
+            }
+        }
+        __syncwarp();
+        // forward substitution: window lane l = z[j + l], l = 0..KB
+        c2<T> w = (lane <= KB && lane < n) ? zs[lane] : mk<T>(0, 0);
+        const int nc = (n + PCH - 1) / PCH;
+        for (int c = 0; c < nc; c++) {
+            if (c + 1 < nc) {
+                issue_fwd(c + 1, (c + 1) & 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncwarp();
+            const c2<T>* Lc = Lb + (c & 1) * PCH * KB;
+            const int* Pc = Pb + (c & 1) * PCH;
+            const int j0 = c * PCH, rows = min(PCH, n - j0);
+            for (int jj = 0; jj < rows; jj++) {
+                const int j = j0 + jj;
+                c2<T> lcur = (lane >= 1 && lane <= KB) ? Lc[jj * KB + lane - 1] : mk<T>(0, 0);
+                int pj = Pc[jj] - j;
+                c2<T> w0 = shfl2<T>(w, 0), wp = shfl2<T>(w, pj);
+                if (lane == 0) w = wp;
+                else if (lane == pj) w = w0;
+                c2<T> zj = shfl2<T>(w, 0);
+                if (lane >= 1 && lane <= KB && j + lane < n) {
+                    w.x -= lcur.x * zj.x - lcur.y * zj.y;
+                    w.y -= lcur.x * zj.y + lcur.y * zj.x;
+                }
+                if (lane == 0) zs[j] = zj;
+                w = shfl2_down<T>(w, 1);
+                if (lane == KB) w = (j + KB + 1 < n) ? zs[j + KB + 1] : mk<T>(0, 0);
+            }
+            __syncwarp();   // buffer (c & 1) is refilled by the next iteration's copy
+        }
+        // back substitution: lane k (1..WU) holds the partial sum of row i - k
+        auto issue_bwd = [&](int c, int b) {
+            int i0 = c * PCH, rows = min(PCH, n - i0);
+            warp_copy16(Ub + b * PCH * (WU + 1), Uk + (int64_t)i0 * (WU + 1), rows * (WU + 1) * (int)sizeof(c2<T>), lane);
+            warp_copy16(Db + b * PCH, Dk + i0, rows * (int)sizeof(c2<T>), lane);
+            cp_async_commit();
+        };
+        issue_bwd(nc - 1, 0);
+        c2<T> acc = mk<T>(0, 0);
+        for (int q = 0; q < nc; q++) {
+            const int c = nc - 1 - q;
+            if (c > 0) {
+                issue_bwd(c - 1, (q + 1) & 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncwarp();
+            const c2<T>* Uc = Ub + (q & 1) * PCH * (WU + 1);
+            const c2<T>* Dc = Db + (q & 1) * PCH;
+            const int i0 = c * PCH, rows = min(PCH, n - i0);
+            for (int ii = rows - 1; ii >= 0; ii--) {
+                const int i = i0 + ii;
+                c2<T> ucur = (lane >= 1 && lane <= WU && i - lane >= 0) ? Uc[ii * (WU + 1) + lane] : mk<T>(0, 0);
+                c2<T> a0 = shfl2<T>(acc, 1);
+                c2<T> xi = mk<T>(0, 0);
+                if (lane == 0) {
+                    c2<T> zi = zs[i];
+                    xi = cm<T>(mk<T>(zi.x - a0.x, zi.y - a0.y), Dc[ii]);
+                    zs[i] = xi;
+                }
+                xi = shfl2<T>(xi, 0);
+                acc = shfl2_down<T>(acc, 1);
+                if (lane == WU) acc = mk<T>(0, 0);
+                if (lane >= 1 && lane <= WU) {
+                    acc.x += ucur.x * xi.x - ucur.y * xi.y;
+                    acc.y += ucur.x * xi.y + ucur.y * xi.x;
+                }
+            }
+            __syncwarp();
+        }
+        // result out, coalesced
+        c2<T>* zc = z + o;
+        for (int i = lane; i < n; i += 32) zc[i] = zs[i];
+    }
+    if (part_nrm) block_reduce_store(make_double2(0, 0), nsum, nullptr, part_nrm, blockIdx.x);
+}
+
+template <class T>
+size_t precond_sm_smem(int n1)
+{
+    return (size_t)prec_sm_warps<T>() * prec_sm_warp_bytes<T, 13>(2 * n1);
+}
+
+// The dynamic shared memory limit is a property of the kernel, shared by every operator in the
+// process: it is raised to the device's opt-in maximum (never lowered to one operator's need, which
+// would make a larger operator's launches fail), and an operator whose need exceeds it is refused.
+template <class T>
+cudaError_t precond_sm_prepare(int n1)
+{
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, k_precond_sm<T, 13>);
+    if (e != cudaSuccess) return e;
+    int lim = optin - (int)fa.sharedSizeBytes;   // static shared memory counts against the same limit
+    if (precond_sm_smem<T>(n1) > (size_t)lim) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(k_precond_sm<T, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+}
+
+template <class T>
+int precond_sm_blocks(int nch)
+{
+    return (nch + prec_sm_warps<T>() - 1) / prec_sm_warps<T>();
+}
+
+template <class T>
+void launch_precond_sm_t(cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv, int mode,
+                         const KState* ks, const void* r, const void* v, void* io, void* z, double* pn)
+{
+    int wb = (int)prec_sm_warp_bytes<T, 13>(2 * A.n1);
+    k_precond_sm<T, 13><<<precond_sm_blocks<T>(A.nch), 32 * prec_sm_warps<T>(), precond_sm_smem<T>(A.n1), st>>>(
+        A, (const c2<T>*)U, (const c2<T>*)L, (const c2<T>*)Dinv, mode, ks, (const c2<T>*)r, (const c2<T>*)v,
+        (c2<T>*)io, (c2<T>*)z, pn, wb);
+}
+template size_t precond_sm_smem<double>(int);
+template size_t precond_sm_smem<float>(int);
+template cudaError_t precond_sm_prepare<double>(int);
+template cudaError_t precond_sm_prepare<float>(int);
+template int precond_sm_blocks<double>(int);
+template int precond_sm_blocks<float>(int);
+template void launch_precond_sm_t<double>(cudaStream_t, const OpView&, const void*, const void*, const void*, int,
+                                          const KState*, const void*, const void*, void*, void*, double*);
+template void launch_precond_sm_t<float>(cudaStream_t, const OpView&, const void*, const void*, const void*, int,
+                                         const KState*, const void*, const void*, void*, void*, double*);
+
+// ---------------------------------------------------------------------------------------------
 // x += alpha ph + omega sh;  r = s - omega t;  partials <rh, r>, ||r||^2.  After the s-check ended
 // the solve (done == 2): x += alpha ph only.
 // ---------------------------------------------------------------------------------------------

@@ -49,8 +49,11 @@ struct dirac_op {
     // nparts_apply: 128-row tiles (FP64 apply, observables); nparts_own: the owner/gather passes
     int nparts_apply = 0, nparts_own = 0, nparts_vec = 0, nparts_prec = 0, nparts_prec32 = 0;
     int prec_warps = 0;          // same-kappa channel groups (lane-per-channel preconditioner)
-    bool prec_lanes = true;      // complex64 preconditioner schedule: one lane (else one warp) per channel
-    float prec_ms[2] = {0, 0};   // the setup's timing of the two schedules (lane, warp)
+    // preconditioner schedules, picked by timing at setup: 0 one lane per channel (complex64 only),
+    // 1 one warp per channel, 2 one warp per channel with shared-memory staging
+    int prec_sched32 = 0, prec_sched64 = 1;
+    bool prec_sm_ok = false;     // the staged kernel fits this radial size
+    float prec_ms32[3] = {0, 0, 0}, prec_ms64[3] = {0, 0, 0};
     int config_gen = 0;          // bumped when a launch choice changes (captured graphs are rebuilt)
     int *wks = nullptr, *wfirst = nullptr, *wcnt = nullptr;
     std::vector<void*> allocs;
@@ -113,6 +116,7 @@ int grid_for(int64_t n, int bs);
 void collect_phases(dirac_op* op);
 dirac_status check_launch(const char* what);
 int apply_parts(const dirac_op* op, const Krylov& K);   // partials of k_apply_launch on K
+int prec_parts(const dirac_op* op, const Krylov& K);    // partials of k_precond_launch on K
 void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void* y, const void* bsub,
                     const void* dv, double2* pdot, double* pnrm, const KState* skip);
 void launch_assemble(dirac_op* op);

@@ -88,3 +88,23 @@ def random_state(n, seed):
     """Seeded complex128 vector with standard-normal real and imaginary parts."""
     g = np.random.default_rng(seed)
     return g.standard_normal(n) + 1j * g.standard_normal(n)
+
+
+def guess_net_init(seed):
+    """Seeded initial parameters of the learned-guess network as one float32 array in the order
+    W1 [32][256], b1, W2 [256][256], b2, W3 [256][256], b3, W4 [256][4], b4: weights uniform in
+    +-1/sqrt(fan_in), the last layer scaled by 1e-2 (the untrained network starts near the
+    extrapolated guess), biases zero."""
+    g = np.random.default_rng(seed)
+    parts = []
+    for name, shp in (("W1", (32, 256)), ("b1", (256,)), ("W2", (256, 256)), ("b2", (256,)), ("W3", (256, 256)),
+                      ("b3", (256,)), ("W4", (256, 4)), ("b4", (4,))):
+        if name[0] == "b":
+            parts.append(np.zeros(shp))
+        else:
+            a = 1.0 / np.sqrt(shp[0])
+            w = g.uniform(-a, a, size=shp)
+            if name == "W4":
+                w = w * 1e-2
+            parts.append(w)
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
