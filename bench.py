@@ -124,6 +124,14 @@ def operator_counts(bas, cfg, kind):
 
 
 FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x max clock (GHz)
+
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of the owner passes from one ncu capture
+# on the medium workload (6944 pairs x 601 radial slots), scaled to the production launch by the
+# units processed (pairs x slots: x 9.817); the summaries under profiles/ give the commands and the
+# raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
+TRAFFIC_MEDIUM = {"df": (1.790703e9 + 0.154498e9, "profiles/k_residual_own_df_medium.md"),
+                  "f32": (0.886551e9 + 0.074471e9, "profiles/k_apply_own32_medium.md")}
+MEDIUM_UNITS = 6944 * 601
 DF_OPS_PER_FMA = 12                 # FP32 operations of one double-float multiply-add (TwoProd + TwoSum)
 
 
@@ -135,7 +143,15 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
     coup, flops, bytes_ = operator_counts(bas, cfg, kind)
     t = ms / cnt / 1000.0
     gbs = bytes_ / t / 1e9
-    out = {"phase": phase, "apply_ms": t * 1000.0, "bytes_per_apply": bytes_, "gbs": gbs, "traffic": None}
+    traffic, tnote = None, None
+    if kind in TRAFFIC_MEDIUM:
+        units = bas.npairs * (cfg["N"] + 1)
+        traffic = TRAFFIC_MEDIUM[kind][0] * units / MEDIUM_UNITS
+        tnote = ("owner pass only, from %s (medium capture) scaled by pairs x radial slots (x%.3f)" %
+                 (TRAFFIC_MEDIUM[kind][1], units / MEDIUM_UNITS))
+    out = {"phase": phase, "apply_ms": t * 1000.0, "bytes_per_apply": bytes_, "gbs": gbs, "traffic": traffic}
+    if tnote:
+        out["traffic_note"] = tnote
     if kind == "f64":
         tf = flops / t / 1e12
         out.update({"kernel": "k_apply<double> (FP64 operator apply)", "flops_per_apply": flops, "bound": "alu",
@@ -282,12 +298,11 @@ def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, pe
     t_data = time.time()
     for pc in L.pulse_variants(cfg, range(1000, 1000 + n_train)):
         tr = L.Trajectory(bas, pc, train_steps, precision=args.precision, tol=cfg["tol"])
-        x, t = L.samples(tr)
-        idx = torch.randint(0, x.shape[0], (min(x.shape[0], per_step * (train_steps - 4)),), device=dev,
-                            generator=g)
-        X.append(x[idx])
-        Tg.append(t[idx])
-        del tr, x, t
+        x, t, sc = L.samples(tr)
+        xs, ts = L.importance_subsample(x, t, sc, per_step * (train_steps - 4), g)
+        X.append(xs)
+        Tg.append(ts)
+        del tr, x, t, sc
         torch.cuda.empty_cache()
     X, Tg = torch.cat(X), torch.cat(Tg)
     n_samples = int(X.shape[0])
@@ -328,7 +343,8 @@ def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, pe
             "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "c64+f64", "c64+df64"][args.precision],
             "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, cfg) + "; learned initial guess, start at t=%.2f" % t0,
-                       "training": "%d seeded pulses x %d steps (extrapolated guess), %d samples, %d Adam steps of "
+                       "training": "%d seeded pulses x %d steps (extrapolated guess), %d samples drawn with "
+                                   "probability proportional to s^2, %d Adam steps of "
                                    "8192; data %.1f s, training %.1f s; loss %.3g -> %.3g" %
                                    (n_train, train_steps, n_samples, iters, t_data, t_train, losses[0], losses[-1])},
             "learned": res[2], "extrapolated": res[1], "speedup_vs_extrapolated": res[2]["value"] / res[1]["value"]}

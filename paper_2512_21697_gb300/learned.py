@@ -55,11 +55,12 @@ class Trajectory:
 
 
 def samples(traj):
-    """(X, T) float32 device tensors over every position of every step n >= 3 of a trajectory."""
+    """(X, T, S) float32 device tensors over every position of every step n >= 3 of a trajectory:
+    features, targets and the positions' scales s (positions with s = 0 are left out)."""
     import torch
     bas, cfg, st = traj.bas, traj.cfg, traj.states
     npos = bas.nch * (cfg["N"] + 1)
-    xs, ts = [], []
+    xs, ts, ss = [], [], []
     for n in range(3, len(st) - 1):
         x = torch.empty((npos, 32), dtype=torch.float32, device="cuda")
         s = torch.empty(npos, dtype=torch.float32, device="cuda")
@@ -70,7 +71,19 @@ def samples(traj):
         keep = s > 0
         xs.append(x[keep])
         ts.append(tg[keep])
-    return torch.cat(xs), torch.cat(ts)
+        ss.append(s[keep])
+    return torch.cat(xs), torch.cat(ts), torch.cat(ss)
+
+
+def importance_subsample(X, T, S, k, generator):
+    """k samples drawn with probability proportional to s^2: the squared guess error of a position is
+    s^2 |out - target|^2, so plain mean squared error over these samples is the relative guess
+    error the solver sees (positions whose amplitude is at the solver's noise level, where the
+    normalised target is large and random, carry their true, negligible weight)."""
+    import torch
+    w = S.double() ** 2
+    idx = torch.multinomial(w / w.sum(), k, replacement=True, generator=generator)
+    return X[idx].contiguous(), T[idx].contiguous()
 
 
 def train(net, X, T, steps, batch=4096, lr=1e-3, seed=0, log_every=0):

@@ -127,13 +127,16 @@ def test_trained_network_beats_extrapolation_on_heldout_pulses():
     bas = B.Basis(base)
     train_cfgs = L.pulse_variants(base, range(1000, 1024))
     test_cfgs = L.pulse_variants(base, range(2000, 2004))
-    X, T = [], []
+    X, T, S = [], [], []
     for cfg in train_cfgs:
         tr = L.Trajectory(bas, cfg, 16)
-        x, t = L.samples(tr)
+        x, t, sc = L.samples(tr)
         X.append(x)
         T.append(t)
-    X, T = torch.cat(X), torch.cat(T)
+        S.append(sc)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    X, T = L.importance_subsample(torch.cat(X), torch.cat(T), torch.cat(S), 400000, g)
     net = B.GuessNet(4096, G.flatten(G.init_params(7)))
     losses = L.train(net, X, T, 800, batch=4096, lr=1e-3, seed=1)
     assert losses[-1] < 0.5 * losses[0]
