@@ -189,6 +189,23 @@ def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
     return outs[dom], outs.get("apply32")
 
 
+def max_over_ranks(ms, dist=None, device=None):
+    """The slowest rank's time (all ranks run the same replica workload; the job takes the longest)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(steps, ms, world):
+    """(per-replica steps/s, whole-job steps/s): N independent replicas each advance `steps` steps
+    in the slowest rank's time."""
+    sps = steps / (ms / 1000.0)
+    return sps, sps * world
+
+
 def fp64_compare(bas, cfg, psi0_h, t0, args, stream, dev):
     """Plain FP64 BiCGSTAB on the same steps from the same state, to the same tolerance."""
     import numpy as np
@@ -330,13 +347,17 @@ def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, pe
         tcur = t0 + (args.warmup + 3) * cfg["dt"]
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        op.profile(True)
         ev0.record(stream)
         its, rr, _ = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
         ev1.record(stream)
         torch.cuda.synchronize()
+        phase_ms, phase_n, _ = op.profile_read()
+        op.profile(False)
         ms = ev0.elapsed_time(ev1)
         res[guess] = {"value": args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
-                      "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(rr))}
+                      "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(rr)),
+                      "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()}}
         del op
     line = {"metric": METRIC, "value": res[2]["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res[2]["ms_per_step"], "higher_is_better": True,
@@ -352,69 +373,136 @@ def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, pe
         print(json.dumps(line), flush=True)
 
 
-def batch_bench(args, world, rank, local, dist):
-    """Batched workload: independent instances (own pulse and radial size) stepped concurrently by
-    dirac_solve_batch with the window and preconditioner schedule picked by dirac_batch_tune.
-    Value: instance-steps per second.  Instances are added only while the free device memory stays
-    above 1.5x the largest instance seen so far plus 24 GB."""
-    import concurrent.futures as cf
-    import numpy as np
-    import torch
-    from paper_2512_21697_gb300 import binding as B, workloads as W
-    dev = torch.device("cuda", local)
-    cfgs = W.batch_instances(args.batch_n, seed0=0)
-    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
-        bases = list(ex.map(B.Basis, cfgs))
-    ops, psis, hists, used = [], [], [], []
+def _batch_ops(B, torch, cfgs, bases, dev, precision, guess):
+    """Operators for as many instances as the free device memory allows (1.5x the largest instance
+    seen so far plus 24 GB must stay free), each on its own stream."""
+    ops, used = [], []
     biggest = 0
-    t_setup = time.time()
     for cfg, bas in zip(cfgs, bases):
         free, _ = torch.cuda.mem_get_info(dev)
         if biggest and free < 1.5 * biggest + 24e9:
             break
-        st = torch.cuda.Stream()
-        op = B.Operator(bas, cfg, stream=st, tol=cfg["tol"], precision=args.precision, max_iter=1000,
-                        tol_inner=1e-5, max_outer=20)
+        op = B.Operator(bas, cfg, stream=torch.cuda.Stream(), tol=cfg["tol"], precision=precision, max_iter=1000,
+                        tol_inner=1e-5, max_outer=20, guess=guess)
         biggest = max(biggest, op.device_bytes())
-        psi0, _ = bas.initial_state()
         ops.append(op)
-        psis.append(torch.from_numpy(psi0).to(dev))
-        hists.append(torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev))
-        used.append(cfg)
-    torch.cuda.synchronize()
-    t_setup = time.time() - t_setup
-    t0s = [0.0] * len(ops)
-    cand = [w for w in (1, 4, 8, 16, 0) if w <= len(ops)]
-    best, ms = B.batch_tune(ops, psis, hists, t0s, cand)
+        used.append((cfg, bas))
+    return ops, used
+
+
+def _batch_time(B, torch, ops, used, dev, args, t0s, window, hist_len):
+    """Warm-up steps (they also fill the history), then the timed batch call: (wall seconds,
+    iterations, residuals)."""
+    psis = [torch.from_numpy(bas.initial_state()[0]).to(dev) for _, bas in used]
+    hists = [torch.zeros(hist_len * bas.n, dtype=torch.complex128, device=dev) for _, bas in used]
     nh = [0] * len(ops)
-    _, _, nh = B.solve_batch(ops, psis, hists, args.warmup, t0s, n_hist=nh, window=best)
-    tcur = [args.warmup * c["dt"] for c in used]
-    clocks = ClockSampler(local)
-    clocks.start()
+    _, _, nh = B.solve_batch(ops, psis, hists, args.warmup, t0s, n_hist=nh, window=window)
+    tcur = [t + args.warmup * c["dt"] for t, (c, _) in zip(t0s, used)]
     torch.cuda.synchronize()
     w0 = time.perf_counter()
-    its, res, nh = B.solve_batch(ops, psis, hists, args.steps, tcur, n_hist=nh, window=best)
+    its, res, nh = B.solve_batch(ops, psis, hists, args.steps, tcur, n_hist=nh, window=window)
     torch.cuda.synchronize()
-    wall = time.perf_counter() - w0
-    ck = clocks.stop()
+    return time.perf_counter() - w0, its, res
+
+
+def batch_bench(args, world, rank, local, dist):
+    """Batched workload: independent instances (own pulse and radial size) stepped concurrently by
+    dirac_solve_batch with the window and preconditioner schedule picked by dirac_batch_tune.
+    Value: instance-steps per second of the mixed-precision batch (with --learned: with the learned
+    guess, trained first on trajectories of the batch's own instances, and the instances start at
+    their peak field).  Beside it, unless --no-fp64-compare: the same instances in plain FP64."""
+    import concurrent.futures as cf
+    import math
+    import numpy as np
+    import torch
+    from paper_2512_21697_gb300 import binding as B, learned as L, workloads as W
+    dev = torch.device("cuda", local)
+    cfgs = W.batch_instances(args.batch_n, seed0=0)
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        bases = list(ex.map(B.Basis, cfgs))
+    peak = args.learned or args.t0 is not None
+    t_setup = time.time()
+    ops, used = _batch_ops(B, torch, cfgs, bases, dev, args.precision, 2 if args.learned else 1)
+    torch.cuda.synchronize()
+    t_setup = time.time() - t_setup
     n_inst = len(ops)
-    value = n_inst * args.steps / wall * world
+    T = [c["n_cycles"] * 2 * math.pi / c["omega"] for c, _ in used]
+    t0s = [0.5 * t for t in T] if peak else [0.0] * n_inst
+    # schedule autotuner on the starting states
+    psis = [torch.from_numpy(bas.initial_state()[0]).to(dev) for _, bas in used]
+    hists = [torch.zeros(3 * bas.n, dtype=torch.complex128, device=dev) for _, bas in used]
+    cand = [w for w in (1, 4, 8, 16, 0) if w <= n_inst]
+    best, tune_ms = B.batch_tune(ops, psis, hists, t0s, cand)
+    del psis, hists
+    out = {}
+    clocks = ClockSampler(local)
+    clocks.start()
+    wall, its, res = _batch_time(B, torch, ops, used, dev, args, t0s, best, 3)
+    ck = clocks.stop()
+    out["mixed"] = {"value": n_inst * args.steps / wall * world, "iters_per_step": float(np.mean(its)),
+                    "max_resid": float(np.max(res))}
+    train_note = None
+    if args.learned:
+        # training data: trajectories of the first instances at seeded times inside their pulses
+        g = torch.Generator(device=dev)
+        g.manual_seed(0)
+        X, Tg = [], []
+        t_train = time.time()
+        for i in range(min(8, n_inst)):
+            cfg, bas = used[i]
+            u = float(np.random.default_rng(1000 + i).uniform(0.1, 0.9))
+            pc = dict(cfg, t_start=u * T[i])   # the instance's own pulse, at a seeded time
+            tr = L.Trajectory(bas, pc, 10, precision=args.precision, tol=cfg["tol"])
+            x, t, sc = L.samples(tr)
+            xs, ts = L.importance_subsample(x, t, sc, 262144, g)
+            X.append(xs)
+            Tg.append(ts)
+            del tr, x, t, sc
+        X, Tg = torch.cat(X), torch.cat(Tg)
+        net = B.GuessNet(8192, W.guess_net_init(7))
+        losses = L.train(net, X, Tg, 1500, batch=8192, lr=1e-3, seed=1)
+        torch.cuda.synchronize()
+        t_train = time.time() - t_train
+        train_note = "8 instances x 10 steps at seeded times, %d samples (p ~ s^2), 1500 Adam steps; %.1f s; loss " \
+                     "%.3g -> %.3g" % (X.shape[0], t_train, losses[0], losses[-1])
+        del X, Tg
+        for op in ops:
+            B.set_guess(op, net)
+        wall_l, its_l, res_l = _batch_time(B, torch, ops, used, dev, args, t0s, best, 3)
+        out["mixed_learned"] = {"value": n_inst * args.steps / wall_l * world, "iters_per_step": float(np.mean(its_l)),
+                                "max_resid": float(np.max(res_l))}
+    del ops
+    torch.cuda.empty_cache()
+    if not args.no_fp64_compare:
+        ops64, used64 = _batch_ops(B, torch, [c for c, _ in used], [b for _, b in used], dev, 0, 1)
+        n64 = len(ops64)
+        t064 = t0s[:n64]
+        wall64, its64, res64 = _batch_time(B, torch, ops64, used64, dev, args, t064, best, 2)
+        out["fp64"] = {"value": n64 * args.steps / wall64 * world, "instances": n64,
+                       "iters_per_step": float(np.mean(its64)), "max_resid": float(np.max(res64))}
+        del ops64
+    head = out.get("mixed_learned", out["mixed"])
     line = {
-        "metric": METRIC, "value": value, "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": wall * 1000.0 / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": head["value"], "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": n_inst * 1000.0 / head["value"] * world, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "c64+f64", "c64+df64"][args.precision],
         "data": "synthetic",
         "config": {"workload": "batch: %d instances (of %d requested), E0 log-uniform [0.02, 0.2], wavelength "
                                "[400, 1600] nm, 2-6 cycles, N 400-1000, |kappa|<=20, l<=2, R=300, dt=0.005, "
-                               "tol=1e-10" % (n_inst, args.batch_n),
-                   "unknowns": int(sum(o.n for o in ops)), "window": best,
-                   "precond_schedule": "tuned (lane or warp per channel)",
-                   "tune_ms": {"windows": cand, "lanes": ms[0].tolist(), "warps": ms[1].tolist()},
+                               "tol=1e-10, start %s" % (n_inst, args.batch_n, "at each instance's peak field"
+                                                        if peak else "at the pulse start"),
+                   "unknowns": int(sum(b.n for _, b in used)), "window": best,
+                   "precond_schedule": "tuned (lane or staged warp per channel)",
+                   "tune_ms": {"windows": cand, "lanes": tune_ms[0].tolist(), "staged_warps": tune_ms[1].tolist()},
                    "setup_s": t_setup, "timing": "host wall clock around the batch call (many streams)",
                    "parallelism": "replicas x%d" % world},
-        "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)),
+        "batch": out,
         "clocks": ck,
     }
+    if train_note:
+        line["config"]["training"] = train_note
+    if "fp64" in out:
+        line["speedup_vs_fp64"] = head["value"] / out["fp64"]["value"]   # instance-steps/s against instance-steps/s
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -481,12 +569,8 @@ def main():
     phase_ms, phase_n, launches = op.profile_read()
     op.profile(False)
     tcur += args.steps * cfg["dt"]
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    sps = args.steps / (ms / 1000.0)
-    value = sps * world
+    ms = max_over_ranks(ms, dist, dev)
+    sps, value = replica_rate(args.steps, ms, world)
 
     # end to end through the C ABI with host buffers: H2D of the state, K steps, D2H of the result
     psi_h = torch.from_numpy(psi0_h).pin_memory()

@@ -135,7 +135,8 @@ dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist
 /* dirac_step as one captured CUDA graph: the time loop, the solve restarts and the BiCGSTAB
  * iterations are conditional WHILE nodes whose conditions the device sets from the solver state,
  * so n_steps run with no host round trip (same arithmetic, kernel sequence and results as
- * dirac_step).  hist_dev (device complex128[2n]) is required; n_hist as in dirac_step.  The graph
+ * dirac_step).  hist_dev (device complex128[2n], [3n] with the learned guess) is required; n_hist
+ * as in dirac_step.  The graph
  * is captured on the first call and re-captured when psi_dev or hist_dev changes or n_steps grows
  * beyond the previous capacity (at least 256).  Same outputs and errors as dirac_step. */
 dirac_status dirac_run(dirac_op* op, void* psi_dev, void* hist_dev, int* n_hist, int n_steps,
@@ -189,13 +190,15 @@ dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, vo
  * number of kernel launches since the reset (counted whether or not timing is on).
  * Phases: DIRAC_PHASE_ASSEMBLE (pulse factors + coupling values), DIRAC_PHASE_APPLY (double
  * precision operator products), DIRAC_PHASE_PRECOND, DIRAC_PHASE_VECTOR (updates, reductions,
- * copies), DIRAC_PHASE_APPLY32 (complex64 operator products of the mixed-precision inner solve). */
+ * copies), DIRAC_PHASE_APPLY32 (complex64 operator products of the mixed-precision inner solve),
+ * DIRAC_PHASE_GUESS (the learned initial guess: features, network, correction). */
 #define DIRAC_PHASE_ASSEMBLE 0
 #define DIRAC_PHASE_APPLY 1
 #define DIRAC_PHASE_PRECOND 2
 #define DIRAC_PHASE_VECTOR 3
 #define DIRAC_PHASE_APPLY32 4
-#define DIRAC_NPHASE 5
+#define DIRAC_PHASE_GUESS 5
+#define DIRAC_NPHASE 6
 dirac_status dirac_profile(dirac_op* op, int enable);
 dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches);
 
@@ -257,8 +260,9 @@ dirac_status dirac_guess_train_step(dirac_guess* net, const float* x_dev, const 
                                     double* loss, void* stream);
 /* Attach a network (not owned; NULL detaches) to an op: dirac_step with solver option guess = 2 then
  * starts each step from the network's guess once three past states are in the history, which must
- * then hold 3 n entries (psi_{n-1}, psi_{n-2}, psi_{n-3}; n_hist up to 3); before that, and in
- * dirac_run / dirac_solve_batch, the extrapolated guess is used. */
+ * then hold 3 n entries (psi_{n-1}, psi_{n-2}, psi_{n-3}; n_hist up to 3); before that the
+ * extrapolated guess is used.  dirac_run and dirac_solve_batch do the same inside the captured
+ * graph (their history buffers then hold 3 n entries too); results equal dirac_step's bit for bit. */
 dirac_status dirac_op_set_guess(dirac_op* op, dirac_guess* net);
 
 /* Overlapped assembly (precision 2 only; no counterpart in the paper, a scheduling choice): with

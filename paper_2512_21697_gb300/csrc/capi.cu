@@ -1051,8 +1051,8 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
             PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
             double2* x = (double2*)K.x;
             if (learned && nh >= 3) {
-                double t_next = t_start + (double)(step + 1) * o.dt;
-                dirac_status ge = guess_into(op, psi, h1, h2, h3, t_next, x);
+                PhaseScope pg(op, DIRAC_PHASE_GUESS, 0);   // guess_into counts its launches
+                dirac_status ge = guess_into(op, psi, h1, h2, h3, t_start, step, x, nullptr, op->st, nullptr);
                 if (ge) return ge;
             } else {
                 k_extrapolate<<<npv, 256, 0, op->st>>>(n, o.guess >= 1 ? std::min(nh, 2) : 0, psi, h1, h2, x);

@@ -23,7 +23,8 @@ namespace dg {
 struct StepCtl {
     double t_start, dt, t_off;   // evaluation time of step s: t_start + s dt + t_off
     int step, n_steps;
-    int hist_n;                  // valid history entries (0..2)
+    int hist_n;                  // valid history entries (0..hist_max)
+    int hist_max;                // 2, or 3 with the learned guess
     int status;                  // first failing status, 0 while all steps succeed
     int accepted, restarts, outer, total_it;
     int max_restarts, max_outer;
@@ -57,15 +58,24 @@ __global__ void k_ctl_begin_step(StepCtl* c, double* t_eval, cudaGraphConditiona
     cudaGraphSetConditional(h_solve, 1);
 }
 
-// x = extrapolated guess from psi and the valid history (guess option 1), else psi
+// x = extrapolated guess from psi and the valid history (guess option >= 1), else psi; skipped when
+// the learned guess produced x this step (*skip set)
 __global__ void k_guess(const StepCtl* c, int use_hist, int64_t n, const double2* psi, const double2* h1,
-                        const double2* h2, double2* x)
+                        const double2* h2, double2* x, const int* skip)
 {
+    if (skip && *skip) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int nh = use_hist ? c->hist_n : 0;
+    int nh = use_hist ? min(c->hist_n, 2) : 0;
     double2 p = psi[i], a = nh >= 1 ? h1[i] : p, b = nh >= 2 ? h2[i] : p;
     x[i] = make_double2(extrapolate(nh, p.x, a.x, b.x), extrapolate(nh, p.y, a.y, b.y));
+}
+
+// learned guess of this step: field factors at t_start + (step + 1) dt, and the gate (three past states)
+__global__ void k_ctl_guess_prep(const StepCtl* c, PulseView P, float* F, int* gate)
+{
+    guess_field_at(P, next_time(c->t_start, c->step, c->dt), F);
+    *gate = c->hist_n >= 3 ? 1 : 0;
 }
 
 // after r = b - A x: accept on the true residual, else iterate
@@ -148,14 +158,15 @@ __global__ void k_ctl_end_step(StepCtl* c, const KState* ks, int* its, double* r
     int s = c->step;
     its[s] = c->total_it;
     res[s] = sqrt(ks->rnorm2 / (ks->bnorm2 > 0 ? ks->bnorm2 : 1.0));
-    c->hist_n = c->hist_n < 2 ? c->hist_n + 1 : 2;
+    c->hist_n = c->hist_n < c->hist_max ? c->hist_n + 1 : c->hist_max;
     c->step = s + 1;
     cudaGraphSetConditional(h_step, (c->step < c->n_steps && c->status == 0) ? 1 : 0);
 }
 
-__global__ void k_copy_if_hist(const StepCtl* c, int64_t n, const double2* a, double2* b)
+// b = a when at least `need` history entries are valid
+__global__ void k_copy_if_hist(const StepCtl* c, int need, int64_t n, const double2* a, double2* b)
 {
-    if (c->hist_n < 1) return;
+    if (c->hist_n < need) return;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) b[i] = a[i];
 }
@@ -331,7 +342,14 @@ static dirac_status build_graph(dirac_op* op, GraphDriver* gd, double2* psi, dou
                 rhs_accurate(op, psi);
             }
             int npv = op->nparts_vec;
-            k_guess<<<npv, 256, 0, s1>>>(gd->ctl, o.guess >= 1, op->n, psi, h1, h2, (double2*)K.x);
+            const bool learned = o.guess == 2 && op->net;
+            if (learned) {
+                k_ctl_guess_prep<<<1, 1, 0, s1>>>(gd->ctl, op->pv, op->gfield, op->ggate);
+                e1 = guess_into(op, psi, h1, h2, h1 + 2 * op->n, 0.0, 0, (double2*)K.x, op->ggate, s1, op->gfield);
+                if (e1) return e1;
+            }
+            k_guess<<<npv, 256, 0, s1>>>(gd->ctl, o.guess >= 1, op->n, psi, h1, h2, (double2*)K.x,
+                                         learned ? op->ggate : nullptr);
             cudaGraph_t solve_body;
             e1 = add_cond(s1, h_solve, cudaGraphCondTypeWhile, &solve_body);
             if (e1) return e1;
@@ -339,7 +357,8 @@ static dirac_status build_graph(dirac_op* op, GraphDriver* gd, double2* psi, dou
                 return o.precision == 0 ? fill_solve64(op, gd, s2, h_solve) : fill_refine(op, gd, s2, h_solve, psi);
             });
             if (e1) return e1;
-            k_copy_if_hist<<<npv, 256, 0, s1>>>(gd->ctl, op->n, h1, h2);
+            if (learned) k_copy_if_hist<<<npv, 256, 0, s1>>>(gd->ctl, 2, op->n, h2, h1 + 2 * op->n);
+            k_copy_if_hist<<<npv, 256, 0, s1>>>(gd->ctl, 1, op->n, h1, h2);
             k_copy64<<<npv, 256, 0, s1>>>(op->n, psi, h1);
             k_copy64<<<npv, 256, 0, s1>>>(op->n, (const double2*)K.x, psi);
             k_ctl_end_step<<<1, 1, 0, s1>>>(gd->ctl, K.ks, gd->its, gd->res, h_step);
@@ -415,7 +434,8 @@ dirac_status run_launch(dirac_op* op, double2* psi, double2* h1, int n_hist, int
     c.dt = o.dt;
     c.t_off = o.time_eval ? o.dt : 0.5 * o.dt;
     c.n_steps = n_steps;
-    c.hist_n = std::max(0, std::min(2, n_hist));
+    c.hist_max = (o.guess == 2 && op->net) ? 3 : 2;
+    c.hist_n = std::max(0, std::min(c.hist_max, n_hist));
     c.max_restarts = 8;
     c.max_outer = o.max_outer;
     k_set_ctl<<<1, 1, 0, op->st>>>(gd->ctl, c);

@@ -58,20 +58,11 @@ namespace dg {
 // ------------------------------------------------------------------------------------------
 // features and the guess
 // ------------------------------------------------------------------------------------------
-struct GuessField {
-    float f[6];
-};
-
-GuessField guess_field(const dirac_op* op, double t)
+// field factors at t_next = t_start + (step + 1) dt (step >= 0), or at t_start itself (step < 0)
+__global__ void k_guess_field(PulseView P, double t_start, int step, double dt, float* F)
 {
-    GuessField g{};
-    double tt = t - op->pv.t0;
-    if (tt >= 0 && tt <= op->pv.T)
-        for (int c = 0; c < 3; c++) {
-            g.f[2 * c] = (float)(op->pv.amp * op->pv.wt[c] * std::sin(op->pv.w[c] * tt));
-            g.f[2 * c + 1] = (float)(op->pv.amp * op->pv.wt[c] * std::cos(op->pv.w[c] * tt));
-        }
-    return g;
+    if (threadIdx.x || blockIdx.x) return;
+    guess_field_at(P, step >= 0 ? next_time(t_start, step, dt) : t_start, F);
 }
 
 // one thread per position (channel, radial slot): backward differences D_0..D_3 of the four
@@ -79,9 +70,11 @@ GuessField guess_field(const dirac_op* op, double t)
 // s = m_3
 __global__ void k_guess_features(int nch, int n1, const int* __restrict__ kappa, const int* __restrict__ two_mu,
                                  const double2* __restrict__ p0, const double2* __restrict__ p1,
-                                 const double2* __restrict__ p2, const double2* __restrict__ p3, GuessField F,
-                                 float* __restrict__ X, float* __restrict__ S)
+                                 const double2* __restrict__ p2, const double2* __restrict__ p3,
+                                 const float* __restrict__ F, float* __restrict__ X, float* __restrict__ S,
+                                 const int* gate)
 {
+    if (gate && !*gate) return;   // uniform: the graph's step has too few past states
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= (int64_t)nch * n1) return;
     int ch = (int)(pos / n1);
@@ -111,7 +104,7 @@ __global__ void k_guess_features(int nch, int n1, const int* __restrict__ kappa,
         if (m[j] > 0 && m[3] > 0) v = fmin(30.0, fmax(-30.0, log10(m[j] / m[3]))) / 10.0;
         x[16 + j] = (float)v;
     }
-    for (int i = 0; i < 6; i++) x[19 + i] = F.f[i];
+    for (int i = 0; i < 6; i++) x[19 + i] = F[i];
     x[25] = (float)kappa[ch] / 10.f;
     x[26] = (float)two_mu[ch] / 20.f;
     for (int i = 27; i < GN_IN; i++) x[i] = 0.f;
@@ -143,8 +136,9 @@ __global__ void k_guess_targets(int64_t npos, const double2* __restrict__ p0, co
 // x = x_ext + s * out
 __global__ void k_guess_apply(int64_t npos, const double2* __restrict__ p0, const double2* __restrict__ p1,
                               const double2* __restrict__ p2, const float* __restrict__ S,
-                              const float* __restrict__ out, double2* __restrict__ x)
+                              const float* __restrict__ out, double2* __restrict__ x, const int* gate)
 {
+    if (gate && !*gate) return;
     int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (pos >= npos) return;
     double s = S[pos];
@@ -369,28 +363,53 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, const uint
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// One 256 -> 256 layer for the warp's 16 rows, output columns [n0, n0 + 128): acc[16][4].
-// act: [FT_M][FT_AST] bf16 (input), wch: chunk buffer [2][FT_KC][FT_WST]; W: global bf16 [256][256]
-__device__ __forceinline__ void ft_load_chunk(__nv_bfloat16* dst, const __nv_bfloat16* W, int k0)
+// Fragments come from shared memory through ldmatrix (A: 16 x 16 activation tiles; B: the weight
+// chunk [k][n] read transposed, two 8-column tiles at a time); weight chunks arrive by cp.async one
+// chunk ahead of the chunk being multiplied.
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p)
 {
-    // 32 rows x 256 bf16 = 16 KB, 16 bytes per thread-iteration
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void ldsm_x4_trans(uint32_t* r, const void* p)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)));
+}
+__device__ __forceinline__ void cpa16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cpa_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// FT_KC weight rows [k0, k0 + FT_KC) of a 256-wide bf16 matrix into a chunk buffer, asynchronously
+__device__ __forceinline__ void ft_load_chunk_async(__nv_bfloat16* dst, const __nv_bfloat16* W, int k0)
+{
     for (int e = threadIdx.x; e < FT_KC * GN_H / 8; e += blockDim.x) {
         int r = e / (GN_H / 8), c8 = e % (GN_H / 8);
-        *reinterpret_cast<uint4*>(dst + r * FT_WST + c8 * 8) =
-            *reinterpret_cast<const uint4*>(W + (int64_t)(k0 + r) * GN_H + c8 * 8);
+        cpa16(dst + r * FT_WST + c8 * 8, W + (int64_t)(k0 + r) * GN_H + c8 * 8);
     }
+    cpa_commit();
 }
 
 __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float* __restrict__ X,
                                                           const __nv_bfloat16* __restrict__ wb,
-                                                          const float* __restrict__ wr, float* __restrict__ out)
+                                                          const float* __restrict__ wr, float* __restrict__ out,
+                                                          const int* gate)
 {
+    if (gate && !*gate) return;
     extern __shared__ __align__(16) unsigned char ft_smem[];
     __nv_bfloat16* actA = reinterpret_cast<__nv_bfloat16*>(ft_smem);
     __nv_bfloat16* actB = actA + FT_M * FT_AST;
     __nv_bfloat16* wch = actB + FT_M * FT_AST;   // [2][FT_KC][FT_WST]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int g = lane >> 2, tq = lane & 3;       // mma fragment coordinates
+    const int mi = lane >> 3, r8 = lane & 7;      // ldmatrix: matrix and row this lane addresses
     const int64_t m0 = (int64_t)blockIdx.x * FT_M;
     const __nv_bfloat16* W1 = wb;
     const __nv_bfloat16* W2 = wb + GN_IN * GN_H;
@@ -400,34 +419,24 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
     const float* b2 = wr + GO_B2;
     const float* b3 = wr + GO_B3;
     const float* b4 = wr + GO_B4;
-    // stage X (bf16) into actB columns 0..31 and W1 (32 x 256) into the chunk buffer 0
+    ft_load_chunk_async(wch, W1, 0);   // W1 is one chunk (32 rows)
+    // stage X (bf16) into actB columns 0..31
     for (int e = threadIdx.x; e < FT_M * GN_IN; e += blockDim.x) {
         int r = e / GN_IN, c = e % GN_IN;
         int64_t gm = m0 + r;
         float v = gm < M ? X[gm * GN_IN + c] : 0.f;
         actB[r * FT_AST + c] = __float2bfloat16_rn(v);
     }
-    ft_load_chunk(wch, W1, 0);
+    cpa_wait0();
     __syncthreads();
     const int rw = warp * 16;   // the warp's rows
-    // A fragment loader from an activation buffer: rows rw + g (+8), k pair kk + 2 tq (+8)
+    // A fragments of rows rw .. rw + 15, columns kk .. kk + 15
     auto load_a = [&](const __nv_bfloat16* act, int kk, uint32_t* a) {
-        const __nv_bfloat16* r0p = act + (rw + g) * FT_AST + kk + 2 * tq;
-        const __nv_bfloat16* r1p = act + (rw + g + 8) * FT_AST + kk + 2 * tq;
-        a[0] = *reinterpret_cast<const uint32_t*>(r0p);
-        a[1] = *reinterpret_cast<const uint32_t*>(r1p);
-        a[2] = *reinterpret_cast<const uint32_t*>(r0p + 8);
-        a[3] = *reinterpret_cast<const uint32_t*>(r1p + 8);
+        ldsm_x4(a, act + (rw + (mi & 1) * 8 + r8) * FT_AST + kk + (mi >> 1) * 8);
     };
-    // B fragment from a weight chunk [k][n] (row-major in k): k = kk + 2 tq (+1, +8, +9), n = n0 + g
-    auto load_b = [&](const __nv_bfloat16* w, int kk, int n, uint32_t* b) {
-        __nv_bfloat162 p0, p1;
-        p0.x = w[(kk + 2 * tq) * FT_WST + n];
-        p0.y = w[(kk + 2 * tq + 1) * FT_WST + n];
-        p1.x = w[(kk + 2 * tq + 8) * FT_WST + n];
-        p1.y = w[(kk + 2 * tq + 9) * FT_WST + n];
-        b[0] = *reinterpret_cast<uint32_t*>(&p0);
-        b[1] = *reinterpret_cast<uint32_t*>(&p1);
+    // B fragments of two 8-column tiles n0 .. n0 + 15 for k = kk .. kk + 15 of a chunk [k][n]
+    auto load_b2 = [&](const __nv_bfloat16* w, int kk, int n0, uint32_t* b) {
+        ldsm_x4_trans(b, w + (kk + (mi & 1) * 8 + r8) * FT_WST + n0 + (mi >> 1) * 8);
     };
     // layer 1: actB[:, 0:32] x W1 -> tanh -> actA
     for (int half = 0; half < 2; half++) {
@@ -437,10 +446,11 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
         for (int kk = 0; kk < GN_IN; kk += 16) {
             uint32_t a[4];
             load_a(actB, kk, a);
-            for (int j = 0; j < 16; j++) {
-                uint32_t b[2];
-                load_b(wch, kk, half * 128 + j * 8 + g, b);
+            for (int j = 0; j < 16; j += 2) {
+                uint32_t b[4];
+                load_b2(wch, kk, half * 128 + j * 8, b);
                 mma_bf16(acc[j], a, b);
+                mma_bf16(acc[j + 1], a, b + 2);
             }
         }
         for (int j = 0; j < 16; j++) {
@@ -453,7 +463,8 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
         }
     }
     __syncthreads();
-    // layers 2 and 3: in -> out, weights streamed in FT_KC-row chunks
+    // layers 2 and 3: in -> out, weights streamed in FT_KC-row chunks, one chunk ahead
+    constexpr int NCH = GN_H / FT_KC;
     for (int layer = 0; layer < 2; layer++) {
         const __nv_bfloat16* W = layer == 0 ? W2 : W3;
         const float* bias = layer == 0 ? b2 : b3;
@@ -463,21 +474,27 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
             float acc[16][4];
             for (int j = 0; j < 16; j++)
                 for (int q = 0; q < 4; q++) acc[j][q] = 0.f;
-            ft_load_chunk(wch, W, 0);
-            __syncthreads();
-            for (int c = 0; c < GN_H / FT_KC; c++) {
-                __nv_bfloat16* cur = wch + (c & 1) * FT_KC * FT_WST;
-                if (c + 1 < GN_H / FT_KC) ft_load_chunk(wch + ((c + 1) & 1) * FT_KC * FT_WST, W, (c + 1) * FT_KC);
+            ft_load_chunk_async(wch, W, 0);
+            for (int c = 0; c < NCH; c++) {
+                if (c + 1 < NCH) {
+                    ft_load_chunk_async(wch + ((c + 1) & 1) * FT_KC * FT_WST, W, (c + 1) * FT_KC);
+                    cpa_wait1();
+                } else {
+                    cpa_wait0();
+                }
+                __syncthreads();
+                const __nv_bfloat16* cur = wch + (c & 1) * FT_KC * FT_WST;
                 for (int kk = 0; kk < FT_KC; kk += 16) {
                     uint32_t a[4];
                     load_a(in, c * FT_KC + kk, a);
-                    for (int j = 0; j < 16; j++) {
-                        uint32_t b[2];
-                        load_b(cur, kk, half * 128 + j * 8 + g, b);
+                    for (int j = 0; j < 16; j += 2) {
+                        uint32_t b[4];
+                        load_b2(cur, kk, half * 128 + j * 8, b);
                         mma_bf16(acc[j], a, b);
+                        mma_bf16(acc[j + 1], a, b + 2);
                     }
                 }
-                __syncthreads();
+                __syncthreads();   // buffer (c & 1) is refilled two chunks later
             }
             for (int j = 0; j < 16; j++) {
                 int cidx = half * 128 + j * 8 + 2 * tq;
@@ -657,10 +674,13 @@ extern "C" dirac_status dirac_guess_features(dirac_op* op, const void* const* st
     for (int k = 0; k < 4; k++)
         if (!states[k]) { set_error("dirac_guess_features: NULL state"); return DIRAC_E_ARG; }
     int64_t npos = (int64_t)op->ov.nch * op->ov.n1;
+    dirac_status fe = guess_buffers(op);
+    if (fe) return fe;
+    k_guess_field<<<1, 1, 0, op->st>>>(op->pv, t_next, -1, 0.0, op->gfield);
     k_guess_features<<<(unsigned)((npos + 255) / 256), 256, 0, op->st>>>(
         op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, (const double2*)states[0], (const double2*)states[1],
-        (const double2*)states[2], (const double2*)states[3], guess_field(op, t_next), x_dev, s_dev);
-    op->launches++;
+        (const double2*)states[2], (const double2*)states[3], op->gfield, x_dev, s_dev, nullptr);
+    op->launches += 2;
     return check_launch("dirac_guess_features");
 }
 
@@ -686,8 +706,8 @@ extern "C" dirac_status dirac_guess_forward(dirac_guess* g, const float* x_dev, 
     cudaStream_t st = (cudaStream_t)stream;
     if (M == 0) return DIRAC_OK;
     if (tensor_cores) {
-        k_guess_forward_tc<<<(unsigned)((M + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), st>>>(M, x_dev, g->wb,
-                                                                                                  g->wr, out_dev);
+        k_guess_forward_tc<<<(unsigned)((M + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), st>>>(
+            M, x_dev, g->wb, g->wr, out_dev, nullptr);
         return check_launch("dirac_guess_forward");
     }
     // FP32 path in batches of max_batch samples (activations live in the training workspace)
@@ -748,19 +768,36 @@ extern "C" dirac_status dirac_guess_train_step(dirac_guess* g, const float* x_de
     return DIRAC_OK;
 }
 
-// the learned guess inside a step: x = x_ext + s net(features), states psi_n, h1, h2, h3
+// the learned guess inside a step: x = x_ext + s net(features), states psi_n, h1, h2, h3, the field
+// at t_start + (step + 1) dt; with a gate (device flag) every kernel returns at once when it is 0
 namespace dg {
+dirac_status guess_buffers(dirac_op* op)
+{
+    if (op->gfield) return DIRAC_OK;
+    GTRY(cudaMalloc(&op->gfield, sizeof(float) * 8), "learned guess");
+    op->allocs.push_back(op->gfield);
+    GTRY(cudaMalloc(&op->ggate, sizeof(int) * 4), "learned guess");
+    op->allocs.push_back(op->ggate);
+    return DIRAC_OK;
+}
+
 dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, const double2* h2, const double2* h3,
-                        double t_next, double2* x)
+                        double t_start, int step, double2* x, const int* gate, cudaStream_t st,
+                        const float* field)
 {
     dirac_guess* g = op->net;
     int64_t npos = (int64_t)op->ov.nch * op->ov.n1;
     unsigned nb = (unsigned)((npos + 255) / 256);
-    k_guess_features<<<nb, 256, 0, op->st>>>(op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, p0, h1, h2, h3,
-                                             guess_field(op, t_next), op->gx, op->gs);
-    k_guess_forward_tc<<<(unsigned)((npos + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), op->st>>>(
-        npos, op->gx, g->wb, g->wr, op->gout);
-    k_guess_apply<<<nb, 256, 0, op->st>>>(npos, p0, h1, h2, op->gs, op->gout, x);
+    if (!field) {
+        k_guess_field<<<1, 1, 0, st>>>(op->pv, t_start, step, op->opts.dt, op->gfield);
+        field = op->gfield;
+        op->launches++;
+    }
+    k_guess_features<<<nb, 256, 0, st>>>(op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, p0, h1, h2, h3,
+                                         field, op->gx, op->gs, gate);
+    k_guess_forward_tc<<<(unsigned)((npos + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), st>>>(
+        npos, op->gx, g->wb, g->wr, op->gout, gate);
+    k_guess_apply<<<nb, 256, 0, st>>>(npos, p0, h1, h2, op->gs, op->gout, x, gate);
     op->launches += 3;
     return check_launch("learned guess");
 }
@@ -778,6 +815,9 @@ extern "C" dirac_status dirac_op_set_guess(dirac_op* op, dirac_guess* net)
         op->allocs.push_back(op->gs);
         GTRY(cudaMalloc(&op->gout, sizeof(float) * npos * GN_OUT), "dirac_op_set_guess");
         op->allocs.push_back(op->gout);
+        dirac_status e = guess_buffers(op);
+        if (e) return e;
     }
+    op->config_gen++;   // captured graphs take the network into account
     return DIRAC_OK;
 }

@@ -97,6 +97,22 @@ __device__ __forceinline__ double extrapolate(int nh, double p, double a, double
 }
 __global__ void k_extrapolate(int64_t n, int nh, const double2* psi, const double2* h1, const double2* h2, double2* x);
 
+// the learned guess's six field factors at time t (the separable carriers of the sin^2 pulse)
+__device__ __forceinline__ void guess_field_at(const PulseView& P, double t, float* f)
+{
+    double tt = t - P.t0;
+    bool on = tt >= 0 && tt <= P.T;
+    for (int c = 0; c < 3; c++) {
+        f[2 * c] = on ? (float)(P.amp * P.wt[c] * sin(P.w[c] * tt)) : 0.f;
+        f[2 * c + 1] = on ? (float)(P.amp * P.wt[c] * cos(P.w[c] * tt)) : 0.f;
+    }
+}
+// time of step `step` + 1 from a start time, explicitly rounded (host loop and graph agree)
+__device__ __forceinline__ double next_time(double t_start, int step, double dt)
+{
+    return __dadd_rn(t_start, __dmul_rn((double)(step + 1), dt));
+}
+
 // warp-per-channel preconditioner with shared-memory staging (band width 13)
 template <class T> size_t precond_sm_smem(int n1);
 template <class T> cudaError_t precond_sm_prepare(int n1);

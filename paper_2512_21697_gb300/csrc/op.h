@@ -85,6 +85,8 @@ struct dirac_op {
     int* ch_two_mu = nullptr;    // [nch] 2 mu of each channel (learned-guess features)
     dirac_guess* net = nullptr;  // learned initial guess (guess option 2), not owned
     float *gx = nullptr, *gs = nullptr, *gout = nullptr;   // its features, scales and outputs
+    float* gfield = nullptr;     // its six field factors (device) and, in a graph, the gate flag
+    int* ggate = nullptr;
     int* dev_err = nullptr;      // set by kernels whose bounded waits ran out
     double2* part_d2 = nullptr;
     double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
@@ -136,7 +138,9 @@ void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start 
 void set_error(const std::string& msg);
 void graph_free(dirac_op* op);
 dirac_status bound_population(dirac_op* op, const double2* psi, double* out);
+dirac_status guess_buffers(dirac_op* op);
 dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, const double2* h2, const double2* h3,
-                        double t_next, double2* x);
+                        double t_start, int step, double2* x, const int* gate, cudaStream_t st,
+                        const float* field);
 
 }  // namespace dg

@@ -155,6 +155,13 @@ def test_trained_network_beats_extrapolation_on_heldout_pulses():
         assert torch.linalg.norm(psi - tr.states[-1]).item() <= 1e-9 * torch.linalg.norm(psi).item()
         it_ext += sum(tr.iters[3:])
         it_net += int(np.sum(its[3:]))
+        # the captured graph driver with the learned guess gives the same steps bit for bit
+        op2 = B.Operator(bas, cfg, tol=1e-12, precision=0, max_iter=1000, guess=2)
+        B.set_guess(op2, net)
+        psi2 = tr.states[0].clone()
+        hist2 = torch.zeros(3 * bas.n, dtype=torch.complex128, device="cuda")
+        its2, res2, nh2 = op2.run(psi2, 16, cfg["t_start"], hist2, n_hist=0)
+        assert nh2 == 3 and np.array_equal(its, its2) and torch.equal(psi, psi2)
     print("learned / extrapolated guess error (held-out pulses):", np.round(ratios, 3),
           "iterations ext %d learned %d" % (it_ext, it_net))
     assert np.mean(ratios) < 0.7
