@@ -157,9 +157,13 @@ void launch_assemble_set(dirac_op* op, cudaStream_t st, const AsmSet& a)
     if (op->npairs) {
         k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, st>>>(
             op->ov, be, a.Gdf, a.Kdf, a.KTdf);
-        launch_assemble_df(dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
-                                (unsigned)std::min<int64_t>(op->npairs, 65535)),
-                           st, op->ov, a.Kdf, a.KTdf, op->cab_df, a.Wh, a.Wl);
+        if (op->asm_chunks)
+            launch_assemble_grp_df(st, op->ov, op->asm_chunks, op->asm_nchunks, op->asm_gpair, op->asm_gcoef,
+                                   a.Kdf, a.KTdf, a.Wh, a.Wl);
+        else
+            launch_assemble_df(dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
+                                    (unsigned)std::min<int64_t>(op->npairs, 65535)),
+                               st, op->ov, a.Kdf, a.KTdf, op->cab_df, a.Wh, a.Wl);
     }
 }
 
@@ -676,8 +680,11 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     // distinct (k', k, l) bands and per-term references to them
     std::vector<int> keyl, tkd(B.pterm.size()), tkt(B.pterm.size());
     std::vector<double> keym, tcab(2 * B.pterm.size());
+    std::vector<int> index((size_t)nk2 * nk2 * (B.p.l_max + 1), -1);
+    auto key_index = [&](int kp, int k, int l) {
+        return index[((size_t)kappa_slot(kp) * nk2 + kappa_slot(k)) * (B.p.l_max + 1) + l];
+    };
     {
-        std::vector<int> index((size_t)nk2 * nk2 * (B.p.l_max + 1), -1);
         auto key_of = [&](int kp, int k, int l) {
             size_t id = ((size_t)kappa_slot(kp) * nk2 + kappa_slot(k)) * (B.p.l_max + 1) + l;
             if (index[id] < 0) {
@@ -796,6 +803,58 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
             cdf[e] = make_float4(a.x, a.y, b.x, b.y);
         }
         TRY(upload(op, &op->cab_df, cdf));
+        // pair groups (same kappa_a, kappa_b; adjacent in porder) in chunks of at most ASM_CHUNK pairs
+        {
+            std::vector<AsmChunk> chunks;
+            std::vector<int> gpair;
+            std::vector<float4> gcoef;
+            bool ok = true;
+            for (int64_t i = 0; i < op->npairs && ok;) {
+                int q0 = porder[i];
+                int ka = B.kap[B.pa[q0]], kb = B.kap[B.pb[q0]];
+                int64_t j = i;
+                while (j < op->npairs && B.kap[B.pa[porder[j]]] == ka && B.kap[B.pb[porder[j]]] == kb) j++;
+                std::vector<int> ls;
+                for (int64_t u = i; u < j; u++)
+                    for (int e = B.pterm_start[porder[u]]; e < B.pterm_start[porder[u] + 1]; e++)
+                        if (std::find(ls.begin(), ls.end(), B.pterm[e].l) == ls.end()) ls.push_back(B.pterm[e].l);
+                std::sort(ls.begin(), ls.end());
+                if ((int)ls.size() > ASM_MAX_NL) { ok = false; break; }
+                int64_t cnt = j - i, nchk = (cnt + ASM_CHUNK - 1) / ASM_CHUNK;
+                for (int64_t c = 0; c < nchk; c++) {
+                    int64_t c0 = i + cnt * c / nchk, c1 = i + cnt * (c + 1) / nchk;
+                    AsmChunk ch{};
+                    ch.first = (int)gpair.size();
+                    ch.count = (int)(c1 - c0);
+                    ch.nl = (int)ls.size();
+                    ch.ka = ka;
+                    ch.kb = kb;
+                    for (int m = 0; m < ASM_MAX_NL; m++) {
+                        int l = m < ch.nl ? ls[m] : ls[0];
+                        ch.kd[m] = key_index(ka, kb, l);
+                        ch.kt[m] = key_index(kb, ka, l);
+                    }
+                    chunks.push_back(ch);
+                    for (int64_t u = c0; u < c1; u++) {
+                        int q = porder[u];
+                        gpair.push_back(q);
+                        size_t base = gcoef.size();
+                        gcoef.resize(base + ASM_MAX_NL, make_float4(0.f, 0.f, 0.f, 0.f));
+                        for (int e = B.pterm_start[q]; e < B.pterm_start[q + 1]; e++) {
+                            int m = (int)(std::find(ls.begin(), ls.end(), B.pterm[e].l) - ls.begin());
+                            gcoef[base + m] = cdf[e];
+                        }
+                    }
+                }
+                i = j;
+            }
+            if (ok && !chunks.empty()) {
+                op->asm_nchunks = (int)chunks.size();
+                TRY(upload(op, &op->asm_chunks, chunks));
+                TRY(upload(op, &op->asm_gpair, gpair));
+                TRY(upload(op, &op->asm_gcoef, gcoef));
+            }
+        }
         TRY(dev_alloc(op, &op->Gdf, (size_t)P.L * 4 * be));
         TRY(dev_alloc(op, &op->Kdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
         TRY(dev_alloc(op, &op->KTdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));

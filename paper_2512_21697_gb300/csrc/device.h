@@ -52,6 +52,16 @@ struct OpView {
     const int* prec_order;    // channels sorted by radial block
 };
 
+// One chunk of a (kappa_a, kappa_b) pair group for the grouped double-float assembly: pairs
+// first .. first + count - 1 of the group-ordered pair list, their nl multipoles' direct and
+// transposed band keys (increasing l).
+constexpr int ASM_MAX_NL = 4;
+constexpr int ASM_CHUNK = 32;
+struct AsmChunk {
+    int first, count, nl, ka, kb;
+    int kd[ASM_MAX_NL], kt[ASM_MAX_NL];
+};
+
 struct PulseView {
     int L;
     double T, amp, t0, dt;

@@ -40,6 +40,17 @@ __device__ __forceinline__ void df_fma(DfAcc& a, float wh, float wl, float xh, f
     a.c += err + e;
 }
 
+// a = (wh + wl) (xh + xl): the first product of a sum (TwoSum with an empty accumulator returns
+// the product itself)
+__device__ __forceinline__ void df_mul(DfAcc& a, float wh, float wl, float xh, float xl)
+{
+    float p = wh * xh;
+    float e = fmaf(wh, xh, -p);
+    e = fmaf(wh, xl, e);
+    a.s = p;
+    a.c = fmaf(wl, xh, e);
+}
+
 // add another accumulator (sign +1 or -1)
 __device__ __forceinline__ void df_add(DfAcc& a, const DfAcc& b, float sign)
 {

@@ -4,6 +4,8 @@
 // stored as hi/lo float pairs; see df64.cuh for the arithmetic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "device.h"
 #include "df64.cuh"
 #include "kernels.h"
@@ -128,6 +130,106 @@ void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float
     if (A.bd == 13) k_assemble_df<13><<<grid, 128, 0, st>>>(A, K, KT, cab, Wh, Wl);
     else k_assemble_df<0><<<grid, 128, 0, st>>>(A, K, KT, cab, Wh, Wl);
 }
+
+// Grouped form of the same assembly.  The pairs of one (kappa_a, kappa_b) group (all mu) combine
+// the same K_l(ka, kb) and KT_l(kb, ka) bands with their own angular coefficients, so a block
+// takes 128 (radial row, block diagonal) positions of one chunk of a group, holds the group's
+// bands at its positions in registers and writes the coupling values of every pair of the chunk:
+// the bands are read once per chunk instead of once per pair.  Each pair's sum runs over the
+// group's multipoles in increasing l, direct band first, as k_assemble_df; a multipole the pair
+// lacks has zero coefficients.  NL = multipoles of the group (1..ASM_MAX_NL).
+template <int BD, int NL>
+__device__ __forceinline__ void assemble_grp_body(const OpView& A, const AsmChunk& ch, const int* sp,
+                                                  const float4* sc, int idx, const float2* __restrict__ K,
+                                                  const float2* __restrict__ KT, float* __restrict__ Wh,
+                                                  float* __restrict__ Wl)
+{
+    const int bd = BD > 0 ? BD : A.bd;
+    const int half = (bd - 1) / 2;
+    const int nrd = A.n1 * bd;
+    int r = idx / bd, d = idx - r * bd, rr = r + d - half;
+    bool inb = rr >= 0 && rr < A.n1;
+    bool keep[4];
+    for (int k = 0; k < 4; k++)
+        keep[k] = inb && used_fn_df(ch.ka, r, k / 2) && used_fn_df(ch.kb, rr, k % 2);
+    const int64_t nb = (int64_t)nrd * 4;
+    float4 g[NL][2], h[NL][2];   // (hi, lo) pairs of the 4 block entries, direct and transposed band
+#pragma unroll
+    for (int j = 0; j < NL; j++) {
+        if (inb) {
+            const float4* gp = reinterpret_cast<const float4*>(K + ch.kd[j] * nb + (int64_t)idx * 4);
+            const float4* hp = reinterpret_cast<const float4*>(KT + ch.kt[j] * nb + (int64_t)idx * 4);
+            g[j][0] = gp[0]; g[j][1] = gp[1]; h[j][0] = hp[0]; h[j][1] = hp[1];
+        } else {
+            g[j][0] = g[j][1] = h[j][0] = h[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    for (int q = 0; q < ch.count; q++) {
+        int64_t p = sp[q];
+        DfAcc w[4];
+        float4 cf = sc[q * ASM_MAX_NL];   // (cA hi, cA lo, cB hi, cB lo)
+        df_mul(w[0], cf.x, cf.y, g[0][0].x, g[0][0].y); df_fma(w[0], cf.z, cf.w, h[0][0].x, h[0][0].y);
+        df_mul(w[1], cf.x, cf.y, g[0][0].z, g[0][0].w); df_fma(w[1], cf.z, cf.w, h[0][0].z, h[0][0].w);
+        df_mul(w[2], cf.x, cf.y, g[0][1].x, g[0][1].y); df_fma(w[2], cf.z, cf.w, h[0][1].x, h[0][1].y);
+        df_mul(w[3], cf.x, cf.y, g[0][1].z, g[0][1].w); df_fma(w[3], cf.z, cf.w, h[0][1].z, h[0][1].w);
+#pragma unroll
+        for (int j = 1; j < NL; j++) {
+            cf = sc[q * ASM_MAX_NL + j];
+            df_fma(w[0], cf.x, cf.y, g[j][0].x, g[j][0].y); df_fma(w[0], cf.z, cf.w, h[j][0].x, h[j][0].y);
+            df_fma(w[1], cf.x, cf.y, g[j][0].z, g[j][0].w); df_fma(w[1], cf.z, cf.w, h[j][0].z, h[j][0].w);
+            df_fma(w[2], cf.x, cf.y, g[j][1].x, g[j][1].y); df_fma(w[2], cf.z, cf.w, h[j][1].x, h[j][1].y);
+            df_fma(w[3], cf.x, cf.y, g[j][1].z, g[j][1].w); df_fma(w[3], cf.z, cf.w, h[j][1].z, h[j][1].w);
+        }
+        float hh[4], ll[4];
+        for (int k = 0; k < 4; k++) {
+            if (!keep[k]) df_zero(w[k]);
+            hh[k] = w[k].s + w[k].c;
+            ll[k] = (w[k].s - hh[k]) + w[k].c;
+        }
+        int64_t o = (p * nrd + idx) * 4;
+        *reinterpret_cast<float4*>(Wh + o) = make_float4(hh[0], hh[1], hh[2], hh[3]);
+        *reinterpret_cast<float4*>(Wl + o) = make_float4(ll[0], ll[1], ll[2], ll[3]);
+    }
+}
+
+template <int BD>
+__global__ void __launch_bounds__(128) k_assemble_grp_df(OpView A, const AsmChunk* __restrict__ chunks, int nchunks,
+                                                         const int* __restrict__ gpair,
+                                                         const float4* __restrict__ gcoef,
+                                                         const float2* __restrict__ K,
+                                                         const float2* __restrict__ KT, float* __restrict__ Wh,
+                                                         float* __restrict__ Wl)
+{
+    __shared__ int sp[ASM_CHUNK];
+    __shared__ float4 sc[ASM_CHUNK * ASM_MAX_NL];
+    const int bd = BD > 0 ? BD : A.bd;
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    bool act = idx < A.n1 * bd;
+    for (int c = blockIdx.y; c < nchunks; c += gridDim.y) {
+        const AsmChunk ch = chunks[c];
+        __syncthreads();   // the previous chunk's coefficients are no longer read
+        for (int i = threadIdx.x; i < ch.count; i += blockDim.x) sp[i] = gpair[ch.first + i];
+        for (int i = threadIdx.x; i < ch.count * ASM_MAX_NL; i += blockDim.x)
+            sc[i] = gcoef[(int64_t)ch.first * ASM_MAX_NL + i];
+        __syncthreads();
+        if (!act) continue;
+        switch (ch.nl) {
+        case 1: assemble_grp_body<BD, 1>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
+        case 2: assemble_grp_body<BD, 2>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
+        case 3: assemble_grp_body<BD, 3>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
+        default: assemble_grp_body<BD, 4>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
+        }
+    }
+}
+
+void launch_assemble_grp_df(cudaStream_t st, const OpView& A, const AsmChunk* chunks, int nchunks, const int* gpair,
+                            const float4* gcoef, const float2* K, const float2* KT, float* Wh, float* Wl)
+{
+    dim3 grid((unsigned)((A.n1 * A.bd + 127) / 128), (unsigned)std::min(nchunks, 65535));
+    if (A.bd == 13) k_assemble_grp_df<13><<<grid, 128, 0, st>>>(A, chunks, nchunks, gpair, gcoef, K, KT, Wh, Wl);
+    else k_assemble_grp_df<0><<<grid, 128, 0, st>>>(A, chunks, nchunks, gpair, gcoef, K, KT, Wh, Wl);
+}
+
 
 // u = psi + x, v = psi - x in double, each split into (re_hi, re_lo, im_hi, im_lo)
 __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,

@@ -69,6 +69,11 @@ struct dirac_op {
     float2 *Gdf = nullptr, *Kdf = nullptr, *KTdf = nullptr, *Sdf = nullptr, *Htdf = nullptr;
     float *Wh = nullptr, *Wl = nullptr;   // coupling hi words (also the FP32 values) and lo words
     float4* cab_df = nullptr;
+    // grouped double-float assembly (null when a group has more than ASM_MAX_NL multipoles)
+    dg::AsmChunk* asm_chunks = nullptr;
+    int asm_nchunks = 0;
+    int* asm_gpair = nullptr;
+    float4* asm_gcoef = nullptr;
     float4* xsplit = nullptr;    // split input vector; u = psi + x in the fused residual
     float4* vsplit = nullptr;    // v = psi - x in the fused residual
     float* W32 = nullptr;        // their FP32 rounding (mixed precision only)

@@ -54,8 +54,13 @@ MEDIUM = _base(R=300.0, N=600, grid=1, r_lin=60.0, n_lin=299, kappa_max=14, two_
 TAIL = _base(R=300.0, N=120, grid=1, r_lin=60.0, n_lin=58, kappa_max=4, two_mu_max=0, l_max=4,
              E0=0.1, omega=omega_from_nm(800), n_cycles=3.0, dt=0.005, steps=20, tol=1e-12)
 
+# Multipoles up to l = 8 on the small system: some (kappa_a, kappa_b) groups couple through five
+# multipoles of one parity, more than the grouped double-float assembly holds in registers, so
+# the assembly takes its per-pair form.
+WIDE_L = dict(SMALL, l_max=8, E0=0.5, omega=omega_from_nm(100))
+
 WORKLOADS = {"small": SMALL, "production": PRODUCTION, "tiny": TINY, "slice": SLICE, "medium": MEDIUM,
-             "tail": TAIL}
+             "tail": TAIL, "wide_l": WIDE_L}
 
 
 def oracle_params(cfg):

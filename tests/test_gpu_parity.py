@@ -210,7 +210,7 @@ def test_mixed_precision_step_matches_oracle(oracle_mod, name):
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
-@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail"])
+@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail", "wide_l"])
 def test_double_float_apply_matches_oracle(oracle_mod, name):
     # precision 2 applies A_+- in double-float (FP32 hi/lo pairs with error-free transforms):
     # ~2^-44 relative per operation, so the bar is 1e-11 of max|y| instead of 1e-12
@@ -227,7 +227,7 @@ def test_double_float_apply_matches_oracle(oracle_mod, name):
         assert np.abs(y - ref).max() <= 1e-11 * np.abs(ref).max(), sign
 
 
-@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail"])
+@pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail", "wide_l"])
 def test_double_float_step_matches_oracle(oracle_mod, name):
     cfg = W.WORKLOADS[name]
     c = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
