@@ -75,15 +75,18 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: a waiting warp sleeps until the phase completes (or the hint
+// runs out) instead of spinning, so warps that wait leave the issue slots to those that compute
+constexpr uint32_t SUSPEND_NS = 20000;
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
@@ -112,6 +115,7 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
     extern __shared__ __align__(128) float wring[];
     __shared__ float4 xs[TR];                        // x_a rows of the tile: (x0.re, x0.im, x1.re, x1.im)
     __shared__ uint64_t full[NST], empty[NST];
+    __shared__ int64_t spair[NST];                   // pair of each stage, written by the producer
     __shared__ int fail, issued;
     const int n1 = A.n1, ntile = gridDim.y;
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
@@ -173,6 +177,7 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
                 const int64_t p = A.own_pair[own0 + k];
                 const int nb = A.own_nbr[own0 + k];
                 float* st = wring + s * STAGE32;
+                spair[s] = p;   // published by the arrive below
                 fence_proxy_async();
                 mbar_expect_tx(&full[s], bytes + xbytes);
                 bulk_load(st, W + (p * n1 + r0) * ROWF, bytes, &full[s]);
@@ -184,7 +189,7 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
         for (int k = 0; k < nown; k++) {
             const int s = k % NST;
             if (!mbar_wait(&full[s], (uint32_t)((k / NST) & 1))) { fail = 1; break; }
-            const int64_t p = A.own_pair[own0 + k];
+            const int64_t p = spair[s];
             const float* Ws = wring + s * STAGE32;
             const float4* Xs = reinterpret_cast<const float4*>(Ws + TR * ROWF);   // x_b row window
             if (tid < NT) {
@@ -302,9 +307,12 @@ __global__ void __launch_bounds__(NT) k_apply_gather32(OpView A, int sign, float
 // Refinement residual r = A_- psi - A_+ x = S (psi - x) - i tau H0 (psi + x) + (W - W^T)(psi + x)
 // in double-float, from u = psi + x and v = psi - x split into (re hi, re lo, im hi, im lo), and,
 // when *need_b is set (the first pass of a step), b = A_- psi in FP32 products for the tolerance
-// scale ||b||.  Owner pass: r_a (diagonal + direct coupling) to r_out, b_a to b_out; partials of the
-// transposed products to part_r (the unnormalised double-float accumulators (s, c) of the four
-// components, two float4 per row: no FP64 instruction in this pass) and part_b.
+// scale ||b||.  Owner pass: the direct coupling sums W_ab u_b of channel a to r_out (W_ab psi_b to
+// b_out); partials of the transposed products to part_r (the unnormalised double-float accumulators
+// (s, c) of the four components, two float4 per row: no FP64 instruction in this pass) and part_b.
+// Gather pass: the diagonal block S v - i tau H0 u of the channel (latency-bound band reads at high
+// occupancy, so the owner pass's warps spend their time on the coupling), plus the direct sums,
+// minus the partials.
 // ---------------------------------------------------------------------------------------------
 namespace {
 constexpr int NSTD = 2;          // ring depth of the double-float pass
@@ -317,10 +325,7 @@ constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8;   // floats: hi and lo words,
 // roles drift freely within the ring instead of meeting at a block barrier for every pair.
 constexpr int NTHR_OWN = 2 * NT + 32;
 
-__global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const float2* __restrict__ S,
-                                                             const float2* __restrict__ Ht,
-                                                             const float4* __restrict__ u,
-                                                             const float4* __restrict__ v,
+__global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const float4* __restrict__ u,
                                                              const float2* __restrict__ psi32,
                                                              const float* __restrict__ Wh, const float* __restrict__ Wl,
                                                              double2* __restrict__ r_out, float2* __restrict__ b_out,
@@ -332,6 +337,8 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
     __shared__ float4 us[2 * TR];                    // u_a rows: (type 0, type 1) split complex
     __shared__ float4 ps[TR];                        // psi_a rows in FP32: (p0.re, p0.im, p1.re, p1.im)
     __shared__ uint64_t full[NSTD], empty[NSTD];
+    __shared__ int64_t spair[NSTD];                  // pair and partner channel of each stage
+    __shared__ int snbr[NSTD];
     __shared__ int fail, issued;
     const bool need_b = *need_b_flag != 0;
     const int n1 = A.n1, ntile = gridDim.y;
@@ -355,7 +362,6 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         mbar_fence_init();
     }
     const float4* ua = u + (int64_t)ch * 2 * n1;
-    const float4* va = v + (int64_t)ch * 2 * n1;
     const float2* pa = psi32 + (int64_t)ch * 2 * n1;
     if (tid < TR) {
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -364,39 +370,27 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         us[2 * tid + 1] = in ? ua[2 * (r0 + tid) + 1] : z;
         ps[tid] = in ? *reinterpret_cast<const float4*>(pa + 2 * (r0 + tid)) : z;
     }
-    const int r = r0 + tid;
-    const bool direct_row = tid < TR && r < n1;
-    DfAcc yv[4];   // (type 0 re, im, type 1 re, im)
-    for (int k = 0; k < 4; k++) df_zero(yv[k]);
-    float bb[4] = {0.f, 0.f, 0.f, 0.f};
-    if (direct_row) {
-        int ks = A.ch_kslot[ch];
-        const float2* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
-        const float2* Hk = Ht + ((int64_t)ks * n1 + r) * ROWF;
-#pragma unroll 1   // keeps the double-float loop bodies within the instruction cache
-        for (int d = 0; d < BDO; d++) {
-            int rr = r + d - HO;
-            if (rr < 0 || rr >= n1) continue;
-            float4 u0 = ua[2 * rr], u1 = ua[2 * rr + 1], v0 = va[2 * rr], v1 = va[2 * rr + 1];
-            float4 pv = need_b ? *reinterpret_cast<const float4*>(pa + 2 * rr) : make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int t = 0; t < 2; t++) {
-                float2 s0 = Sk[d * 4 + 2 * t], s1 = Sk[d * 4 + 2 * t + 1];
-                float2 h0 = Hk[d * 4 + 2 * t], h1 = Hk[d * 4 + 2 * t + 1];
-                // re: S v_re + tau H u_im ;  im: S v_im - tau H u_re
-                df_fma(yv[2 * t], s0.x, s0.y, v0.x, v0.y);
-                df_fma(yv[2 * t], s1.x, s1.y, v1.x, v1.y);
-                df_fma(yv[2 * t], h0.x, h0.y, u0.z, u0.w);
-                df_fma(yv[2 * t], h1.x, h1.y, u1.z, u1.w);
-                df_fma(yv[2 * t + 1], s0.x, s0.y, v0.z, v0.w);
-                df_fma(yv[2 * t + 1], s1.x, s1.y, v1.z, v1.w);
-                df_fma(yv[2 * t + 1], -h0.x, -h0.y, u0.x, u0.y);
-                df_fma(yv[2 * t + 1], -h1.x, -h1.y, u1.x, u1.y);
-                // b = (S - i tau H) psi
-                bb[2 * t] += s0.x * pv.x + s1.x * pv.z + h0.x * pv.y + h1.x * pv.w;
-                bb[2 * t + 1] += s0.x * pv.y + s1.x * pv.w - h0.x * pv.x - h1.x * pv.z;
+    // window rows outside the radial grid are never copied: zero them once in both stages, so the
+    // direct products need no range test (the stored coupling is zero at those band positions)
+    {
+        const int wlo = lo - (r0 - HO), whi = hi - (r0 - HO);
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = tid; i < NSTD * NOUT; i += NTHR_OWN) {
+            int sg = i / NOUT, w = i - sg * NOUT;
+            if (w < wlo || w >= whi) {
+                float4* Uz = reinterpret_cast<float4*>(wring + sg * stage_f + 2 * TR * ROWF);
+                Uz[2 * w] = z;
+                Uz[2 * w + 1] = z;
             }
         }
     }
+    // consumer threads: group g = tid / NT (0 or 1), local index lt = tid % NT.  For the k-th owned
+    // pair, group (k + g) % 2 forms the direct products of row r0 + lt and the other group the
+    // transposed products of output row r0 - h + lt: every warp alternates the two roles, so both
+    // groups finish together whatever the relative cost of the roles.
+    const int grp = tid / NT, lt = tid % NT;
+    const int r = r0 + lt;
+    const bool direct_row = tid < 2 * NT && lt < TR && r < n1;
     __syncthreads();   // barriers initialised, us and ps staged
     DfAcc dd[4];
     for (int k = 0; k < 4; k++) df_zero(dd[k]);
@@ -410,6 +404,8 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 const int64_t p = A.own_pair[own0 + k];
                 const int nb = A.own_nbr[own0 + k];
                 float* st = wring + s * stage_f;
+                spair[s] = p;   // published by the arrive below
+                snbr[s] = nb;
                 fence_proxy_async();
                 mbar_expect_tx(&full[s], 2 * bytes + ubytes);
                 bulk_load(st, Wh + (p * n1 + r0) * ROWF, bytes, &full[s]);
@@ -422,29 +418,26 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         for (int k = 0; k < nown; k++) {
             const int s = k % NSTD;
             if (!mbar_wait(&full[s], (uint32_t)((k / NSTD) & 1))) { fail = 1; break; }
-            const int e = own0 + k;
-            const int64_t p = A.own_pair[e];
             const float* Hs = wring + s * stage_f;
             const float* Ls = Hs + TR * ROWF;
             const float4* Us = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window][2]
-            if (tid < NT) {
+            if (((k + grp) & 1) == 0) {
                 if (direct_row) {
-                    const int nb = A.own_nbr[e];
-                    const float2* pb = psi32 + (int64_t)nb * 2 * n1;
+                    const float2* pb = psi32 + (int64_t)snbr[s] * 2 * n1;
 #pragma unroll 1
                     for (int d = 0; d < BDO; d++) {
-                        int rr = r + d - HO;
-                        if (rr < 0 || rr >= n1) continue;
-                        // window index of row rr: rr - (r0 - h) = tid + d
-                        float4 x0 = Us[2 * (tid + d)], x1 = Us[2 * (tid + d) + 1];
-                        float4 wh = *reinterpret_cast<const float4*>(Hs + tid * ROWF + d * 4);
-                        float4 wl = *reinterpret_cast<const float4*>(Ls + tid * ROWF + d * 4);
+                        // window index of row rr = r + d - h: rr - (r0 - h) = lt + d; rows outside the
+                        // grid are zero in the window and in W
+                        float4 x0 = Us[2 * (lt + d)], x1 = Us[2 * (lt + d) + 1];
+                        float4 wh = *reinterpret_cast<const float4*>(Hs + lt * ROWF + d * 4);
+                        float4 wl = *reinterpret_cast<const float4*>(Ls + lt * ROWF + d * 4);
                         // W[t][u] = (w.x, w.y ; w.z, w.w)
                         df_fma(dd[0], wh.x, wl.x, x0.x, x0.y); df_fma(dd[0], wh.y, wl.y, x1.x, x1.y);
                         df_fma(dd[1], wh.x, wl.x, x0.z, x0.w); df_fma(dd[1], wh.y, wl.y, x1.z, x1.w);
                         df_fma(dd[2], wh.z, wl.z, x0.x, x0.y); df_fma(dd[2], wh.w, wl.w, x1.x, x1.y);
                         df_fma(dd[3], wh.z, wl.z, x0.z, x0.w); df_fma(dd[3], wh.w, wl.w, x1.z, x1.w);
-                        if (need_b) {
+                        const int rr = r + d - HO;
+                        if (need_b && rr >= 0 && rr < n1) {
                             float4 q = *reinterpret_cast<const float4*>(pb + 2 * rr);
                             db[0] += wh.x * q.x + wh.y * q.z;
                             db[1] += wh.x * q.y + wh.y * q.w;
@@ -454,16 +447,18 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                     }
                 }
             } else {
+                const int64_t p = spair[s];
                 float4* pr = part_r + (((int64_t)p * ntile + tile) * NOUT) * 2;
                 float4* pbp = part_b + ((int64_t)p * ntile + tile) * NOUT;
-                const int j = tid - NT;   // one output row per thread (NOUT == NT)
+                const int j = lt;   // one output row per thread (NOUT == NT)
                 DfAcc tt[4];
                 for (int q = 0; q < 4; q++) df_zero(tt[q]);
                 float tb[4] = {0.f, 0.f, 0.f, 0.f};
+                // diagonals whose W row r0 + j - d lies in the tile
+                const int dlo = max(0, j - rows + 1), dhi = min(BDO - 1, j);
 #pragma unroll 1
-                for (int d = 0; d < BDO; d++) {
+                for (int d = dlo; d <= dhi; d++) {
                     int lr = j - d;
-                    if (lr < 0 || lr >= rows) continue;
                     float4 wh = *reinterpret_cast<const float4*>(Hs + lr * ROWF + d * 4);
                     float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
                     float4 x0 = us[2 * lr], x1 = us[2 * lr + 1];
@@ -498,20 +493,39 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         }
         return;
     }
-    if (direct_row) {
-        for (int k = 0; k < 4; k++) df_add(yv[k], dd[k], 1.f);
+    // group 1's direct sums to shared memory (the ring is free: every copy has been consumed),
+    // group 0 adds them in a fixed order and stores the row
+    float4* xch = reinterpret_cast<float4*>(wring);   // [NT][3]: (s, c) x 4, then the FP32 b sums
+    if (grp == 1 && direct_row) {
+        xch[3 * lt] = make_float4(dd[0].s, dd[0].c, dd[1].s, dd[1].c);
+        xch[3 * lt + 1] = make_float4(dd[2].s, dd[2].c, dd[3].s, dd[3].c);
+        xch[3 * lt + 2] = make_float4(db[0], db[1], db[2], db[3]);
+    }
+    __syncthreads();
+    if (grp == 0 && direct_row) {
+        float4 a0 = xch[3 * lt], a1 = xch[3 * lt + 1], a2 = xch[3 * lt + 2];
+        DfAcc o0 = {a0.x, a0.y}, o1 = {a0.z, a0.w}, o2 = {a1.x, a1.y}, o3 = {a1.z, a1.w};
+        df_add(dd[0], o0, 1.f);
+        df_add(dd[1], o1, 1.f);
+        df_add(dd[2], o2, 1.f);
+        df_add(dd[3], o3, 1.f);
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
-        r_out[o] = make_double2(df_value(yv[0]), df_value(yv[1]));
-        r_out[o + 1] = make_double2(df_value(yv[2]), df_value(yv[3]));
+        r_out[o] = make_double2(df_value(dd[0]), df_value(dd[1]));
+        r_out[o + 1] = make_double2(df_value(dd[2]), df_value(dd[3]));
         if (need_b)
             *reinterpret_cast<float4*>(b_out + o) =
-                make_float4(bb[0] + db[0], bb[1] + db[1], bb[2] + db[2], bb[3] + db[3]);
+                make_float4(db[0] + a2.x, db[1] + a2.y, db[2] + a2.z, db[3] + a2.w);
     }
 }
 
 // r_b -= sum of the transposed partials (own tile and the neighbours' halo rows, fixed order) in
 // double-float; partials of ||r||^2 and, on a step's first pass, of ||b||^2
-__global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, double2* __restrict__ r_out,
+__global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float2* __restrict__ S,
+                                                           const float2* __restrict__ Ht,
+                                                           const float4* __restrict__ u,
+                                                           const float4* __restrict__ v,
+                                                           const float2* __restrict__ psi32,
+                                                           double2* __restrict__ r_out,
                                                            const float2* __restrict__ b_out,
                                                            const float4* __restrict__ part_r,
                                                            const float4* __restrict__ part_b,
@@ -524,15 +538,51 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, double2* __
     double nr = 0, nb = 0;
     if (tid < TR && r < n1) {
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
+        // diagonal block: S (psi - x) - i tau H0 (psi + x), and b's FP32 part (S - i tau H0) psi
+        const float4* ua = u + (int64_t)ch * 2 * n1;
+        const float4* va = v + (int64_t)ch * 2 * n1;
+        const float2* pa = psi32 + (int64_t)ch * 2 * n1;
+        int ks = A.ch_kslot[ch];
+        const float2* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
+        const float2* Hk = Ht + ((int64_t)ks * n1 + r) * ROWF;
+        DfAcc acc[4];   // (type 0 re, im, type 1 re, im)
+        for (int k = 0; k < 4; k++) df_zero(acc[k]);
+        float bb[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int d = 0; d < BDO; d++) {
+            int rr = r + d - HO;
+            if (rr < 0 || rr >= n1) continue;
+            float4 u0 = ua[2 * rr], u1 = ua[2 * rr + 1], v0 = va[2 * rr], v1 = va[2 * rr + 1];
+            float4 pv = need_b ? *reinterpret_cast<const float4*>(pa + 2 * rr) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int t = 0; t < 2; t++) {
+                float2 s0 = Sk[d * 4 + 2 * t], s1 = Sk[d * 4 + 2 * t + 1];
+                float2 h0 = Hk[d * 4 + 2 * t], h1 = Hk[d * 4 + 2 * t + 1];
+                // re: S v_re + tau H u_im ;  im: S v_im - tau H u_re
+                df_fma(acc[2 * t], s0.x, s0.y, v0.x, v0.y);
+                df_fma(acc[2 * t], s1.x, s1.y, v1.x, v1.y);
+                df_fma(acc[2 * t], h0.x, h0.y, u0.z, u0.w);
+                df_fma(acc[2 * t], h1.x, h1.y, u1.z, u1.w);
+                df_fma(acc[2 * t + 1], s0.x, s0.y, v0.z, v0.w);
+                df_fma(acc[2 * t + 1], s1.x, s1.y, v1.z, v1.w);
+                df_fma(acc[2 * t + 1], -h0.x, -h0.y, u0.x, u0.y);
+                df_fma(acc[2 * t + 1], -h1.x, -h1.y, u1.x, u1.y);
+                bb[2 * t] += s0.x * pv.x + s1.x * pv.z + h0.x * pv.y + h1.x * pv.w;
+                bb[2 * t + 1] += s0.x * pv.y + s1.x * pv.w - h0.x * pv.x - h1.x * pv.z;
+            }
+        }
+        // + the owner pass's direct coupling sums W (psi + x)
         double2 y0 = r_out[o], y1 = r_out[o + 1];
-        DfAcc acc[4];
         const double yv[4] = {y0.x, y0.y, y1.x, y1.y};
         for (int k = 0; k < 4; k++) {
             float2 h = df_split(yv[k]);
-            acc[k].s = h.x;
-            acc[k].c = h.y;
+            DfAcc t = {h.x, h.y};
+            df_add(acc[k], t, 1.f);
         }
-        float4 bv = need_b ? *reinterpret_cast<const float4*>(b_out + o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (need_b) {
+            float4 bo = *reinterpret_cast<const float4*>(b_out + o);
+            bv = make_float4(bb[0] + bo.x, bb[1] + bo.y, bb[2] + bo.z, bb[3] + bo.w);
+        }
         for (int e = A.in_start[ch]; e < A.in_start[ch + 1]; e++) {
             int64_t p = A.in_pair[e];
             const float4* pr = part_r + (int64_t)p * ntile * NOUT * 2;
@@ -575,9 +625,9 @@ void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, c
                             double* pn_b, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_residual_own_df<<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, S, Ht, u, v, psi32, Wh, Wl, r, b, part_r,
-                                                                    part_b, need_b, err);
-    k_residual_gather_df<<<grid, NT, 0, st>>>(A, r, b, part_r, part_b, need_b, pn_r, pn_b);
+    k_residual_own_df<<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b,
+                                                                    need_b, err);
+    k_residual_gather_df<<<grid, NT, 0, st>>>(A, S, Ht, u, v, psi32, r, b, part_r, part_b, need_b, pn_r, pn_b);
 }
 
 size_t apply_own32_smem() { return (size_t)NST * STAGE32 * sizeof(float); }
