@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
             if (((k + grp) & 1) == 0) {
                 if (direct_row) {
                     const float2* pb = psi32 + (int64_t)snbr[s] * 2 * n1;
-#pragma unroll 1
+#pragma unroll
                     for (int d = 0; d < BDO; d++) {
                         // window index of row rr = r + d - h: rr - (r0 - h) = lt + d; rows outside the
                         // grid are zero in the window and in W
@@ -454,11 +454,12 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 DfAcc tt[4];
                 for (int q = 0; q < 4; q++) df_zero(tt[q]);
                 float tb[4] = {0.f, 0.f, 0.f, 0.f};
-                // diagonals whose W row r0 + j - d lies in the tile
+                // diagonals whose W row r0 + j - d lies in the tile (a rolled loop: with the direct
+                // products unrolled, unrolling this one too overflows the instruction cache)
                 const int dlo = max(0, j - rows + 1), dhi = min(BDO - 1, j);
 #pragma unroll 1
                 for (int d = dlo; d <= dhi; d++) {
-                    int lr = j - d;
+                    const int lr = j - d;
                     float4 wh = *reinterpret_cast<const float4*>(Hs + lr * ROWF + d * 4);
                     float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
                     float4 x0 = us[2 * lr], x1 = us[2 * lr + 1];
