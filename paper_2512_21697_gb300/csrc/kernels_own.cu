@@ -7,10 +7,12 @@
 //                     pair the channel owns, a producer warp copies the TR rows of W_ab and the
 //                     window of x_b the band needs into shared memory with the bulk-copy engine
 //                     (cp.async.bulk into an NST-deep ring: a "full" mbarrier per stage completes on
-//                     the bytes, an "empty" one when the consumers release it); warps 0..3
-//                     accumulate W_ab x_b for their row, warps 4..7 form the transposed product
-//                     W_ab^T x_a restricted to those rows (TR + 2h = 128 output rows, one per thread)
-//                     and store it in the pair's partial slot.  y_a = D x_a - sign sum W_ab x_b.
+//                     the bytes, an "empty" one when the consumers release it).  Two groups of four
+//                     warps take the two products of a pair: one accumulates W_ab x_b for its row,
+//                     the other forms the transposed product W_ab^T x_a restricted to those rows
+//                     (TR + 2h = 128 output rows, one per thread) and stores it in the pair's
+//                     partial slot; the groups swap roles from pair to pair.
+//                     y_a = D x_a - sign sum W_ab x_b.
 //   k_apply_gather32: block = (channel b, tile).  y_b += sign sum of the partials of the pairs b is
 //                     the upper channel of (own tile, and the halo rows of the two neighbouring
 //                     tiles), in a fixed order, then the BiCGSTAB epilogues (y <- bsub - y, <dv, y>,
@@ -109,9 +111,9 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
                                                              const KState* skip, int* err)
 {
     if (skip && skip->done) return;   // uniform over the grid: the solve already finished
-    // ring stage: the TR coupling rows, then x_b rows r0 - h .. r0 + TR + h.  Warps 0..3: direct
-    // products, warps 4..7: transposed products, warp 8: producer of the bulk copies; a stage is
-    // refilled when the eight consumer warps have released it.
+    // ring stage: the TR coupling rows, then x_b rows r0 - h .. r0 + TR + h.  Warps 0..7 consume
+    // (two groups alternating the direct and transposed products), warp 8 produces the bulk
+    // copies; a stage is refilled when the eight consumer warps have released it.
     extern __shared__ __align__(128) float wring[];
     __shared__ float4 xs[TR];                        // x_a rows of the tile: (x0.re, x0.im, x1.re, x1.im)
     __shared__ uint64_t full[NST], empty[NST];
@@ -144,30 +146,23 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
         }
         xs[tid] = v;
     }
-    // diagonal block (S + sign i tau H0) x_a for the direct threads' row
-    const int r = r0 + tid;
-    const bool direct_row = tid < TR && r < n1;
-    float2 y0 = make_float2(0.f, 0.f), y1 = make_float2(0.f, 0.f);
-    if (direct_row) {
-        int ks = A.ch_kslot[ch];
-        const float* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
-        const float* Hk = H + ((int64_t)ks * n1 + r) * ROWF;
-        float st = (float)(sign * A.tau);
-#pragma unroll
-        for (int d = 0; d < BDO; d++) {
-            int rr = r + d - HO;
-            if (rr < 0 || rr >= n1) continue;
-            float4 xv = *reinterpret_cast<const float4*>(xa + 2 * rr);
-            float4 sv = *reinterpret_cast<const float4*>(Sk + d * 4);
-            float4 hv = *reinterpret_cast<const float4*>(Hk + d * 4);
-            float h00 = st * hv.x, h01 = st * hv.y, h10 = st * hv.z, h11 = st * hv.w;
-            y0.x += sv.x * xv.x + sv.y * xv.z - (h00 * xv.y + h01 * xv.w);
-            y0.y += sv.x * xv.y + sv.y * xv.w + (h00 * xv.x + h01 * xv.z);
-            y1.x += sv.z * xv.x + sv.w * xv.z - (h10 * xv.y + h11 * xv.w);
-            y1.y += sv.z * xv.y + sv.w * xv.w + (h10 * xv.x + h11 * xv.z);
+    // window rows outside the radial grid are never copied: zero them once in both stages (the
+    // stored coupling is zero at those band positions, so the direct products need no range test)
+    {
+        const int wlo = lo - (r0 - HO), whi = hi - (r0 - HO);
+        for (int i = tid; i < NST * NOUT; i += 2 * NT + 32) {
+            int sg = i / NOUT, w = i - sg * NOUT;
+            if (w < wlo || w >= whi)
+                reinterpret_cast<float4*>(wring + sg * STAGE32 + TR * ROWF)[w] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    __syncthreads();   // barriers initialised, xs staged
+    // consumer threads: group g = tid / NT, local index lt = tid % NT; for the k-th owned pair group
+    // (k + g) % 2 forms the direct products of row r0 + lt, the other the transposed products of
+    // output row r0 - h + lt, so every warp alternates the roles and both groups finish together
+    const int grp = tid / NT, lt = tid % NT;
+    const int r = r0 + lt;
+    const bool direct_row = tid < 2 * NT && lt < TR && r < n1;
+    __syncthreads();   // barriers initialised, xs staged, window margins zeroed
     float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
     if (warp == 2 * NT / 32) {
         if (lane == 0) {
@@ -186,35 +181,56 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
             }
         }
     } else {
+        // group 0's diagonal block (S + sign i tau H0) x_a, while the first copies are in flight
+        if (grp == 0 && direct_row) {
+            int ks = A.ch_kslot[ch];
+            const float* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
+            const float* Hk = H + ((int64_t)ks * n1 + r) * ROWF;
+            const float* xaf = reinterpret_cast<const float*>(xa);
+            float st = (float)(sign * A.tau);
+#pragma unroll
+            for (int d = 0; d < BDO; d++) {
+                int rr = r + d - HO;
+                if (rr < 0 || rr >= n1) continue;
+                float4 xv = *reinterpret_cast<const float4*>(xaf + 4 * rr);
+                float4 sv = *reinterpret_cast<const float4*>(Sk + d * 4);
+                float4 hv = *reinterpret_cast<const float4*>(Hk + d * 4);
+                float h00 = st * hv.x, h01 = st * hv.y, h10 = st * hv.z, h11 = st * hv.w;
+                d0.x += sv.x * xv.x + sv.y * xv.z - (h00 * xv.y + h01 * xv.w);
+                d0.y += sv.x * xv.y + sv.y * xv.w + (h00 * xv.x + h01 * xv.z);
+                d1.x += sv.z * xv.x + sv.w * xv.z - (h10 * xv.y + h11 * xv.w);
+                d1.y += sv.z * xv.y + sv.w * xv.w + (h10 * xv.x + h11 * xv.z);
+            }
+        }
+        // the coupling sums are accumulated apart from the diagonal block and subtracted at the end
+        float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
         for (int k = 0; k < nown; k++) {
             const int s = k % NST;
             if (!mbar_wait(&full[s], (uint32_t)((k / NST) & 1))) { fail = 1; break; }
-            const int64_t p = spair[s];
             const float* Ws = wring + s * STAGE32;
             const float4* Xs = reinterpret_cast<const float4*>(Ws + TR * ROWF);   // x_b row window
-            if (tid < NT) {
+            if (((k + grp) & 1) == 0) {
                 if (direct_row) {
 #pragma unroll
                     for (int d = 0; d < BDO; d++) {
-                        int rr = r + d - HO;
-                        if (rr < 0 || rr >= n1) continue;
-                        float4 xv = Xs[tid + d];   // row rr = r0 - h + (tid + d)
-                        float4 w = *reinterpret_cast<const float4*>(Ws + tid * ROWF + d * 4);
-                        d0.x = fmaf(w.x, xv.x, d0.x); d0.x = fmaf(w.y, xv.z, d0.x);
-                        d0.y = fmaf(w.x, xv.y, d0.y); d0.y = fmaf(w.y, xv.w, d0.y);
-                        d1.x = fmaf(w.z, xv.x, d1.x); d1.x = fmaf(w.w, xv.z, d1.x);
-                        d1.y = fmaf(w.z, xv.y, d1.y); d1.y = fmaf(w.w, xv.w, d1.y);
+                        float4 xv = Xs[lt + d];   // row rr = r0 - h + (lt + d); zero outside the grid
+                        float4 w = *reinterpret_cast<const float4*>(Ws + lt * ROWF + d * 4);
+                        c0.x = fmaf(w.x, xv.x, c0.x); c0.x = fmaf(w.y, xv.z, c0.x);
+                        c0.y = fmaf(w.x, xv.y, c0.y); c0.y = fmaf(w.y, xv.w, c0.y);
+                        c1.x = fmaf(w.z, xv.x, c1.x); c1.x = fmaf(w.w, xv.z, c1.x);
+                        c1.y = fmaf(w.z, xv.y, c1.y); c1.y = fmaf(w.w, xv.w, c1.y);
                     }
                 }
             } else {
                 // transposed: output row rb = r0 - h + j of channel b from the tile's rows of W_ab
+                const int64_t p = spair[s];
                 float4* pp = part + ((int64_t)p * ntile + tile) * NOUT;
-                const int j = tid - NT;
+                const int j = lt;
                 float2 t0 = make_float2(0.f, 0.f), t1 = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int d = 0; d < BDO; d++) {
+                const int dlo = max(0, j - rows + 1), dhi = min(BDO - 1, j);
+#pragma unroll 1
+                for (int d = dlo; d <= dhi; d++) {
                     int lr = j - d;   // W row r0 + lr couples to column rb through diagonal d
-                    if (lr < 0 || lr >= rows) continue;
                     float4 w = *reinterpret_cast<const float4*>(Ws + lr * ROWF + d * 4);
                     float4 xv = xs[lr];
                     // (W^T)[t][u] = W[u][t]
@@ -228,6 +244,9 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
         }
+        float sg = (float)sign;
+        d0.x = fmaf(-sg, c0.x, d0.x); d0.y = fmaf(-sg, c0.y, d0.y);
+        d1.x = fmaf(-sg, c1.x, d1.x); d1.y = fmaf(-sg, c1.y, d1.y);
     }
     __syncthreads();
     if (fail) {
@@ -239,12 +258,14 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
         }
         return;
     }
-    if (direct_row) {
-        float sg = (float)sign;
-        y0.x = fmaf(-sg, d0.x, y0.x); y0.y = fmaf(-sg, d0.y, y0.y);
-        y1.x = fmaf(-sg, d1.x, y1.x); y1.y = fmaf(-sg, d1.y, y1.y);
+    // group 1's part of the rows to shared memory (the ring is free), group 0 adds it and stores
+    float4* xch = reinterpret_cast<float4*>(wring);
+    if (grp == 1 && direct_row) xch[lt] = make_float4(d0.x, d0.y, d1.x, d1.y);
+    __syncthreads();
+    if (grp == 0 && direct_row) {
+        float4 o1 = xch[lt];
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
-        *reinterpret_cast<float4*>(y + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
+        *reinterpret_cast<float4*>(y + o) = make_float4(d0.x + o1.x, d0.y + o1.y, d1.x + o1.z, d1.y + o1.w);
     }
 }
 
@@ -319,10 +340,11 @@ constexpr int NSTD = 2;          // ring depth of the double-float pass
 constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8;   // floats: hi and lo words, u_b row window
 }
 
-// Warp roles: warps 0..3 direct products (row r0 + tid), warps 4..7 transposed products (output row
-// r0 - h + tid - 128), warp 8 the producer that keeps the NSTD-deep ring of bulk copies filled.  A
-// stage is refilled when all eight consumer warps have released it (an "empty" mbarrier), so the two
-// roles drift freely within the ring instead of meeting at a block barrier for every pair.
+// Warp roles: two groups of four consumer warps alternate the direct products (row r0 + lt) and the
+// transposed products (output row r0 - h + lt) from pair to pair; warp 8 is the producer that keeps
+// the NSTD-deep ring of bulk copies filled.  A stage is refilled when all eight consumer warps have
+// released it (an "empty" mbarrier), so the groups drift freely within the ring instead of meeting
+// at a block barrier for every pair.
 constexpr int NTHR_OWN = 2 * NT + 32;
 
 __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const float4* __restrict__ u,
