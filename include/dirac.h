@@ -159,7 +159,7 @@ dirac_status dirac_solve_batch(dirac_op* const* ops, int n_inst, void* const* ps
 
 /* Schedule autotuner of dirac_solve_batch: for each candidate window cand[0..ncand) and each
  * schedule of the complex64 preconditioner (v = 0: one lane per channel, v = 1: one warp per
- * channel) it times one step of all instances (host clock around launch and completion) from the
+ * channel, the fastest warp schedule available: rotated lanes, else staged, else plain) it times one step of all instances (host clock around launch and completion) from the
  * current states, restoring the states and histories afterwards (it allocates 3 n_i complex128
  * scratch per instance).  The fastest window goes to *best_window and every op keeps the fastest
  * preconditioner schedule (results are identical up to the solver tolerance across schedules; the
@@ -276,9 +276,12 @@ dirac_status dirac_op_set_overlap(dirac_op* op, int enable);
 /* Preconditioner schedule of the complex128 (complex64 = 0) or complex64 (complex64 = 1) solve:
  * 0 one lane per channel (complex64 only; the channels of one kappa share the factor rows),
  * 1 one warp per channel, 2 one warp per channel with the vector and the factor rows staged
- * through shared memory.  dirac_operator_setup times the available ones and keeps the fastest;
- * this call overrides it (DIRAC_E_ARG if the schedule is not available for the op).  Schedules 1
- * and 2 give identical results; 0 rounds differently (within the solver tolerance). */
+ * through shared memory, 3 one warp per channel with each row fixed to one lane (one shuffle
+ * round per row; only factor chunks in shared memory, so every channel's warp is resident at
+ * once).  dirac_operator_setup times the available ones and keeps the fastest; this call
+ * overrides it (DIRAC_E_ARG if the schedule is not available for the op).  Schedules 1, 2 and 3
+ * perform the same operations in the same order; 0 rounds differently (within the solver
+ * tolerance). */
 dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched);
 int dirac_op_get_schedule(const dirac_op* op, int complex64);   /* -1 for a NULL op */
 

@@ -232,7 +232,8 @@ class Operator:
         return self.opts.precision
 
     def set_schedule(self, complex64, sched):
-        """dirac_op_set_schedule: 0 lane / 1 warp / 2 staged-warp preconditioner schedule."""
+        """dirac_op_set_schedule: 0 lane / 1 warp / 2 staged-warp / 3 rotated-lane-warp preconditioner
+        schedule."""
         _check(lib().dirac_op_set_schedule(self._h, int(bool(complex64)), int(sched)), "dirac_op_set_schedule")
 
     def schedule(self, complex64):

@@ -269,12 +269,16 @@ void k_precond_launch(dirac_op* op, const Krylov& K, int mode, const KState* ks,
                                           op->wcnt, mode, ks, r, v, io, z, pn);
         else if (op->prec_sched32 == 2 && op->prec_sm_ok)
             launch_precond_sm_t<float>(op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
+        else if (op->prec_sched32 == 3 && op->prec_rot_ok)
+            launch_precond_rot_t<float>(op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
         else
             launch_precond_t<float>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z,
                                     pn);
     } else {
         if (op->prec_sched64 == 2 && op->prec_sm_ok)
             launch_precond_sm_t<double>(op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
+        else if (op->prec_sched64 == 3 && op->prec_rot_ok)
+            launch_precond_rot_t<double>(op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z, pn);
         else
             launch_precond_t<double>(grid_for(op->ov.nch, 4), op->st, op->ov, K.U, K.L, K.Dinv, mode, ks, r, v, io, z,
                                      pn);
@@ -286,9 +290,11 @@ int prec_parts(const dirac_op* op, const Krylov& K)
     if (K.prec == 1) {
         if (op->prec_sched32 == 0 && op->prec_warps) return op->prec_warps;
         if (op->prec_sched32 == 2 && op->prec_sm_ok) return precond_sm_blocks<float>(op->ov.nch);
+        if (op->prec_sched32 == 3 && op->prec_rot_ok) return precond_rot_blocks<float>(op->ov.nch);
         return grid_for(op->ov.nch, 4);
     }
     if (op->prec_sched64 == 2 && op->prec_sm_ok) return precond_sm_blocks<double>(op->ov.nch);
+    if (op->prec_sched64 == 3 && op->prec_rot_ok) return precond_rot_blocks<double>(op->ov.nch);
     return grid_for(op->ov.nch, 4);
 }
 
@@ -489,11 +495,13 @@ extern "C" int64_t dirac_op_device_bytes(const dirac_op* op) { return op ? (int6
 
 // Preconditioner schedules, picked by timing: one lane per channel (the channels of one kappa share
 // the factor rows read through shared memory), one warp per channel (more parallelism along the
-// band), or one warp per channel with the vector and factor rows staged through shared memory.
+// band), one warp per channel with the vector and factor rows staged through shared memory, or one
+// warp per channel with each row fixed to a lane (one shuffle round per row, factor chunks only in
+// shared memory).
 // Which is fastest depends on the channel count and radial size, so the operator times one
 // application of each on zeroed vectors (after a warm-up) and keeps the fastest, for the complex64
 // inner solve and for the complex128 solve.  The choice does not change results beyond the solver
-// tolerance (lane and warp substitutions round differently; the two warp kernels are identical).
+// tolerance (lane and warp substitutions round differently; the three warp kernels are identical).
 static dirac_status time_precond(dirac_op* op, Krylov& K, int sched, float* ms)
 {
     int& slot = K.prec == 1 ? op->prec_sched32 : op->prec_sched64;
@@ -518,7 +526,7 @@ static std::map<std::tuple<int, int, int, int>, int> g_sched_cache;
 
 static dirac_status tune_precond(dirac_op* op, Krylov& K)
 {
-    auto key = std::make_tuple(op->ov.n1, op->ov.nch, K.prec, (int)op->prec_sm_ok);
+    auto key = std::make_tuple(op->ov.n1, op->ov.nch, K.prec, (int)op->prec_sm_ok * 2 + (int)op->prec_rot_ok);
     {
         std::lock_guard<std::mutex> lock(g_sched_mutex);
         auto it = g_sched_cache.find(key);
@@ -532,10 +540,11 @@ static dirac_status tune_precond(dirac_op* op, Krylov& K)
     CUDA_TRY(cudaMemsetAsync(K.sh, 0, es * (size_t)op->n, op->st));
     float* ms = K.prec == 1 ? op->prec_ms32 : op->prec_ms64;
     int best = -1;
-    for (int sched = 0; sched < 3; sched++) {
+    for (int sched = 0; sched < 4; sched++) {
         ms[sched] = 0;
         if (sched == 0 && (K.prec != 1 || !op->prec_warps)) continue;
         if (sched == 2 && !op->prec_sm_ok) continue;
+        if (sched == 3 && !op->prec_rot_ok) continue;
         dirac_status e = time_precond(op, K, sched, &ms[sched]);
         if (e) return e;
         if (best < 0 || ms[sched] < ms[best]) best = sched;
@@ -922,7 +931,8 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     op->nparts_prec = grid_for(B.nch, 4);                     // ||s||^2 partials, warp-per-channel kernel
     op->nparts_prec32 = op->prec_warps ? op->prec_warps : grid_for(B.nch, 4);   // lane-per-channel kernel
     int np = std::max({op->nparts_apply, op->nparts_own, op->nparts_vec, op->nparts_prec, op->nparts_prec32,
-                       precond_sm_blocks<double>(B.nch), precond_sm_blocks<float>(B.nch)});
+                       precond_sm_blocks<double>(B.nch), precond_sm_blocks<float>(B.nch),
+                       precond_rot_blocks<double>(B.nch), precond_rot_blocks<float>(B.nch)});
     TRY(dev_alloc(op, &op->part_d, (size_t)np));
     TRY(dev_alloc(op, &op->part_d2, (size_t)np));
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
@@ -957,6 +967,9 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     for (int c = 0; c < 3; c++) { pv.w[c] = P.w[c]; pv.wt[c] = P.wt[c]; }
     pv.M = dM;
     op->prec_sm_ok = precond_sm_prepare<float>(n1) == cudaSuccess && precond_sm_prepare<double>(n1) == cudaSuccess;
+    cudaGetLastError();
+    op->prec_rot_ok = bd == 13 && precond_rot_prepare<float>() == cudaSuccess &&
+                      precond_rot_prepare<double>() == cudaSuccess;
     cudaGetLastError();
     {
         dirac_status ts = tune_precond(op, op->k64);
@@ -1000,8 +1013,8 @@ extern "C" dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, voi
 
 extern "C" dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched)
 {
-    if (!op || sched < 0 || sched > 2 || (sched == 0 && (!complex64 || !op->prec_warps)) ||
-        (sched == 2 && !op->prec_sm_ok) || (complex64 && !op->k32.ks)) {
+    if (!op || sched < 0 || sched > 3 || (sched == 0 && (!complex64 || !op->prec_warps)) ||
+        (sched == 2 && !op->prec_sm_ok) || (sched == 3 && !op->prec_rot_ok) || (complex64 && !op->k32.ks)) {
         set_error("dirac_op_set_schedule: schedule not available for this operator");
         return DIRAC_E_ARG;
     }

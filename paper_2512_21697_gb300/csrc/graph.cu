@@ -559,7 +559,8 @@ extern "C" dirac_status dirac_solve_batch(dirac_op* const* ops, int n_inst, void
 }
 
 // Schedule autotuner of the batch: times one step of every instance for each candidate window
-// (instances in flight) and each inner-preconditioner schedule (one lane or one warp per channel),
+// (instances in flight) and each inner-preconditioner schedule (one lane or one warp per channel;
+// the warp schedule is the best available: rotated lanes, else staged, else plain),
 // on saved copies of the states, restores the states and histories, and leaves every op on the
 // fastest preconditioner schedule.  Returns the best window and, per tried configuration, the
 // milliseconds (ms_out[v * ncand + c], v = 0 lanes, 1 warps), when ms_out is given.
@@ -598,9 +599,13 @@ extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void*
     };
     double best = 1e300;
     int bw = cand[0], bv = 0;
+    auto sched_of = [](const dirac_op* op, int v) {
+        if (v == 0) return 0;
+        return op->prec_rot_ok ? 3 : op->prec_sm_ok ? 2 : 1;
+    };
     for (int v = 0; v < 2 && !first; v++) {
         for (int i = 0; i < n_inst; i++) {
-            ops[i]->prec_sched32 = v == 0 ? 0 : 2;
+            ops[i]->prec_sched32 = sched_of(ops[i], v);
             ops[i]->config_gen++;
         }
         restore();
@@ -618,7 +623,7 @@ extern "C" dirac_status dirac_batch_tune(dirac_op* const* ops, int n_inst, void*
     restore();
     for (int i = 0; i < n_inst; i++) {
         if (ops[i]) {
-            ops[i]->prec_sched32 = bv == 0 ? 0 : 2;
+            ops[i]->prec_sched32 = sched_of(ops[i], bv);
             ops[i]->config_gen++;
             if (ops[i]->st) cudaStreamSynchronize(ops[i]->st);
         }

@@ -125,6 +125,13 @@ template <class T>
 void launch_precond_sm_t(cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv, int mode,
                          const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
 
+// rotated-lane warp-per-channel preconditioner (band width 13): factor chunks only in shared memory
+template <class T> cudaError_t precond_rot_prepare();
+template <class T> int precond_rot_blocks(int nch);
+template <class T>
+void launch_precond_rot_t(cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv, int mode,
+                          const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
+
 // complex64 apply with each coupling block read once (owner pass + gather pass, bd = 13)
 size_t apply_own32_smem();
 int apply_own_tile();

@@ -618,6 +618,200 @@ __global__ void k_precond_sm(OpView A, const c2<T>* __restrict__ Ucol, const c2<
     if (part_nrm) block_reduce_store(make_double2(0, 0), nsum, nullptr, part_nrm, blockIdx.x);
 }
 
+// ---------------------------------------------------------------------------------------------
+// Rotated-lane form of the same substitutions: row r of the window lives in lane r mod 32 for
+// its whole life, so the window never shifts.  A forward step j takes the pivot row's value with
+// one shuffle (plus the row-j value for the interchange, in parallel), and the lanes of rows
+// j+1..j+kb subtract L[j] z[j]; a backward step i forms x[i] in lane i mod 32 from its completed
+// sum and broadcasts it with one shuffle to the lanes of rows i-1..i-2kb.  That is one shuffle
+// round per row on the dependency chain (two in the shifting window).  The vector never lives in
+// shared memory: a lane loads the input of its next row (32 rows ahead) when it finishes a row, the
+// forward result goes to z and comes back to the same lane for the backward sweep, so a warp needs
+// only the staged factor chunks and every channel's warp is resident at once.  Same arithmetic,
+// in the same order, as the shifting-window kernels.
+// ---------------------------------------------------------------------------------------------
+template <class T>
+constexpr int prec_rot_warps() { return sizeof(T) == 4 ? 4 : 2; }
+
+template <class T, int KB>
+__host__ __device__ constexpr size_t prec_rot_warp_bytes()
+{
+    return prec_sm_fbytes<T, KB>();
+}
+
+template <class T, int KB>
+__global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2<T>* __restrict__ L,
+                              const c2<T>* __restrict__ Dinv, int mode, const KState* st,
+                              const c2<T>* __restrict__ r, const c2<T>* __restrict__ v, c2<T>* __restrict__ io,
+                              c2<T>* __restrict__ z, double* part_nrm)
+{
+    constexpr int WU = 2 * KB;
+    static_assert(WU + 1 <= 32, "the backward window must fit in a warp");
+    extern __shared__ __align__(16) unsigned char prec_smem[];
+    const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
+    const int n = 2 * A.n1;
+    unsigned char* fb = prec_smem + (size_t)wib * prec_rot_warp_bytes<T, KB>();
+    c2<T>* Lb = reinterpret_cast<c2<T>*>(fb);                          // [2][PCH * KB]
+    int* Pb = reinterpret_cast<int*>(fb + sizeof(c2<T>) * 2 * PCH * KB);  // [2][PCH]
+    c2<T>* Ub = reinterpret_cast<c2<T>*>(fb);                          // [2][PCH * (WU + 1)]
+    c2<T>* Db = Ub + 2 * PCH * (WU + 1);                               // [2][PCH]
+    double nsum = 0;
+    if (warp < A.nch && !(st && st->done)) {
+        const int ch = A.prec_order[warp];
+        const int ks = A.ch_kslot[ch];
+        const c2<T>* Uk = Ucol + (int64_t)ks * n * (WU + 1);
+        const c2<T>* Lk = L + (int64_t)ks * n * KB;
+        const c2<T>* Dk = Dinv + (int64_t)ks * n;
+        const int* P = A.luP + (int64_t)ks * n;
+        const int64_t o = (int64_t)ch * n;
+        auto issue_fwd = [&](int c, int b) {
+            int j0 = c * PCH, rows = min(PCH, n - j0);
+            warp_copy16(Lb + b * PCH * KB, Lk + (int64_t)j0 * KB, rows * KB * (int)sizeof(c2<T>), lane);
+            for (int e = lane; e < rows; e += 32) cp_async4(Pb + b * PCH + e, P + j0 + e);
+            cp_async_commit();
+        };
+        issue_fwd(0, 0);
+        // prologue: the input vector, in global memory (lane l writes and later reads rows l mod 32)
+        const c2<T>* b = r + o;
+        if (mode == 1) {
+            c2<T> beta = from_d<T>(st->beta), omega = from_d<T>(st->omega);
+            for (int i = lane; i < n; i += 32) {
+                c2<T> pv = io[o + i], vv = v[o + i], rv = r[o + i];
+                c2<T> t = cm<T>(omega, vv);
+                c2<T> q = cm<T>(beta, mk<T>(pv.x - t.x, pv.y - t.y));
+                io[o + i] = mk<T>(rv.x + q.x, rv.y + q.y);
+            }
+            b = io + o;
+        } else if (mode == 2) {
+            c2<T> alpha = from_d<T>(st->alpha);
+            for (int i = lane; i < n; i += 32) {
+                c2<T> t = cm<T>(alpha, v[o + i]);
+                c2<T> rv = r[o + i];
+                c2<T> sv = mk<T>(rv.x - t.x, rv.y - t.y);
+                io[o + i] = sv;
+                nsum += (double)sv.x * sv.x + (double)sv.y * sv.y;
+            }
+            b = io + o;
+        }
+        c2<T>* zo = z + o;
+        // forward: lane l holds row j + ((l - j) mod 32); rows j .. j + KB form the window
+        c2<T> nxt = lane < n ? b[lane] : mk<T>(0, 0);   // input of the lane's next row
+        c2<T> w = lane < KB ? nxt : mk<T>(0, 0);
+        const int nc = (n + PCH - 1) / PCH;
+        for (int c = 0; c < nc; c++) {
+            if (c + 1 < nc) {
+                issue_fwd(c + 1, (c + 1) & 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncwarp();
+            const c2<T>* Lc = Lb + (c & 1) * PCH * KB;
+            const int* Pc = Pb + (c & 1) * PCH;
+            const int j0 = c * PCH, rows = min(PCH, n - j0);
+            for (int jj = 0; jj < rows; jj++) {
+                const int j = j0 + jj;
+                const int k = (lane - j) & 31;   // this lane's row is j + k
+                if (k == KB) w = nxt;             // row j + KB enters the window
+                c2<T> lcur = (k >= 1 && k <= KB) ? Lc[jj * KB + k - 1] : mk<T>(0, 0);
+                const int pj = Pc[jj] - j;
+                const int l0 = j & 31, lp = (j + pj) & 31;
+                c2<T> zj = shfl2<T>(w, lp), w0 = shfl2<T>(w, l0);
+                if (lane == lp && pj != 0) w = w0;   // recorded interchange of rows j and j + pj
+                if (k >= 1 && k <= KB && j + k < n) {
+                    w.x -= lcur.x * zj.x - lcur.y * zj.y;
+                    w.y -= lcur.x * zj.y + lcur.y * zj.x;
+                }
+                if (lane == l0) {
+                    zo[j] = zj;
+                    nxt = j + 32 < n ? b[j + 32] : mk<T>(0, 0);
+                }
+            }
+            __syncwarp();   // buffer (c & 1) is refilled by the next iteration's copy
+        }
+        // backward: lane l holds row i - m, m = (i - l) mod 32; rows i - 1 .. i - WU accumulate
+        auto issue_bwd = [&](int c, int bb) {
+            int i0 = c * PCH, rows = min(PCH, n - i0);
+            warp_copy16(Ub + bb * PCH * (WU + 1), Uk + (int64_t)i0 * (WU + 1), rows * (WU + 1) * (int)sizeof(c2<T>),
+                        lane);
+            warp_copy16(Db + bb * PCH, Dk + i0, rows * (int)sizeof(c2<T>), lane);
+            cp_async_commit();
+        };
+        issue_bwd(nc - 1, 0);
+        const int rfirst = (n - 1) - ((n - 1 - lane) & 31);   // the lane's first (highest) row
+        c2<T> zc = rfirst >= 0 ? zo[rfirst] : mk<T>(0, 0);     // forward result of the lane's row
+        c2<T> acc = mk<T>(0, 0), x = mk<T>(0, 0);
+        for (int q = 0; q < nc; q++) {
+            const int c = nc - 1 - q;
+            if (c > 0) {
+                issue_bwd(c - 1, (q + 1) & 1);
+                cp_async_wait1();
+            } else {
+                cp_async_wait0();
+            }
+            __syncwarp();
+            const c2<T>* Uc = Ub + (q & 1) * PCH * (WU + 1);
+            const c2<T>* Dc = Db + (q & 1) * PCH;
+            const int i0 = c * PCH, rows = min(PCH, n - i0);
+            for (int ii = rows - 1; ii >= 0; ii--) {
+                const int i = i0 + ii;
+                const int m = (i - lane) & 31;
+                c2<T> ucur = (m >= 1 && m <= WU && i - m >= 0) ? Uc[ii * (WU + 1) + m] : mk<T>(0, 0);
+                if (m == 0) x = cm<T>(mk<T>(zc.x - acc.x, zc.y - acc.y), Dc[ii]);
+                c2<T> xi = shfl2<T>(x, i & 31);
+                if (m >= 1 && m <= WU) {
+                    acc.x += ucur.x * xi.x - ucur.y * xi.y;
+                    acc.y += ucur.x * xi.y + ucur.y * xi.x;
+                }
+                if (m == 0) {
+                    zo[i] = xi;
+                    acc = mk<T>(0, 0);                               // the lane's next row: i - 32
+                    zc = i - 32 >= 0 ? zo[i - 32] : mk<T>(0, 0);
+                }
+            }
+            __syncwarp();
+        }
+    }
+    if (part_nrm) block_reduce_store(make_double2(0, 0), nsum, nullptr, part_nrm, blockIdx.x);
+}
+
+template <class T>
+size_t precond_rot_smem()
+{
+    return (size_t)prec_rot_warps<T>() * prec_rot_warp_bytes<T, 13>();
+}
+
+template <class T>
+cudaError_t precond_rot_prepare()
+{
+    return cudaFuncSetAttribute(k_precond_rot<T, 13>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)precond_rot_smem<T>());
+}
+
+template <class T>
+int precond_rot_blocks(int nch)
+{
+    return (nch + prec_rot_warps<T>() - 1) / prec_rot_warps<T>();
+}
+
+template <class T>
+void launch_precond_rot_t(cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv, int mode,
+                          const KState* ks, const void* r, const void* v, void* io, void* z, double* pn)
+{
+    k_precond_rot<T, 13><<<precond_rot_blocks<T>(A.nch), 32 * prec_rot_warps<T>(), precond_rot_smem<T>(), st>>>(
+        A, (const c2<T>*)U, (const c2<T>*)L, (const c2<T>*)Dinv, mode, ks, (const c2<T>*)r, (const c2<T>*)v,
+        (c2<T>*)io, (c2<T>*)z, pn);
+}
+template cudaError_t precond_rot_prepare<double>();
+template cudaError_t precond_rot_prepare<float>();
+template int precond_rot_blocks<double>(int);
+template int precond_rot_blocks<float>(int);
+template void launch_precond_rot_t<double>(cudaStream_t, const OpView&, const void*, const void*, const void*, int,
+                                           const KState*, const void*, const void*, void*, void*, double*);
+template void launch_precond_rot_t<float>(cudaStream_t, const OpView&, const void*, const void*, const void*, int,
+                                          const KState*, const void*, const void*, void*, void*, double*);
+
 template <class T>
 size_t precond_sm_smem(int n1)
 {

@@ -53,7 +53,8 @@ struct dirac_op {
     // 1 one warp per channel, 2 one warp per channel with shared-memory staging
     int prec_sched32 = 0, prec_sched64 = 1;
     bool prec_sm_ok = false;     // the staged kernel fits this radial size
-    float prec_ms32[3] = {0, 0, 0}, prec_ms64[3] = {0, 0, 0};
+    bool prec_rot_ok = false;    // the rotated-lane kernel is set up (band width 13)
+    float prec_ms32[4] = {0, 0, 0, 0}, prec_ms64[4] = {0, 0, 0, 0};
     int config_gen = 0;          // bumped when a launch choice changes (captured graphs are rebuilt)
     int *wks = nullptr, *wfirst = nullptr, *wcnt = nullptr;
     std::vector<void*> allocs;

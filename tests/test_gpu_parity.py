@@ -70,9 +70,9 @@ def test_apply_matches_oracle(case):
             assert np.all(y[~case.orc.active_mask()] == 0)
 
 
-@pytest.mark.parametrize("sched", [1, 2])
+@pytest.mark.parametrize("sched", [1, 2, 3])
 def test_precond_matches_oracle(case, sched):
-    # both complex128 schedules (warp per channel; warp per channel staged through shared memory)
+    # the complex128 schedules (warp per channel; staged through shared memory; rows fixed to lanes)
     r = case.random(2)
     rd = case.to_dev(r)
     zd = case.torch.empty_like(rd)
@@ -83,14 +83,21 @@ def test_precond_matches_oracle(case, sched):
     z = case.from_dev(zd)
     ref = case.orc.precond(r)
     assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+    if sched == 3:
+        # the same operations in the same order as the shifting-window warp kernel
+        z1 = case.torch.empty_like(rd)
+        case.op.set_schedule(False, 1)
+        case.op.precond(rd, z1)
+        case.op.set_schedule(False, keep)
+        assert case.torch.equal(zd, z1)
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2])
+@pytest.mark.parametrize("sched", [0, 1, 2, 3])
 @pytest.mark.parametrize("name", ["small", "tail"])
 def test_mixed_step_each_precond_schedule(oracle_mod, name, sched):
     # the complex64 inner solve with every preconditioner schedule: the refinement ends on the
     # accurate residual, so the step meets the FP64 parity bar whichever schedule the inner solve
-    # used; the two warp schedules give bitwise identical states
+    # used; the three warp schedules give bitwise identical states
     cfg = W.WORKLOADS[name]
     c = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
     c.op.set_schedule(True, sched)
@@ -103,7 +110,7 @@ def test_mixed_step_each_precond_schedule(oracle_mod, name, sched):
         ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
     assert np.all(res <= STEP_TOL)
     assert np.linalg.norm(c.from_dev(psid) - ref) <= 1e-10 * np.linalg.norm(ref)
-    if sched == 2:
+    if sched in (2, 3):
         c2 = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
         c2.op.set_schedule(True, 1)
         pd2 = c2.to_dev(psi0)
