@@ -710,7 +710,9 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
             const c2<T>* Lc = Lb + (c & 1) * PCH * KB;
             const int* Pc = Pb + (c & 1) * PCH;
             const int j0 = c * PCH, rows = min(PCH, n - j0);
-            for (int jj = 0; jj < rows; jj++) {
+#pragma unroll
+            for (int jj = 0; jj < PCH; jj++) {
+                if (jj >= rows) break;
                 const int j = j0 + jj;
                 const int k = (lane - j) & 31;   // this lane's row is j + k
                 if (k == KB) w = nxt;             // row j + KB enters the window
@@ -754,7 +756,10 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
             const c2<T>* Uc = Ub + (q & 1) * PCH * (WU + 1);
             const c2<T>* Dc = Db + (q & 1) * PCH;
             const int i0 = c * PCH, rows = min(PCH, n - i0);
-            for (int ii = rows - 1; ii >= 0; ii--) {
+#pragma unroll
+            for (int iq = 0; iq < PCH; iq++) {
+                const int ii = rows - 1 - iq;
+                if (ii < 0) break;
                 const int i = i0 + ii;
                 const int m = (i - lane) & 31;
                 c2<T> ucur = (m >= 1 && m <= WU && i - m >= 0) ? Uc[ii * (WU + 1) + m] : mk<T>(0, 0);
