@@ -624,19 +624,21 @@ __global__ void k_precond_sm(OpView A, const c2<T>* __restrict__ Ucol, const c2<
 // one shuffle (plus the row-j value for the interchange, in parallel), and the lanes of rows
 // j+1..j+kb subtract L[j] z[j]; a backward step i forms x[i] in lane i mod 32 from its completed
 // sum and broadcasts it with one shuffle to the lanes of rows i-1..i-2kb.  That is one shuffle
-// round per row on the dependency chain (two in the shifting window).  The vector never lives in
-// shared memory: a lane loads the input of its next row (32 rows ahead) when it finishes a row, the
-// forward result goes to z and comes back to the same lane for the backward sweep, so a warp needs
-// only the staged factor chunks and every channel's warp is resident at once.  Same arithmetic,
-// in the same order, as the shifting-window kernels.
+// round per row on the dependency chain (two in the shifting window).  The vector never lives
+// whole in shared memory: 16-row chunks of the input (forward) and of the forward result
+// (backward) arrive by cp.async together with the factor chunks, so a warp needs a few KB and
+// every channel's warp is resident at once.  The forward result goes to z and comes back for the
+// backward sweep.  Same arithmetic, in the same order, as the shifting-window kernels.
 // ---------------------------------------------------------------------------------------------
 template <class T>
 constexpr int prec_rot_warps() { return sizeof(T) == 4 ? 4 : 2; }
 
+constexpr int ROT_VRING = 4;   // vector chunks in flight per warp (forward input, backward z)
+
 template <class T, int KB>
 __host__ __device__ constexpr size_t prec_rot_warp_bytes()
 {
-    return prec_sm_fbytes<T, KB>();
+    return prec_sm_fbytes<T, KB>() + sizeof(c2<T>) * ROT_VRING * PCH;
 }
 
 template <class T, int KB>
@@ -646,7 +648,7 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
                               c2<T>* __restrict__ z, double* part_nrm)
 {
     constexpr int WU = 2 * KB;
-    static_assert(WU + 1 <= 32, "the backward window must fit in a warp");
+    static_assert(WU + 1 <= 32 && KB < PCH, "the windows must fit in a warp and reach one chunk ahead");
     extern __shared__ __align__(16) unsigned char prec_smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int warp = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -656,6 +658,7 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
     int* Pb = reinterpret_cast<int*>(fb + sizeof(c2<T>) * 2 * PCH * KB);  // [2][PCH]
     c2<T>* Ub = reinterpret_cast<c2<T>*>(fb);                          // [2][PCH * (WU + 1)]
     c2<T>* Db = Ub + 2 * PCH * (WU + 1);                               // [2][PCH]
+    c2<T>* Vb = reinterpret_cast<c2<T>*>(fb + prec_sm_fbytes<T, KB>());  // [ROT_VRING][PCH]
     double nsum = 0;
     if (warp < A.nch && !(st && st->done)) {
         const int ch = A.prec_order[warp];
@@ -665,14 +668,7 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
         const c2<T>* Dk = Dinv + (int64_t)ks * n;
         const int* P = A.luP + (int64_t)ks * n;
         const int64_t o = (int64_t)ch * n;
-        auto issue_fwd = [&](int c, int b) {
-            int j0 = c * PCH, rows = min(PCH, n - j0);
-            warp_copy16(Lb + b * PCH * KB, Lk + (int64_t)j0 * KB, rows * KB * (int)sizeof(c2<T>), lane);
-            for (int e = lane; e < rows; e += 32) cp_async4(Pb + b * PCH + e, P + j0 + e);
-            cp_async_commit();
-        };
-        issue_fwd(0, 0);
-        // prologue: the input vector, in global memory (lane l writes and later reads rows l mod 32)
+        // prologue: the input vector, in global memory
         const c2<T>* b = r + o;
         if (mode == 1) {
             c2<T> beta = from_d<T>(st->beta), omega = from_d<T>(st->omega);
@@ -694,11 +690,25 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
             }
             b = io + o;
         }
+        __syncwarp();   // the prologue's stores are visible to the warp's copies below
         c2<T>* zo = z + o;
-        // forward: lane l holds row j + ((l - j) mod 32); rows j .. j + KB form the window
-        c2<T> nxt = lane < n ? b[lane] : mk<T>(0, 0);   // input of the lane's next row
-        c2<T> w = lane < KB ? nxt : mk<T>(0, 0);
         const int nc = (n + PCH - 1) / PCH;
+        auto copy_vec = [&](const c2<T>* src, int c) {   // vector chunk c (rows < n) into its ring slot
+            int j0 = c * PCH, rows = min(PCH, n - j0);
+            if (rows > 0) warp_copy16(Vb + (c % ROT_VRING) * PCH, src + j0, rows * (int)sizeof(c2<T>), lane);
+        };
+        // forward group c: factor chunk c and input chunk c + 1 (input chunk 0 goes with group 0)
+        auto issue_fwd = [&](int c, int bb) {
+            int j0 = c * PCH, rows = min(PCH, n - j0);
+            warp_copy16(Lb + bb * PCH * KB, Lk + (int64_t)j0 * KB, rows * KB * (int)sizeof(c2<T>), lane);
+            for (int e = lane; e < rows; e += 32) cp_async4(Pb + bb * PCH + e, P + j0 + e);
+            if (c == 0) copy_vec(b, 0);
+            copy_vec(b, c + 1);
+            cp_async_commit();
+        };
+        issue_fwd(0, 0);
+        // forward: lane l holds row j + ((l - j) mod 32); rows j .. j + KB form the window
+        c2<T> w = mk<T>(0, 0);
         for (int c = 0; c < nc; c++) {
             if (c + 1 < nc) {
                 issue_fwd(c + 1, (c + 1) & 1);
@@ -707,6 +717,7 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
                 cp_async_wait0();
             }
             __syncwarp();
+            if (c == 0 && lane < KB && lane < n) w = Vb[lane];   // rows 0 .. KB - 1 start the window
             const c2<T>* Lc = Lb + (c & 1) * PCH * KB;
             const int* Pc = Pb + (c & 1) * PCH;
             const int j0 = c * PCH, rows = min(PCH, n - j0);
@@ -715,7 +726,9 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
                 if (jj >= rows) break;
                 const int j = j0 + jj;
                 const int k = (lane - j) & 31;   // this lane's row is j + k
-                if (k == KB) w = nxt;             // row j + KB enters the window
+                // row j + KB enters the window: its input, from chunk c or c + 1 of the ring
+                const c2<T> vin = Vb[((c + (jj + KB) / PCH) % ROT_VRING) * PCH + (jj + KB) % PCH];
+                if (k == KB) w = vin;
                 c2<T> lcur = (k >= 1 && k <= KB) ? Lc[jj * KB + k - 1] : mk<T>(0, 0);
                 const int pj = Pc[jj] - j;
                 const int l0 = j & 31, lp = (j + pj) & 31;
@@ -725,24 +738,22 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
                     w.x -= lcur.x * zj.x - lcur.y * zj.y;
                     w.y -= lcur.x * zj.y + lcur.y * zj.x;
                 }
-                if (lane == l0) {
-                    zo[j] = zj;
-                    nxt = j + 32 < n ? b[j + 32] : mk<T>(0, 0);
-                }
+                if (lane == l0) zo[j] = zj;
             }
-            __syncwarp();   // buffer (c & 1) is refilled by the next iteration's copy
+            __syncwarp();   // buffers (c & 1) and ring slot c are refilled by later copies
         }
-        // backward: lane l holds row i - m, m = (i - l) mod 32; rows i - 1 .. i - WU accumulate
+        __syncwarp();   // the forward results are visible to the warp's copies below
+        // backward group q (chunk c = nc - 1 - q): factor chunk c and forward-result chunk c
         auto issue_bwd = [&](int c, int bb) {
             int i0 = c * PCH, rows = min(PCH, n - i0);
             warp_copy16(Ub + bb * PCH * (WU + 1), Uk + (int64_t)i0 * (WU + 1), rows * (WU + 1) * (int)sizeof(c2<T>),
                         lane);
             warp_copy16(Db + bb * PCH, Dk + i0, rows * (int)sizeof(c2<T>), lane);
+            copy_vec(zo, c);
             cp_async_commit();
         };
         issue_bwd(nc - 1, 0);
-        const int rfirst = (n - 1) - ((n - 1 - lane) & 31);   // the lane's first (highest) row
-        c2<T> zc = rfirst >= 0 ? zo[rfirst] : mk<T>(0, 0);     // forward result of the lane's row
+        // backward: lane l holds row i - m, m = (i - l) mod 32; rows i - 1 .. i - WU accumulate
         c2<T> acc = mk<T>(0, 0), x = mk<T>(0, 0);
         for (int q = 0; q < nc; q++) {
             const int c = nc - 1 - q;
@@ -755,6 +766,7 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
             __syncwarp();
             const c2<T>* Uc = Ub + (q & 1) * PCH * (WU + 1);
             const c2<T>* Dc = Db + (q & 1) * PCH;
+            const c2<T>* Zc = Vb + (c % ROT_VRING) * PCH;
             const int i0 = c * PCH, rows = min(PCH, n - i0);
 #pragma unroll
             for (int iq = 0; iq < PCH; iq++) {
@@ -763,7 +775,8 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
                 const int i = i0 + ii;
                 const int m = (i - lane) & 31;
                 c2<T> ucur = (m >= 1 && m <= WU && i - m >= 0) ? Uc[ii * (WU + 1) + m] : mk<T>(0, 0);
-                if (m == 0) x = cm<T>(mk<T>(zc.x - acc.x, zc.y - acc.y), Dc[ii]);
+                const c2<T> zi = Zc[ii], di = Dc[ii];
+                if (m == 0) x = cm<T>(mk<T>(zi.x - acc.x, zi.y - acc.y), di);
                 c2<T> xi = shfl2<T>(x, i & 31);
                 if (m >= 1 && m <= WU) {
                     acc.x += ucur.x * xi.x - ucur.y * xi.y;
@@ -771,8 +784,7 @@ __global__ void k_precond_rot(OpView A, const c2<T>* __restrict__ Ucol, const c2
                 }
                 if (m == 0) {
                     zo[i] = xi;
-                    acc = mk<T>(0, 0);                               // the lane's next row: i - 32
-                    zc = i - 32 >= 0 ? zo[i - 32] : mk<T>(0, 0);
+                    acc = mk<T>(0, 0);   // the lane's next row is i - 32
                 }
             }
             __syncwarp();
