@@ -155,15 +155,16 @@ void launch_assemble_set(dirac_op* op, cudaStream_t st, const AsmSet& a)
     int be = op->ov.n1 * op->ov.bd * 4;
     k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, st>>>(op->pv, be, a.s, a.Gdf);
     if (op->npairs) {
-        k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, st>>>(
-            op->ov, be, a.Gdf, a.Kdf, a.KTdf);
-        if (op->asm_chunks)
+        if (op->asm_chunks) {
             launch_assemble_grp_df(st, op->ov, op->asm_chunks, op->asm_nchunks, op->asm_gpair, op->asm_gcoef,
-                                   a.Kdf, a.KTdf, a.Wh, a.Wl);
-        else
+                                   a.Gdf, a.Wh, a.Wl);
+        } else {
+            k_build_K_df<<<dim3(grid_for(be, 256), (unsigned)std::min(op->ov.nkeys, 65535)), 256, 0, st>>>(
+                op->ov, be, a.Gdf, a.Kdf, a.KTdf);
             launch_assemble_df(dim3(grid_for((int64_t)op->ov.n1 * op->ov.bd, 128),
                                     (unsigned)std::min<int64_t>(op->npairs, 65535)),
                                st, op->ov, a.Kdf, a.KTdf, op->cab_df, a.Wh, a.Wl);
+        }
     }
 }
 
@@ -838,11 +839,7 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
                     ch.nl = (int)ls.size();
                     ch.ka = ka;
                     ch.kb = kb;
-                    for (int m = 0; m < ASM_MAX_NL; m++) {
-                        int l = m < ch.nl ? ls[m] : ls[0];
-                        ch.kd[m] = key_index(ka, kb, l);
-                        ch.kt[m] = key_index(kb, ka, l);
-                    }
+                    for (int m = 0; m < ASM_MAX_NL; m++) ch.l[m] = m < ch.nl ? ls[m] : ls[0];
                     chunks.push_back(ch);
                     for (int64_t u = c0; u < c1; u++) {
                         int q = porder[u];
@@ -865,8 +862,10 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
             }
         }
         TRY(dev_alloc(op, &op->Gdf, (size_t)P.L * 4 * be));
-        TRY(dev_alloc(op, &op->Kdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
-        TRY(dev_alloc(op, &op->KTdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
+        if (!op->asm_chunks) {   // the per-pair assembly reads combined K bands; the grouped one forms them
+            TRY(dev_alloc(op, &op->Kdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
+            TRY(dev_alloc(op, &op->KTdf, (size_t)std::max<size_t>(keyl.size(), 1) * be));
+        }
         TRY(dev_alloc(op, &op->Wh, (size_t)std::max<int64_t>(op->npairs, 1) * be));
         TRY(dev_alloc(op, &op->Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be));
         TRY(dev_alloc(op, &op->xsplit, (size_t)op->n));
@@ -1058,8 +1057,8 @@ extern "C" dirac_status dirac_op_set_overlap(dirac_op* op, int enable)
         dirac_status e;
         if ((e = dev_alloc(op, &a.t_eval, 1)) || (e = dev_alloc(op, &a.s, (size_t)op->pv.L * 3)) ||
             (e = dev_alloc(op, &a.Gdf, (size_t)op->pv.L * 4 * be)) ||
-            (e = dev_alloc(op, &a.Kdf, (size_t)std::max(op->ov.nkeys, 1) * be)) ||
-            (e = dev_alloc(op, &a.KTdf, (size_t)std::max(op->ov.nkeys, 1) * be)) ||
+            (!op->asm_chunks && (e = dev_alloc(op, &a.Kdf, (size_t)std::max(op->ov.nkeys, 1) * be))) ||
+            (!op->asm_chunks && (e = dev_alloc(op, &a.KTdf, (size_t)std::max(op->ov.nkeys, 1) * be))) ||
             (e = dev_alloc(op, &a.Wh, (size_t)std::max<int64_t>(op->npairs, 1) * be)) ||
             (e = dev_alloc(op, &a.Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be)))
             return e;

@@ -53,13 +53,13 @@ struct OpView {
 };
 
 // One chunk of a (kappa_a, kappa_b) pair group for the grouped double-float assembly: pairs
-// first .. first + count - 1 of the group-ordered pair list, their nl multipoles' direct and
-// transposed band keys (increasing l).
+// first .. first + count - 1 of the group-ordered pair list and the group's nl multipoles
+// (increasing l).
 constexpr int ASM_MAX_NL = 4;
-constexpr int ASM_CHUNK = 32;
+constexpr int ASM_CHUNK = 64;
 struct AsmChunk {
     int first, count, nl, ka, kb;
-    int kd[ASM_MAX_NL], kt[ASM_MAX_NL];
+    int l[ASM_MAX_NL];
 };
 
 struct PulseView {

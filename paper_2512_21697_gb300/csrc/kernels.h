@@ -65,7 +65,7 @@ void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float
 // grouped assembly: grid (positions / 128, chunks); gpair/gcoef in group order, ASM_MAX_NL
 // (cA hi, cA lo, cB hi, cB lo) per pair
 void launch_assemble_grp_df(cudaStream_t st, const OpView& A, const AsmChunk* chunks, int nchunks, const int* gpair,
-                            const float4* gcoef, const float2* K, const float2* KT, float* Wh, float* Wl);
+                            const float4* gcoef, const float2* G, float* Wh, float* Wl);
 __global__ void k_split_uv3(int64_t n, const double2* psi, const double2* x, float4* u, float4* v, float2* psi32);
 __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
                            float4* __restrict__ u, float4* __restrict__ v);

@@ -133,36 +133,61 @@ void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float
 
 // Grouped form of the same assembly.  The pairs of one (kappa_a, kappa_b) group (all mu) combine
 // the same K_l(ka, kb) and KT_l(kb, ka) bands with their own angular coefficients, so a block
-// takes 128 (radial row, block diagonal) positions of one chunk of a group, holds the group's
-// bands at its positions in registers and writes the coupling values of every pair of the chunk:
-// the bands are read once per chunk instead of once per pair.  Each pair's sum runs over the
-// group's multipoles in increasing l, direct band first, as k_assemble_df; a multipole the pair
-// lacks has zero coefficients.  NL = multipoles of the group (1..ASM_MAX_NL).
+// takes 128 (radial row, block diagonal) positions of one chunk of a group, forms the group's
+// bands at its positions from G (as k_build_K_df: K = sum_n m_n G^n_l with m = 1, k', k, k'k,
+// rounded to double-float; KT from the block-transposed position) and keeps them in registers,
+// then writes the coupling values of every pair of the chunk.  G is a few MB and stays in L2; the
+// combined bands are never stored.  Each pair's sum runs over the group's multipoles in
+// increasing l, direct band first, as k_assemble_df; a multipole the pair lacks has zero
+// coefficients.  NL = multipoles of the group (1..ASM_MAX_NL).
+__device__ __forceinline__ float4 df_round2(const DfAcc& a, const DfAcc& b)
+{
+    float ha = a.s + a.c, hb = b.s + b.c;
+    return make_float4(ha, (a.s - ha) + a.c, hb, (b.s - hb) + b.c);
+}
+
 template <int BD, int NL>
 __device__ __forceinline__ void assemble_grp_body(const OpView& A, const AsmChunk& ch, const int* sp,
-                                                  const float4* sc, int idx, const float2* __restrict__ K,
-                                                  const float2* __restrict__ KT, float* __restrict__ Wh,
-                                                  float* __restrict__ Wl)
+                                                  const float4* sc, int idx, const float2* __restrict__ G,
+                                                  float* __restrict__ Wh, float* __restrict__ Wl)
 {
     const int bd = BD > 0 ? BD : A.bd;
     const int half = (bd - 1) / 2;
     const int nrd = A.n1 * bd;
+    const int64_t be = (int64_t)nrd * 4;   // elements of one band
     int r = idx / bd, d = idx - r * bd, rr = r + d - half;
     bool inb = rr >= 0 && rr < A.n1;
     bool keep[4];
     for (int k = 0; k < 4; k++)
         keep[k] = inb && used_fn_df(ch.ka, r, k / 2) && used_fn_df(ch.kb, rr, k % 2);
-    const int64_t nb = (int64_t)nrd * 4;
+    const int idxt = inb ? rr * bd + (2 * half - d) : 0;   // block-transposed position
+    const float mk[4] = {1.f, (float)ch.ka, (float)ch.kb, (float)(ch.ka * ch.kb)};
+    const float mt[4] = {1.f, (float)ch.kb, (float)ch.ka, (float)(ch.ka * ch.kb)};
     float4 g[NL][2], h[NL][2];   // (hi, lo) pairs of the 4 block entries, direct and transposed band
 #pragma unroll
     for (int j = 0; j < NL; j++) {
-        if (inb) {
-            const float4* gp = reinterpret_cast<const float4*>(K + ch.kd[j] * nb + (int64_t)idx * 4);
-            const float4* hp = reinterpret_cast<const float4*>(KT + ch.kt[j] * nb + (int64_t)idx * 4);
-            g[j][0] = gp[0]; g[j][1] = gp[1]; h[j][0] = hp[0]; h[j][1] = hp[1];
-        } else {
-            g[j][0] = g[j][1] = h[j][0] = h[j][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4* Gl = reinterpret_cast<const float4*>(G + (int64_t)ch.l[j] * 4 * be);
+        DfAcc kd[4], kt[4];
+        for (int k = 0; k < 4; k++) { df_zero(kd[k]); df_zero(kt[k]); }
+        for (int n = 0; n < 4; n++) {
+            const float4* Gn = Gl + n * be / 2;
+            float4 a0 = Gn[2 * idx], a1 = Gn[2 * idx + 1];   // entries (0,0), (0,1) | (1,0), (1,1)
+            df_fma(kd[0], mk[n], 0.f, a0.x, a0.y);
+            df_fma(kd[1], mk[n], 0.f, a0.z, a0.w);
+            df_fma(kd[2], mk[n], 0.f, a1.x, a1.y);
+            df_fma(kd[3], mk[n], 0.f, a1.z, a1.w);
+            if (inb) {   // KT[t][u] = K[u][t] at the transposed position
+                float4 b0 = Gn[2 * idxt], b1 = Gn[2 * idxt + 1];
+                df_fma(kt[0], mt[n], 0.f, b0.x, b0.y);
+                df_fma(kt[1], mt[n], 0.f, b1.x, b1.y);
+                df_fma(kt[2], mt[n], 0.f, b0.z, b0.w);
+                df_fma(kt[3], mt[n], 0.f, b1.z, b1.w);
+            }
         }
+        g[j][0] = df_round2(kd[0], kd[1]);
+        g[j][1] = df_round2(kd[2], kd[3]);
+        h[j][0] = df_round2(kt[0], kt[1]);
+        h[j][1] = df_round2(kt[2], kt[3]);
     }
     for (int q = 0; q < ch.count; q++) {
         int64_t p = sp[q];
@@ -196,8 +221,7 @@ template <int BD>
 __global__ void __launch_bounds__(128) k_assemble_grp_df(OpView A, const AsmChunk* __restrict__ chunks, int nchunks,
                                                          const int* __restrict__ gpair,
                                                          const float4* __restrict__ gcoef,
-                                                         const float2* __restrict__ K,
-                                                         const float2* __restrict__ KT, float* __restrict__ Wh,
+                                                         const float2* __restrict__ G, float* __restrict__ Wh,
                                                          float* __restrict__ Wl)
 {
     __shared__ int sp[ASM_CHUNK];
@@ -214,22 +238,21 @@ __global__ void __launch_bounds__(128) k_assemble_grp_df(OpView A, const AsmChun
         __syncthreads();
         if (!act) continue;
         switch (ch.nl) {
-        case 1: assemble_grp_body<BD, 1>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
-        case 2: assemble_grp_body<BD, 2>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
-        case 3: assemble_grp_body<BD, 3>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
-        default: assemble_grp_body<BD, 4>(A, ch, sp, sc, idx, K, KT, Wh, Wl); break;
+        case 1: assemble_grp_body<BD, 1>(A, ch, sp, sc, idx, G, Wh, Wl); break;
+        case 2: assemble_grp_body<BD, 2>(A, ch, sp, sc, idx, G, Wh, Wl); break;
+        case 3: assemble_grp_body<BD, 3>(A, ch, sp, sc, idx, G, Wh, Wl); break;
+        default: assemble_grp_body<BD, 4>(A, ch, sp, sc, idx, G, Wh, Wl); break;
         }
     }
 }
 
 void launch_assemble_grp_df(cudaStream_t st, const OpView& A, const AsmChunk* chunks, int nchunks, const int* gpair,
-                            const float4* gcoef, const float2* K, const float2* KT, float* Wh, float* Wl)
+                            const float4* gcoef, const float2* G, float* Wh, float* Wl)
 {
     dim3 grid((unsigned)((A.n1 * A.bd + 127) / 128), (unsigned)std::min(nchunks, 65535));
-    if (A.bd == 13) k_assemble_grp_df<13><<<grid, 128, 0, st>>>(A, chunks, nchunks, gpair, gcoef, K, KT, Wh, Wl);
-    else k_assemble_grp_df<0><<<grid, 128, 0, st>>>(A, chunks, nchunks, gpair, gcoef, K, KT, Wh, Wl);
+    if (A.bd == 13) k_assemble_grp_df<13><<<grid, 128, 0, st>>>(A, chunks, nchunks, gpair, gcoef, G, Wh, Wl);
+    else k_assemble_grp_df<0><<<grid, 128, 0, st>>>(A, chunks, nchunks, gpair, gcoef, G, Wh, Wl);
 }
-
 
 // u = psi + x, v = psi - x in double, each split into (re_hi, re_lo, im_hi, im_lo)
 __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
