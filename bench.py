@@ -129,7 +129,8 @@ FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x
 # on the medium workload (6944 pairs x 601 radial slots), scaled to the production launch by the
 # units processed (pairs x slots: x 9.817); the summaries under profiles/ give the commands and the
 # raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
-TRAFFIC_MEDIUM = {"df": (1.762372e9 + 0.155071e9, "profiles/k_residual_own_df_medium.md")}
+TRAFFIC_MEDIUM = {"df": (1.762372e9 + 0.155071e9, "profiles/k_residual_own_df_medium.md"),
+                  "f32": (0.886455e9 + 0.075098e9, "profiles/k_apply_own32_medium.md")}
 MEDIUM_UNITS = 6944 * 601
 DF_OPS_PER_FMA = 12                 # FP32 operations of one double-float multiply-add (TwoProd + TwoSum)
 
@@ -491,8 +492,8 @@ def batch_bench(args, world, rank, local, dist):
                                "tol=1e-10, start %s" % (n_inst, args.batch_n, "at each instance's peak field"
                                                         if peak else "at the pulse start"),
                    "unknowns": int(sum(b.n for _, b in used)), "window": best,
-                   "precond_schedule": "tuned (lane or staged warp per channel)",
-                   "tune_ms": {"windows": cand, "lanes": tune_ms[0].tolist(), "staged_warps": tune_ms[1].tolist()},
+                   "precond_schedule": "tuned (one lane per channel, or one warp per channel with rows fixed to lanes)",
+                   "tune_ms": {"windows": cand, "lanes": tune_ms[0].tolist(), "warps": tune_ms[1].tolist()},
                    "setup_s": t_setup, "timing": "host wall clock around the batch call (many streams)",
                    "parallelism": "replicas x%d" % world},
         "batch": out,
