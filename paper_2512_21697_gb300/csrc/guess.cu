@@ -68,49 +68,82 @@ __global__ void k_guess_field(PulseView P, double t_start, int step, double dt, 
 // one thread per position (channel, radial slot): backward differences D_0..D_3 of the four
 // states, their rms m_k, x = [D_k / m_k, clip(log10(m_j / m_3)) / 10, field, kappa / 10, 2 mu / 20],
 // s = m_3
-__global__ void k_guess_features(int nch, int n1, const int* __restrict__ kappa, const int* __restrict__ two_mu,
-                                 const double2* __restrict__ p0, const double2* __restrict__ p1,
-                                 const double2* __restrict__ p2, const double2* __restrict__ p3,
-                                 const float* __restrict__ F, float* __restrict__ X, float* __restrict__ S,
-                                 const int* gate)
+// Features of one position (one thread), written through shared memory so that a warp stores
+// whole 512-byte runs of X.  The backward differences need FP64 (they cancel to ~1e-6 of the
+// states); everything after them runs in FP32 on a copy scaled by an exact power of two taken
+// from the largest difference, so that neither the squares nor the normalisation under- or
+// overflow (GB300's FP64 rate is 1/64 of FP32: a double sqrt, division and log10 per feature
+// cost more than the rest of the guess).  The rms, the normalised differences and the log-ratios
+// match the FP64 definition to FP32 rounding.
+constexpr int GF_THREADS = 256;
+__global__ void __launch_bounds__(GF_THREADS) k_guess_features(int nch, int n1, const int* __restrict__ kappa,
+                                                               const int* __restrict__ two_mu,
+                                                               const double2* __restrict__ p0,
+                                                               const double2* __restrict__ p1,
+                                                               const double2* __restrict__ p2,
+                                                               const double2* __restrict__ p3,
+                                                               const float* __restrict__ F, float* __restrict__ X,
+                                                               float* __restrict__ S, const int* gate)
 {
+    __shared__ float xs[GF_THREADS * (GN_IN + 1)];   // +1: conflict-free column access
     if (gate && !*gate) return;   // uniform: the graph's step has too few past states
-    int64_t pos = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pos >= (int64_t)nch * n1) return;
-    int ch = (int)(pos / n1);
-    double D[4][4];
-    for (int t = 0; t < 2; t++) {
-        double2 a = p0[2 * pos + t], b = p1[2 * pos + t], c = p2[2 * pos + t], d = p3[2 * pos + t];
-        double re[4] = {a.x, a.x - b.x, a.x - 2.0 * b.x + c.x, a.x - 3.0 * b.x + 3.0 * c.x - d.x};
-        double im[4] = {a.y, a.y - b.y, a.y - 2.0 * b.y + c.y, a.y - 3.0 * b.y + 3.0 * c.y - d.y};
-        for (int k = 0; k < 4; k++) {
-            D[k][2 * t] = re[k];
-            D[k][2 * t + 1] = im[k];
+    const int64_t npos = (int64_t)nch * n1;
+    const int64_t base = (int64_t)blockIdx.x * GF_THREADS;
+    int64_t pos = base + threadIdx.x;
+    float* xr = xs + threadIdx.x * (GN_IN + 1);
+    if (pos < npos) {
+        int ch = (int)(pos / n1);
+        double D[4][4];
+        for (int t = 0; t < 2; t++) {
+            double2 a = p0[2 * pos + t], b = p1[2 * pos + t], c = p2[2 * pos + t], d = p3[2 * pos + t];
+            double re[4] = {a.x, a.x - b.x, a.x - 2.0 * b.x + c.x, a.x - 3.0 * b.x + 3.0 * c.x - d.x};
+            double im[4] = {a.y, a.y - b.y, a.y - 2.0 * b.y + c.y, a.y - 3.0 * b.y + 3.0 * c.y - d.y};
+            for (int k = 0; k < 4; k++) {
+                D[k][2 * t] = re[k];
+                D[k][2 * t + 1] = im[k];
+            }
         }
+        float ms[4];   // rms of the scaled differences
+        int ex[4];     // D[k] = Ds[k] 2^ex[k]
+        for (int k = 0; k < 4; k++) {
+            double amax = fmax(fmax(fabs(D[k][0]), fabs(D[k][1])), fmax(fabs(D[k][2]), fabs(D[k][3])));
+            int e = 0;
+            if (amax > 0) {
+                // exponent of amax from its bit pattern (finite, nonzero): amax in [2^e, 2^(e+1))
+                long long bits = __double_as_longlong(amax);
+                int be = (int)((bits >> 52) & 0x7ff);
+                e = be > 0 ? be - 1023 : -1022;   // subnormal differences: scale from 2^-1022
+            }
+            double sc = ldexp(1.0, -e);   // exact power of two
+            float q = 0.f, v[4];
+            for (int i = 0; i < 4; i++) {
+                v[i] = (float)(D[k][i] * sc);
+                q = fmaf(v[i], v[i], q);
+            }
+            ms[k] = sqrtf(0.25f * q);
+            ex[k] = e;
+            float inv = ms[k] > 0.f ? 1.f / ms[k] : 0.f;
+            for (int i = 0; i < 4; i++) xr[4 * k + i] = v[i] * inv;
+        }
+        for (int j = 0; j < 3; j++) {
+            float w = 0.f;
+            if (ms[j] > 0.f && ms[3] > 0.f) {
+                float lg = log10f(ms[j] / ms[3]) + (float)(ex[j] - ex[3]) * 0.30102999566398120f;
+                w = fminf(30.f, fmaxf(-30.f, lg)) / 10.f;
+            }
+            xr[16 + j] = w;
+        }
+        for (int i = 0; i < 6; i++) xr[19 + i] = F[i];
+        xr[25] = (float)kappa[ch] / 10.f;
+        xr[26] = (float)two_mu[ch] / 20.f;
+        for (int i = 27; i < GN_IN; i++) xr[i] = 0.f;
+        S[pos] = ldexpf(ms[3], ex[3]);
     }
-    double m[4];
-    for (int k = 0; k < 4; k++) {
-        double q = 0;
-        for (int i = 0; i < 4; i++) q += D[k][i] * D[k][i];
-        m[k] = sqrt(q / 4.0);
-    }
-    float x[GN_IN];
-    for (int k = 0; k < 4; k++) {
-        double inv = m[k] > 0 ? 1.0 / m[k] : 0.0;
-        for (int i = 0; i < 4; i++) x[4 * k + i] = (float)(D[k][i] * inv);
-    }
-    for (int j = 0; j < 3; j++) {
-        double v = 0;
-        if (m[j] > 0 && m[3] > 0) v = fmin(30.0, fmax(-30.0, log10(m[j] / m[3]))) / 10.0;
-        x[16 + j] = (float)v;
-    }
-    for (int i = 0; i < 6; i++) x[19 + i] = F[i];
-    x[25] = (float)kappa[ch] / 10.f;
-    x[26] = (float)two_mu[ch] / 20.f;
-    for (int i = 27; i < GN_IN; i++) x[i] = 0.f;
-    float4* xo = reinterpret_cast<float4*>(X + pos * GN_IN);
-    for (int i = 0; i < GN_IN / 4; i++) xo[i] = make_float4(x[4 * i], x[4 * i + 1], x[4 * i + 2], x[4 * i + 3]);
-    S[pos] = (float)m[3];
+    __syncthreads();
+    // block's rows of X, contiguous: element i of the block's run is row i / GN_IN, column i % GN_IN
+    const int64_t nrows = min((int64_t)GF_THREADS, npos - base);
+    float* Xb = X + base * GN_IN;
+    for (int i = threadIdx.x; i < nrows * GN_IN; i += GF_THREADS) Xb[i] = xs[(i / GN_IN) * (GN_IN + 1) + i % GN_IN];
 }
 
 // target = (psi_{n+1} - x_ext) / s (zero where s = 0)
@@ -397,6 +430,15 @@ __device__ __forceinline__ void ft_load_chunk_async(__nv_bfloat16* dst, const __
     cpa_commit();
 }
 
+// hardware tanh (one MUFU instruction): relative error about 2^-11, below the bfloat16 rounding the
+// activations get next; the FP32 kernels (training, reference forward) keep tanhf
+__device__ __forceinline__ float tanh_hw(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float* __restrict__ X,
                                                           const __nv_bfloat16* __restrict__ wb,
                                                           const float* __restrict__ wr, float* __restrict__ out,
@@ -457,9 +499,9 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
             int c = half * 128 + j * 8 + 2 * tq;
             float bb0 = b1[c], bb1 = b1[c + 1];
             *reinterpret_cast<uint32_t*>(actA + (rw + g) * FT_AST + c) =
-                pack_bf16(tanhf(acc[j][0] + bb0), tanhf(acc[j][1] + bb1));
+                pack_bf16(tanh_hw(acc[j][0] + bb0), tanh_hw(acc[j][1] + bb1));
             *reinterpret_cast<uint32_t*>(actA + (rw + g + 8) * FT_AST + c) =
-                pack_bf16(tanhf(acc[j][2] + bb0), tanhf(acc[j][3] + bb1));
+                pack_bf16(tanh_hw(acc[j][2] + bb0), tanh_hw(acc[j][3] + bb1));
         }
     }
     __syncthreads();
@@ -500,9 +542,9 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
                 int cidx = half * 128 + j * 8 + 2 * tq;
                 float bb0 = bias[cidx], bb1 = bias[cidx + 1];
                 *reinterpret_cast<uint32_t*>(outb + (rw + g) * FT_AST + cidx) =
-                    pack_bf16(tanhf(acc[j][0] + bb0), tanhf(acc[j][1] + bb1));
+                    pack_bf16(tanh_hw(acc[j][0] + bb0), tanh_hw(acc[j][1] + bb1));
                 *reinterpret_cast<uint32_t*>(outb + (rw + g + 8) * FT_AST + cidx) =
-                    pack_bf16(tanhf(acc[j][2] + bb0), tanhf(acc[j][3] + bb1));
+                    pack_bf16(tanh_hw(acc[j][2] + bb0), tanh_hw(acc[j][3] + bb1));
             }
         }
         __syncthreads();
@@ -677,7 +719,7 @@ extern "C" dirac_status dirac_guess_features(dirac_op* op, const void* const* st
     dirac_status fe = guess_buffers(op);
     if (fe) return fe;
     k_guess_field<<<1, 1, 0, op->st>>>(op->pv, t_next, -1, 0.0, op->gfield);
-    k_guess_features<<<(unsigned)((npos + 255) / 256), 256, 0, op->st>>>(
+    k_guess_features<<<(unsigned)((npos + GF_THREADS - 1) / GF_THREADS), GF_THREADS, 0, op->st>>>(
         op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, (const double2*)states[0], (const double2*)states[1],
         (const double2*)states[2], (const double2*)states[3], op->gfield, x_dev, s_dev, nullptr);
     op->launches += 2;
@@ -793,8 +835,8 @@ dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, cons
         field = op->gfield;
         op->launches++;
     }
-    k_guess_features<<<nb, 256, 0, st>>>(op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, p0, h1, h2, h3,
-                                         field, op->gx, op->gs, gate);
+    k_guess_features<<<(unsigned)((npos + GF_THREADS - 1) / GF_THREADS), GF_THREADS, 0, st>>>(
+        op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, p0, h1, h2, h3, field, op->gx, op->gs, gate);
     k_guess_forward_tc<<<(unsigned)((npos + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), st>>>(
         npos, op->gx, g->wb, g->wr, op->gout, gate);
     k_guess_apply<<<nb, 256, 0, st>>>(npos, p0, h1, h2, op->gs, op->gout, x, gate);
