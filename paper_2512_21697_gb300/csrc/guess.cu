@@ -377,6 +377,7 @@ __global__ void k_adam(int64_t n, float* __restrict__ w, float* __restrict__ m, 
 // 256 x 256 weights stream through shared memory in 32-row chunks, double buffered.
 // ------------------------------------------------------------------------------------------
 constexpr int FT_M = 128;                 // positions per block
+constexpr int FT_THREADS = 512;           // 16 warps: 4 x 4 tiles of 32 rows x 64 columns
 constexpr int FT_KC = 32;                 // weight rows per chunk
 constexpr int FT_AST = GN_H + 8;          // activation row stride (bf16), padded against bank conflicts
 constexpr int FT_WST = GN_H + 8;          // weight chunk row stride (bf16)
@@ -439,7 +440,7 @@ __device__ __forceinline__ float tanh_hw(float x)
     return y;
 }
 
-__global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float* __restrict__ X,
+__global__ void __launch_bounds__(FT_THREADS) k_guess_forward_tc(int64_t M, const float* __restrict__ X,
                                                           const __nv_bfloat16* __restrict__ wb,
                                                           const float* __restrict__ wr, float* __restrict__ out,
                                                           const int* gate)
@@ -471,38 +472,55 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
     }
     cpa_wait0();
     __syncthreads();
-    const int rw = warp * 16;   // the warp's rows
-    // A fragments of rows rw .. rw + 15, columns kk .. kk + 15
+    const int rw = warp * 16;   // the warp's rows in layer 4
+    // A fragments of rows rw .. rw + 15, columns kk .. kk + 15 (layer 4)
     auto load_a = [&](const __nv_bfloat16* act, int kk, uint32_t* a) {
         ldsm_x4(a, act + (rw + (mi & 1) * 8 + r8) * FT_AST + kk + (mi >> 1) * 8);
     };
-    // B fragments of two 8-column tiles n0 .. n0 + 15 for k = kk .. kk + 15 of a chunk [k][n]
-    auto load_b2 = [&](const __nv_bfloat16* w, int kk, int n0, uint32_t* b) {
-        ldsm_x4_trans(b, w + (kk + (mi & 1) * 8 + r8) * FT_WST + n0 + (mi >> 1) * 8);
-    };
-    // layer 1: actB[:, 0:32] x W1 -> tanh -> actA
-    for (int half = 0; half < 2; half++) {
-        float acc[16][4];
-        for (int j = 0; j < 16; j++)
-            for (int q = 0; q < 4; q++) acc[j][q] = 0.f;
-        for (int kk = 0; kk < GN_IN; kk += 16) {
-            uint32_t a[4];
-            load_a(actB, kk, a);
-            for (int j = 0; j < 16; j += 2) {
-                uint32_t b[4];
-                load_b2(wch, kk, half * 128 + j * 8, b);
-                mma_bf16(acc[j], a, b);
-                mma_bf16(acc[j + 1], a, b + 2);
+    // layers 1-3: the 16 warps tile the 128-row x 256-column output as 4 x 4 warps of 32 rows x
+    // 64 columns, so each B fragment feeds two row blocks and each A fragment four column pairs,
+    // and every weight chunk is streamed once per layer
+    const int wm = warp >> 2, wn = warp & 3;
+    const int rwm = wm * 32;
+    auto mma_step = [&](const __nv_bfloat16* act, int ka, const __nv_bfloat16* w, int kw, float (&acc)[2][8][4]) {
+        uint32_t a[2][4];
+#pragma unroll
+        for (int mb = 0; mb < 2; mb++)
+            ldsm_x4(a[mb], act + (rwm + mb * 16 + (mi & 1) * 8 + r8) * FT_AST + ka + (mi >> 1) * 8);
+#pragma unroll
+        for (int jp = 0; jp < 4; jp++) {
+            uint32_t bf[4];
+            ldsm_x4_trans(bf, w + (kw + (mi & 1) * 8 + r8) * FT_WST + wn * 64 + jp * 16 + (mi >> 1) * 8);
+#pragma unroll
+            for (int mb = 0; mb < 2; mb++) {
+                mma_bf16(acc[mb][2 * jp], a[mb], bf);
+                mma_bf16(acc[mb][2 * jp + 1], a[mb], bf + 2);
             }
         }
-        for (int j = 0; j < 16; j++) {
-            int c = half * 128 + j * 8 + 2 * tq;
-            float bb0 = b1[c], bb1 = b1[c + 1];
-            *reinterpret_cast<uint32_t*>(actA + (rw + g) * FT_AST + c) =
-                pack_bf16(tanh_hw(acc[j][0] + bb0), tanh_hw(acc[j][1] + bb1));
-            *reinterpret_cast<uint32_t*>(actA + (rw + g + 8) * FT_AST + c) =
-                pack_bf16(tanh_hw(acc[j][2] + bb0), tanh_hw(acc[j][3] + bb1));
-        }
+    };
+    // tanh(acc + bias) as bf16 into the output activations (the thread's rows and columns)
+    auto epilogue = [&](float (&acc)[2][8][4], const float* bias, __nv_bfloat16* outb) {
+#pragma unroll
+        for (int mb = 0; mb < 2; mb++)
+#pragma unroll
+            for (int j = 0; j < 8; j++) {
+                int c = wn * 64 + j * 8 + 2 * tq;
+                float bb0 = bias[c], bb1 = bias[c + 1];
+                int r = rwm + mb * 16 + g;
+                *reinterpret_cast<uint32_t*>(outb + r * FT_AST + c) =
+                    pack_bf16(tanh_hw(acc[mb][j][0] + bb0), tanh_hw(acc[mb][j][1] + bb1));
+                *reinterpret_cast<uint32_t*>(outb + (r + 8) * FT_AST + c) =
+                    pack_bf16(tanh_hw(acc[mb][j][2] + bb0), tanh_hw(acc[mb][j][3] + bb1));
+            }
+    };
+    // layer 1: actB[:, 0:32] x W1 -> tanh -> actA
+    {
+        float acc[2][8][4];
+        for (int mb = 0; mb < 2; mb++)
+            for (int j = 0; j < 8; j++)
+                for (int q = 0; q < 4; q++) acc[mb][j][q] = 0.f;
+        for (int kk = 0; kk < GN_IN; kk += 16) mma_step(actB, kk, wch, kk, acc);
+        epilogue(acc, b1, actA);
     }
     __syncthreads();
     // layers 2 and 3: in -> out, weights streamed in FT_KC-row chunks, one chunk ahead
@@ -512,10 +530,11 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
         const float* bias = layer == 0 ? b2 : b3;
         __nv_bfloat16* in = layer == 0 ? actA : actB;
         __nv_bfloat16* outb = layer == 0 ? actB : actA;
-        for (int half = 0; half < 2; half++) {
-            float acc[16][4];
-            for (int j = 0; j < 16; j++)
-                for (int q = 0; q < 4; q++) acc[j][q] = 0.f;
+        {
+            float acc[2][8][4];
+            for (int mb = 0; mb < 2; mb++)
+                for (int j = 0; j < 8; j++)
+                    for (int q = 0; q < 4; q++) acc[mb][j][q] = 0.f;
             ft_load_chunk_async(wch, W, 0);
             for (int c = 0; c < NCH; c++) {
                 if (c + 1 < NCH) {
@@ -526,31 +545,15 @@ __global__ void __launch_bounds__(256) k_guess_forward_tc(int64_t M, const float
                 }
                 __syncthreads();
                 const __nv_bfloat16* cur = wch + (c & 1) * FT_KC * FT_WST;
-                for (int kk = 0; kk < FT_KC; kk += 16) {
-                    uint32_t a[4];
-                    load_a(in, c * FT_KC + kk, a);
-                    for (int j = 0; j < 16; j += 2) {
-                        uint32_t b[4];
-                        load_b2(cur, kk, half * 128 + j * 8, b);
-                        mma_bf16(acc[j], a, b);
-                        mma_bf16(acc[j + 1], a, b + 2);
-                    }
-                }
+                for (int kk = 0; kk < FT_KC; kk += 16) mma_step(in, c * FT_KC + kk, cur, kk, acc);
                 __syncthreads();   // buffer (c & 1) is refilled two chunks later
             }
-            for (int j = 0; j < 16; j++) {
-                int cidx = half * 128 + j * 8 + 2 * tq;
-                float bb0 = bias[cidx], bb1 = bias[cidx + 1];
-                *reinterpret_cast<uint32_t*>(outb + (rw + g) * FT_AST + cidx) =
-                    pack_bf16(tanh_hw(acc[j][0] + bb0), tanh_hw(acc[j][1] + bb1));
-                *reinterpret_cast<uint32_t*>(outb + (rw + g + 8) * FT_AST + cidx) =
-                    pack_bf16(tanh_hw(acc[j][2] + bb0), tanh_hw(acc[j][3] + bb1));
-            }
+            epilogue(acc, bias, outb);
         }
         __syncthreads();
     }
-    // layer 4: actA x W4 (256 x 8, columns 4..7 zero) -> out (FP32)
-    {
+    // layer 4: actA x W4 (256 x 8, columns 4..7 zero) -> out (FP32), warps 0..7 (16 rows each)
+    if (warp < FT_M / 16) {
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
         for (int kk = 0; kk < GN_H; kk += 16) {
             uint32_t a[4], b[2];
@@ -748,7 +751,7 @@ extern "C" dirac_status dirac_guess_forward(dirac_guess* g, const float* x_dev, 
     cudaStream_t st = (cudaStream_t)stream;
     if (M == 0) return DIRAC_OK;
     if (tensor_cores) {
-        k_guess_forward_tc<<<(unsigned)((M + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), st>>>(
+        k_guess_forward_tc<<<(unsigned)((M + FT_M - 1) / FT_M), FT_THREADS, guess_forward_tc_smem(), st>>>(
             M, x_dev, g->wb, g->wr, out_dev, nullptr);
         return check_launch("dirac_guess_forward");
     }
@@ -837,7 +840,7 @@ dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, cons
     }
     k_guess_features<<<(unsigned)((npos + GF_THREADS - 1) / GF_THREADS), GF_THREADS, 0, st>>>(
         op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, p0, h1, h2, h3, field, op->gx, op->gs, gate);
-    k_guess_forward_tc<<<(unsigned)((npos + FT_M - 1) / FT_M), 256, guess_forward_tc_smem(), st>>>(
+    k_guess_forward_tc<<<(unsigned)((npos + FT_M - 1) / FT_M), FT_THREADS, guess_forward_tc_smem(), st>>>(
         npos, op->gx, g->wb, g->wr, op->gout, gate);
     k_guess_apply<<<nb, 256, 0, st>>>(npos, p0, h1, h2, op->gs, op->gout, x, gate);
     op->launches += 3;
