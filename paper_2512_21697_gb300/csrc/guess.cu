@@ -372,12 +372,16 @@ __global__ void k_adam(int64_t n, float* __restrict__ w, float* __restrict__ m, 
 }
 
 // ------------------------------------------------------------------------------------------
-// Tensor-core forward: 128 positions per block (8 warps x 16 rows), bf16 mma.sync m16n8k16 with
-// FP32 accumulators.  Activations stay in shared memory as bf16 (two 128 x 256 buffers); the
-// 256 x 256 weights stream through shared memory in 32-row chunks, double buffered.
+// Tensor-core forward: 64 positions per block (8 warps, each a 32-row x 64-column tile of every
+// layer), bf16 mma.sync m16n8k16 with FP32 accumulators.  Activations stay in shared memory as
+// bf16 (two 64 x 256 buffers); the 256 x 256 weights stream through shared memory in 32-row
+// chunks, double buffered, once per layer; two blocks fit on an SM.
 // ------------------------------------------------------------------------------------------
-constexpr int FT_M = 128;                 // positions per block
-constexpr int FT_THREADS = 512;           // 16 warps: 4 x 4 tiles of 32 rows x 64 columns
+constexpr int FT_M = 64;                  // positions per block (two blocks per SM)
+constexpr int FT_WM = 2, FT_WN = 4;       // warps along rows and along the 256 columns
+constexpr int FT_THREADS = 32 * FT_WM * FT_WN;
+constexpr int FT_MB = FT_M / FT_WM / 16;  // 16-row blocks per warp
+constexpr int FT_JP = GN_H / FT_WN / 16;  // 16-column pairs of 8-column tiles per warp
 constexpr int FT_KC = 32;                 // weight rows per chunk
 constexpr int FT_AST = GN_H + 8;          // activation row stride (bf16), padded against bank conflicts
 constexpr int FT_WST = GN_H + 8;          // weight chunk row stride (bf16)
@@ -477,34 +481,35 @@ __global__ void __launch_bounds__(FT_THREADS) k_guess_forward_tc(int64_t M, cons
     auto load_a = [&](const __nv_bfloat16* act, int kk, uint32_t* a) {
         ldsm_x4(a, act + (rw + (mi & 1) * 8 + r8) * FT_AST + kk + (mi >> 1) * 8);
     };
-    // layers 1-3: the 16 warps tile the 128-row x 256-column output as 4 x 4 warps of 32 rows x
-    // 64 columns, so each B fragment feeds two row blocks and each A fragment four column pairs,
-    // and every weight chunk is streamed once per layer
-    const int wm = warp >> 2, wn = warp & 3;
-    const int rwm = wm * 32;
-    auto mma_step = [&](const __nv_bfloat16* act, int ka, const __nv_bfloat16* w, int kw, float (&acc)[2][8][4]) {
-        uint32_t a[2][4];
+    // layers 1-3: FT_WM x FT_WN warps tile the FT_M-row x 256-column output (32 x 64 per warp), so
+    // each B fragment feeds FT_MB row blocks and each A fragment FT_JP column pairs, and every
+    // weight chunk is streamed once per layer
+    const int wm = warp / FT_WN, wn = warp % FT_WN;
+    const int rwm = wm * FT_MB * 16, cwn = wn * FT_JP * 16;
+    auto mma_step = [&](const __nv_bfloat16* act, int ka, const __nv_bfloat16* w, int kw,
+                        float (&acc)[FT_MB][2 * FT_JP][4]) {
+        uint32_t a[FT_MB][4];
 #pragma unroll
-        for (int mb = 0; mb < 2; mb++)
+        for (int mb = 0; mb < FT_MB; mb++)
             ldsm_x4(a[mb], act + (rwm + mb * 16 + (mi & 1) * 8 + r8) * FT_AST + ka + (mi >> 1) * 8);
 #pragma unroll
-        for (int jp = 0; jp < 4; jp++) {
+        for (int jp = 0; jp < FT_JP; jp++) {
             uint32_t bf[4];
-            ldsm_x4_trans(bf, w + (kw + (mi & 1) * 8 + r8) * FT_WST + wn * 64 + jp * 16 + (mi >> 1) * 8);
+            ldsm_x4_trans(bf, w + (kw + (mi & 1) * 8 + r8) * FT_WST + cwn + jp * 16 + (mi >> 1) * 8);
 #pragma unroll
-            for (int mb = 0; mb < 2; mb++) {
+            for (int mb = 0; mb < FT_MB; mb++) {
                 mma_bf16(acc[mb][2 * jp], a[mb], bf);
                 mma_bf16(acc[mb][2 * jp + 1], a[mb], bf + 2);
             }
         }
     };
     // tanh(acc + bias) as bf16 into the output activations (the thread's rows and columns)
-    auto epilogue = [&](float (&acc)[2][8][4], const float* bias, __nv_bfloat16* outb) {
+    auto epilogue = [&](float (&acc)[FT_MB][2 * FT_JP][4], const float* bias, __nv_bfloat16* outb) {
 #pragma unroll
-        for (int mb = 0; mb < 2; mb++)
+        for (int mb = 0; mb < FT_MB; mb++)
 #pragma unroll
-            for (int j = 0; j < 8; j++) {
-                int c = wn * 64 + j * 8 + 2 * tq;
+            for (int j = 0; j < 2 * FT_JP; j++) {
+                int c = cwn + j * 8 + 2 * tq;
                 float bb0 = bias[c], bb1 = bias[c + 1];
                 int r = rwm + mb * 16 + g;
                 *reinterpret_cast<uint32_t*>(outb + r * FT_AST + c) =
@@ -515,9 +520,9 @@ __global__ void __launch_bounds__(FT_THREADS) k_guess_forward_tc(int64_t M, cons
     };
     // layer 1: actB[:, 0:32] x W1 -> tanh -> actA
     {
-        float acc[2][8][4];
-        for (int mb = 0; mb < 2; mb++)
-            for (int j = 0; j < 8; j++)
+        float acc[FT_MB][2 * FT_JP][4];
+        for (int mb = 0; mb < FT_MB; mb++)
+            for (int j = 0; j < 2 * FT_JP; j++)
                 for (int q = 0; q < 4; q++) acc[mb][j][q] = 0.f;
         for (int kk = 0; kk < GN_IN; kk += 16) mma_step(actB, kk, wch, kk, acc);
         epilogue(acc, b1, actA);
@@ -531,9 +536,9 @@ __global__ void __launch_bounds__(FT_THREADS) k_guess_forward_tc(int64_t M, cons
         __nv_bfloat16* in = layer == 0 ? actA : actB;
         __nv_bfloat16* outb = layer == 0 ? actB : actA;
         {
-            float acc[2][8][4];
-            for (int mb = 0; mb < 2; mb++)
-                for (int j = 0; j < 8; j++)
+            float acc[FT_MB][2 * FT_JP][4];
+            for (int mb = 0; mb < FT_MB; mb++)
+                for (int j = 0; j < 2 * FT_JP; j++)
                     for (int q = 0; q < 4; q++) acc[mb][j][q] = 0.f;
             ft_load_chunk_async(wch, W, 0);
             for (int c = 0; c < NCH; c++) {
