@@ -965,7 +965,9 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     pv.L = P.L; pv.T = P.T; pv.amp = P.amp; pv.t0 = pulse->t0; pv.dt = opts->dt;
     for (int c = 0; c < 3; c++) { pv.w[c] = P.w[c]; pv.wt[c] = P.wt[c]; }
     pv.M = dM;
-    op->prec_sm_ok = precond_sm_prepare<float>(n1) == cudaSuccess && precond_sm_prepare<double>(n1) == cudaSuccess;
+    // the staged and rotated-lane kernels are built for 13 block-diagonals (order-7 splines)
+    op->prec_sm_ok = bd == 13 && precond_sm_prepare<float>(n1) == cudaSuccess &&
+                     precond_sm_prepare<double>(n1) == cudaSuccess;
     cudaGetLastError();
     op->prec_rot_ok = bd == 13 && precond_rot_prepare<float>() == cudaSuccess &&
                       precond_rot_prepare<double>() == cudaSuccess;

@@ -59,8 +59,13 @@ TAIL = _base(R=300.0, N=120, grid=1, r_lin=60.0, n_lin=58, kappa_max=4, two_mu_m
 # the assembly takes its per-pair form.
 WIDE_L = dict(SMALL, l_max=8, E0=0.5, omega=omega_from_nm(100))
 
+# Order-5 B-splines on the small system: a band of 9 block-diagonals instead of 13, so every
+# kernel takes its general-bandwidth form (plain warp-per-channel preconditioner, per-row applies
+# and residual instead of the owner passes).
+ORDER5 = dict(SMALL, order=5, N=40)
+
 WORKLOADS = {"small": SMALL, "production": PRODUCTION, "tiny": TINY, "slice": SLICE, "medium": MEDIUM,
-             "tail": TAIL, "wide_l": WIDE_L}
+             "tail": TAIL, "wide_l": WIDE_L, "order5": ORDER5}
 
 
 def oracle_params(cfg):
