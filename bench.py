@@ -348,16 +348,19 @@ def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, pe
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         op.profile(True)
+        clocks = ClockSampler(local)
+        clocks.start()
         ev0.record(stream)
         its, rr, _ = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
         ev1.record(stream)
         torch.cuda.synchronize()
+        ck = clocks.stop()
         phase_ms, phase_n, _ = op.profile_read()
         op.profile(False)
         ms = ev0.elapsed_time(ev1)
         res[guess] = {"value": args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
                       "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(rr)),
-                      "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()}}
+                      "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()}, "clocks": ck}
         del op
     line = {"metric": METRIC, "value": res[2]["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res[2]["ms_per_step"], "higher_is_better": True,
@@ -368,7 +371,8 @@ def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, pe
                                    "probability proportional to s^2, %d Adam steps of "
                                    "8192; data %.1f s, training %.1f s; loss %.3g -> %.3g" %
                                    (n_train, train_steps, n_samples, iters, t_data, t_train, losses[0], losses[-1])},
-            "learned": res[2], "extrapolated": res[1], "speedup_vs_extrapolated": res[2]["value"] / res[1]["value"]}
+            "learned": res[2], "extrapolated": res[1], "speedup_vs_extrapolated": res[2]["value"] / res[1]["value"],
+            "clocks": res[2]["clocks"]}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
