@@ -285,6 +285,13 @@ dirac_status dirac_op_set_overlap(dirac_op* op, int enable);
 dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched);
 int dirac_op_get_schedule(const dirac_op* op, int complex64);   /* -1 for a NULL op */
 
+/* Self-test of the bounded waits of the owner passes (their bulk-copy rings): one block waits
+ * limit_cycles SM clocks (at most 4e9, about two seconds) on an mbarrier phase that nothing
+ * completes, records the time-out in the op's error word exactly as those passes do, and
+ * *timed_out receives it (1 expected; the word is cleared again).  The context stays usable.
+ * Synchronises the op's stream.  DIRAC_E_ARG on bad arguments. */
+dirac_status dirac_selftest_wait(dirac_op* op, double limit_cycles, int* timed_out);
+
 const char* dirac_last_error(void);
 
 #ifdef __cplusplus

@@ -81,6 +81,7 @@ SIGNATURES = {
     "dirac_op_set_guess": (C.c_int, [_VP, _VP]),
     "dirac_op_set_overlap": (C.c_int, [_VP, C.c_int]),
     "dirac_op_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "dirac_selftest_wait": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int)]),
     "dirac_op_get_schedule": (C.c_int, [_VP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
 }
@@ -230,6 +231,12 @@ class Operator:
     @property
     def precision(self):
         return self.opts.precision
+
+    def selftest_wait(self, limit_cycles):
+        """dirac_selftest_wait: 1 if a wait on a never-completed mbarrier ran out of time."""
+        t = C.c_int(0)
+        _check(lib().dirac_selftest_wait(self._h, float(limit_cycles), C.byref(t)), "dirac_selftest_wait")
+        return t.value
 
     def set_schedule(self, complex64, sched):
         """dirac_op_set_schedule: 0 lane / 1 warp / 2 staged-warp / 3 rotated-lane-warp preconditioner

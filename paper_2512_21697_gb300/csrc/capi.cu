@@ -380,6 +380,22 @@ void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start)
     vzero(op, K, K.v);
 }
 
+extern "C" dirac_status dirac_selftest_wait(dirac_op* op, double limit_cycles, int* timed_out)
+{
+    if (!op || !timed_out || !(limit_cycles >= 0) || limit_cycles > 4e9) {
+        set_error("dirac_selftest_wait: bad argument");
+        return DIRAC_E_ARG;
+    }
+    CUDA_TRY(cudaMemsetAsync(op->dev_err, 0, sizeof(int), op->st));
+    CUDA_TRY(launch_wait_selftest(op->st, (long long)limit_cycles, op->dev_err));
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, op->dev_err, sizeof(int), cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    CUDA_TRY(cudaMemsetAsync(op->dev_err, 0, sizeof(int), op->st));
+    *timed_out = h;
+    return DIRAC_OK;
+}
+
 // the error word of kernels with bounded waits (synchronises the stream); cleared after reading
 dirac_status check_dev_err(dirac_op* op, const char* what)
 {

@@ -132,6 +132,9 @@ template <class T>
 void launch_precond_rot_t(cudaStream_t st, const OpView& A, const void* U, const void* L, const void* Dinv, int mode,
                           const KState* ks, const void* r, const void* v, void* io, void* z, double* pn);
 
+// bounded-wait self-test: one block waits `limit` cycles on an mbarrier nothing completes
+cudaError_t launch_wait_selftest(cudaStream_t st, long long limit, int* err);
+
 // complex64 apply with each coupling block read once (owner pass + gather pass, bd = 13)
 size_t apply_own32_smem();
 int apply_own_tile();

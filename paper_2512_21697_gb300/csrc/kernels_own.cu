@@ -94,15 +94,37 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
 }
 
 // wait for a ring stage; false after the time limit (the caller records the failure)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = WAIT_CYCLES)
 {
     long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
 }  // namespace
+
+// Self-test of the bounded wait: one block waits on an mbarrier phase that nothing completes, with
+// the given cycle limit, then records the time-out in *err exactly as the owner passes do (no copy
+// is in flight, so the block can leave at once).
+__global__ void k_wait_selftest(long long limit, int* err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    bool ok = mbar_wait(&bar, 0, limit);   // phase 0 never completes: no thread arrives
+    __syncthreads();
+    if (threadIdx.x == 0 && !ok) atomicExch(err, 1);
+}
+
+cudaError_t launch_wait_selftest(cudaStream_t st, long long limit, int* err)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(limit, err);
+    return cudaGetLastError();
+}
 
 __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const float* __restrict__ S,
                                                              const float* __restrict__ H, int sign,
