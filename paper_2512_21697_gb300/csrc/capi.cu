@@ -1135,15 +1135,15 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
         } else {
             rhs_accurate(op, psi);
         }
-        // initial guess
+        // initial guess (timed as its own phase when learned, else with the vector kernels)
         {
-            PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
             double2* x = (double2*)K.x;
             if (learned && nh >= 3) {
                 PhaseScope pg(op, DIRAC_PHASE_GUESS, 0);   // guess_into counts its launches
                 dirac_status ge = guess_into(op, psi, h1, h2, h3, t_start, step, x, nullptr, op->st, nullptr);
                 if (ge) return ge;
             } else {
+                PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);
                 k_extrapolate<<<npv, 256, 0, op->st>>>(n, o.guess >= 1 ? std::min(nh, 2) : 0, psi, h1, h2, x);
             }
         }
