@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--batch-n", type=int, default=64, help="instances of --workload batch")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned initial guess on production trajectories, then time guess=2 vs guess=1")
+    ap.add_argument("--factorised", action="store_true",
+                    help="factorised complex64 apply in the inner solve (coupling never stored)")
     ap.add_argument("--overlap", action="store_true",
                     help="precision 2: assemble the next step during the current solve (same arithmetic)")
     return ap.parse_args()
@@ -547,6 +549,8 @@ def main():
                     tol_inner=1e-5, max_outer=20)
     if args.precision == 2 and args.overlap:
         op.set_overlap(True)   # next step's assembly overlaps the current solve (same arithmetic)
+    if args.precision == 2 and args.factorised:
+        op.set_factorised(True)
     dev = torch.device("cuda", local)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)

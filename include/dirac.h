@@ -285,6 +285,14 @@ dirac_status dirac_op_set_overlap(dirac_op* op, int enable);
 dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched);
 int dirac_op_get_schedule(const dirac_op* op, int complex64);   /* -1 for a NULL op */
 
+/* Factorised complex64 apply for the inner solve (precision 2, order-7 splines): the coupling is
+ * applied from the time-dependent radial bands and the angular coefficients (four band products
+ * per channel and multipole, combined per pair) instead of the stored coupling values.  Same
+ * operator (Eq. fullH); FP32 rounding differs, within the inner tolerance.  Allocates the
+ * products of one radial tile (channels x multipoles x 4 x 64 x 2 complex64) on first use.
+ * DIRAC_E_ARG for other precisions or spline orders. */
+dirac_status dirac_op_set_factorised(dirac_op* op, int enable);
+
 /* Self-test of the bounded waits of the owner passes (their bulk-copy rings): one block waits
  * limit_cycles SM clocks (at most 4e9, about two seconds) on an mbarrier phase that nothing
  * completes, records the time-out in the op's error word exactly as those passes do, and

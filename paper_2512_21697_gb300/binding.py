@@ -82,6 +82,7 @@ SIGNATURES = {
     "dirac_op_set_overlap": (C.c_int, [_VP, C.c_int]),
     "dirac_op_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
     "dirac_selftest_wait": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int)]),
+    "dirac_op_set_factorised": (C.c_int, [_VP, C.c_int]),
     "dirac_op_get_schedule": (C.c_int, [_VP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
 }
@@ -231,6 +232,10 @@ class Operator:
     @property
     def precision(self):
         return self.opts.precision
+
+    def set_factorised(self, enable=True):
+        """dirac_op_set_factorised: factorised complex64 apply in the inner solve."""
+        _check(lib().dirac_op_set_factorised(self._h, int(bool(enable))), "dirac_op_set_factorised")
 
     def selftest_wait(self, limit_cycles):
         """dirac_selftest_wait: 1 if a wait on a never-completed mbarrier ran out of time."""

@@ -127,6 +127,7 @@ void collect_phases(dirac_op* op)
 // ---- launch helpers ------------------------------------------------------------------------
 int apply_parts(const dirac_op* op, const Krylov& K)
 {
+    if (K.prec == 1 && op->fact32) return grid_for(op->ov.n1, FTR) * op->ov.nch;
     return (K.prec == 1 && op->part_own) ? op->nparts_own : op->nparts_apply;
 }
 
@@ -138,6 +139,9 @@ void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void
     if (K.prec == 0)
         launch_apply_t<double>(grid, op->st, op->ov, (const double*)K.S, (const double*)K.H, sign, x,
                                (const double*)K.W, y, bsub, dv, pdot, pnrm, skip);
+    else if (op->fact32)
+        launch_fact32(op->st, op->ov, op->rad_chunks, op->nrad, op->Gdf, op->pv.L, (const float*)K.S,
+                      (const float*)K.H, sign, x, op->Zf, op->cab_df, y, bsub, dv, pdot, pnrm, skip);
     else if (op->part_own)
         launch_apply_own32(op->st, op->ov, (const float*)K.S, (const float*)K.H, sign, x, (const float*)K.W, y,
                            op->part_own, bsub, dv, pdot, pnrm, skip, op->dev_err);
@@ -946,6 +950,7 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     op->nparts_prec = grid_for(B.nch, 4);                     // ||s||^2 partials, warp-per-channel kernel
     op->nparts_prec32 = op->prec_warps ? op->prec_warps : grid_for(B.nch, 4);   // lane-per-channel kernel
     int np = std::max({op->nparts_apply, op->nparts_own, op->nparts_vec, op->nparts_prec, op->nparts_prec32,
+                       grid_for(n1, FTR) * B.nch,
                        precond_sm_blocks<double>(B.nch), precond_sm_blocks<float>(B.nch),
                        precond_rot_blocks<double>(B.nch), precond_rot_blocks<float>(B.nch)});
     TRY(dev_alloc(op, &op->part_d, (size_t)np));
@@ -1037,6 +1042,36 @@ extern "C" dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int s
     }
     (complex64 ? op->prec_sched32 : op->prec_sched64) = sched;
     op->config_gen++;   // captured graphs hold the old kernel
+    return DIRAC_OK;
+}
+
+extern "C" dirac_status dirac_op_set_factorised(dirac_op* op, int enable)
+{
+    if (!op || (enable && (op->opts.precision != 2 || op->ov.bd != 13 || !op->cab_df))) {
+        set_error("dirac_op_set_factorised: needs precision 2 and order-7 splines");
+        return DIRAC_E_ARG;
+    }
+    if (enable && !op->Zf) {
+        // kappa groups of the kappa-sorted channel order, in chunks of at most FCOL channels
+        std::vector<int> ks(op->ov.nch), ordv(op->ov.nch), kap(op->ov.nch);
+        CUDA_TRY(cudaMemcpy(ordv.data(), op->ov.prec_order, sizeof(int) * ordv.size(), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(ks.data(), op->ov.ch_kslot, sizeof(int) * ks.size(), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(kap.data(), op->ov.ch_kappa, sizeof(int) * kap.size(), cudaMemcpyDeviceToHost));
+        std::vector<RadChunk> rc;
+        for (int i = 0; i < op->ov.nch;) {
+            int j = i;
+            while (j < op->ov.nch && ks[ordv[j]] == ks[ordv[i]] && j - i < FCOL) j++;
+            rc.push_back(RadChunk{ks[ordv[i]], kap[ordv[i]], i, j - i});
+            i = j;
+        }
+        dirac_status e = upload(op, &op->rad_chunks, rc);
+        if (e) return e;
+        op->nrad = (int)rc.size();
+        e = dev_alloc(op, &op->Zf, (size_t)op->ov.nch * op->pv.L * 4 * FTR * 2);
+        if (e) return e;
+    }
+    op->fact32 = enable != 0;
+    op->config_gen++;   // captured graphs hold the other apply
     return DIRAC_OK;
 }
 

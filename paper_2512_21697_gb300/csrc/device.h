@@ -62,6 +62,14 @@ struct AsmChunk {
     int l[ASM_MAX_NL];
 };
 
+// Factorised complex64 apply: radial tiles of FTR rows; the band products of up to FCOL channels
+// of one kappa (consecutive in the kappa-sorted channel order, from index first) per block.
+constexpr int FTR = 64;
+constexpr int FCOL = 8;
+struct RadChunk {
+    int ks, kappa, first, count;
+};
+
 struct PulseView {
     int L;
     double T, amp, t0, dt;

@@ -135,6 +135,12 @@ void launch_precond_rot_t(cudaStream_t st, const OpView& A, const void* U, const
 // bounded-wait self-test: one block waits `limit` cycles on an mbarrier nothing completes
 cudaError_t launch_wait_selftest(cudaStream_t st, long long limit, int* err);
 
+// factorised complex64 apply (coupling values never stored): radial + angular pass per tile
+int fact_tile();
+void launch_fact32(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc, const float2* G, int L,
+                   const float* S, const float* H, int sign, const void* x, float2* Z, const float4* cab, void* y,
+                   const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip);
+
 // complex64 apply with each coupling block read once (owner pass + gather pass, bd = 13)
 size_t apply_own32_smem();
 int apply_own_tile();

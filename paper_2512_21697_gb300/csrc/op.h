@@ -70,6 +70,11 @@ struct dirac_op {
     float2 *Gdf = nullptr, *Kdf = nullptr, *KTdf = nullptr, *Sdf = nullptr, *Htdf = nullptr;
     float *Wh = nullptr, *Wl = nullptr;   // coupling hi words (also the FP32 values) and lo words
     float4* cab_df = nullptr;
+    // factorised complex64 apply of the inner solve (dirac_op_set_factorised)
+    bool fact32 = false;
+    dg::RadChunk* rad_chunks = nullptr;
+    int nrad = 0;
+    float2* Zf = nullptr;        // band products of one radial tile
     // grouped double-float assembly (null when a group has more than ASM_MAX_NL multipoles)
     dg::AsmChunk* asm_chunks = nullptr;
     int asm_nchunks = 0;
