@@ -132,6 +132,7 @@ FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x
 # units processed (pairs x slots: x 9.817); the summaries under profiles/ give the commands and the
 # raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
 TRAFFIC_MEDIUM = {"df": (1.762372e9 + 0.155071e9, "profiles/k_residual_own_df_medium.md"),
+                  "df_owner": (1.762372e9 + 0.155071e9, "profiles/k_residual_own_df_medium.md"),
                   "f32": (0.886455e9 + 0.075098e9, "profiles/k_apply_own32_medium.md")}
 MEDIUM_UNITS = 6944 * 601
 DF_OPS_PER_FMA = 12                 # FP32 operations of one double-float multiply-add (TwoProd + TwoSum)
@@ -141,8 +142,8 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
     """Roofline of one operator-apply launch group, timed live by the library's event timers.
 
     kind 'f64': FP64 apply (FP64 ALU bound), 'f32': complex64 owner/gather apply (HBM bound),
-    'df': double-float refinement residual (FP32 ALU/issue bound)."""
-    coup, flops, bytes_ = operator_counts(bas, cfg, kind)
+    'df': double-float refinement residual pass (FP32 ALU/issue bound), 'df_owner': its owner pass."""
+    coup, flops, bytes_ = operator_counts(bas, cfg, "df" if kind == "df_owner" else kind)
     t = ms / cnt / 1000.0
     gbs = bytes_ / t / 1e9
     traffic, tnote = None, None
@@ -163,6 +164,17 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
         out.update({"kernel": "k_apply_own32 + k_apply_gather32 (complex64 inner-solve apply)",
                     "flops_per_apply": flops, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak})
+    elif kind == "df_owner":
+        # the owner pass alone: each stored value twice (W u_b, W^T u_a) on re and im
+        dfma = 4 * coup
+        ops = dfma * DF_OPS_PER_FMA
+        tops = ops / t / 1e12
+        peak = FP32_LANE_OPS / 1e3
+        out.update({"kernel": "k_residual_own_df (double-float refinement residual, owner pass)",
+                    "df_fma_per_apply": dfma, "ops_per_apply": ops, "bound": "alu", "achieved": tops, "peak": peak,
+                    "unit": "T FP32-lane-ops/s", "frac": tops / peak,
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (1 op per lane per clock); "
+                                   "12 ops per double-float multiply-add"})
     else:
         # double-float multiply-adds: each stored value twice (W u_b, W^T u_a) on re and im, the
         # diagonal blocks S and tau H0 on both u and v (4 per entry and channel)
@@ -180,7 +192,9 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
 
 
 def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
-    """The dominant apply launch group's roofline, plus the complex64 SpMV's when it ran."""
+    """The dominant kernel's roofline, plus the complex64 SpMV's when it ran.  In precision 2 the
+    dominant kernel is the residual's owner pass, timed on its own (its phase lies inside 'apply');
+    the whole residual pass (split, owner, gather) is reported beside it."""
     cands = []
     if phase_n.get("apply", 0):
         cands.append(("apply", "df" if precision == 2 else "f64", phase_ms["apply"], phase_n["apply"]))
@@ -188,6 +202,11 @@ def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
         cands.append(("apply32", "f32", phase_ms["apply32"], phase_n["apply32"]))
     outs = {c[0]: roofline_of(bas, cfg, c[0], c[1], c[2], c[3], hbm_peak) for c in cands}
     dom = max(cands, key=lambda c: c[2])[0]
+    if dom == "apply" and precision == 2 and phase_n.get("owner", 0):
+        whole = outs["apply"]
+        own = roofline_of(bas, cfg, "owner", "df_owner", phase_ms["owner"], phase_n["owner"], hbm_peak)
+        own["residual_pass"] = {k: whole[k] for k in ("kernel", "apply_ms", "achieved", "frac")}
+        return own, outs.get("apply32")
     return outs[dom], outs.get("apply32")
 
 

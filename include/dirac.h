@@ -191,14 +191,17 @@ dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, vo
  * Phases: DIRAC_PHASE_ASSEMBLE (pulse factors + coupling values), DIRAC_PHASE_APPLY (double
  * precision operator products), DIRAC_PHASE_PRECOND, DIRAC_PHASE_VECTOR (updates, reductions,
  * copies), DIRAC_PHASE_APPLY32 (complex64 operator products of the mixed-precision inner solve),
- * DIRAC_PHASE_GUESS (the learned initial guess: features, network, correction). */
+ * DIRAC_PHASE_GUESS (the learned initial guess: features, network, correction), DIRAC_PHASE_OWNER
+ * (the owner pass of the double-float refinement residual alone; also counted in
+ * DIRAC_PHASE_APPLY, which covers the whole pass). */
 #define DIRAC_PHASE_ASSEMBLE 0
 #define DIRAC_PHASE_APPLY 1
 #define DIRAC_PHASE_PRECOND 2
 #define DIRAC_PHASE_VECTOR 3
 #define DIRAC_PHASE_APPLY32 4
 #define DIRAC_PHASE_GUESS 5
-#define DIRAC_NPHASE 6
+#define DIRAC_PHASE_OWNER 6
+#define DIRAC_NPHASE 7
 dirac_status dirac_profile(dirac_op* op, int enable);
 dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches);
 

@@ -267,7 +267,7 @@ class Operator:
     def profile(self, enable=True):
         _check(lib().dirac_profile(self._h, 1 if enable else 0), "dirac_profile")
 
-    PHASES = ("assemble", "apply", "precond", "vector", "apply32", "guess")
+    PHASES = ("assemble", "apply", "precond", "vector", "apply32", "guess", "owner")
 
     def profile_read(self):
         """({phase: ms}, {phase: timed launch groups}, kernel launches) since the last reset."""

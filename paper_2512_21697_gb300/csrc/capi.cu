@@ -239,9 +239,14 @@ void residual_accurate(dirac_op* op, const void* psi)
             PhaseScope ps(op, DIRAC_PHASE_APPLY, 3);
             k_split_uv3<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)psi, (const double2*)K.x,
                                                            op->xsplit, op->vsplit, op->psi32);
-            launch_residual_own_df(op->st, op->ov, op->Sdf, op->Htdf, op->xsplit, op->vsplit, op->psi32, op->Wh,
-                                   op->Wl, (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b,
-                                   op->part_n, op->part_n2, op->dev_err);
+            {
+                PhaseScope po(op, DIRAC_PHASE_OWNER, 0);   // the owner pass alone, inside the apply phase
+                launch_residual_owner_df(op->st, op->ov, op->xsplit, op->psi32, op->Wh, op->Wl, (double2*)K.r,
+                                         op->b32, op->part_rdf, op->part_bdf, op->need_b, op->dev_err);
+            }
+            launch_residual_gather_df(op->st, op->ov, op->Sdf, op->Htdf, op->xsplit, op->vsplit, op->psi32,
+                                      (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b, op->part_n,
+                                      op->part_n2);
         }
         {
             PhaseScope ps(op, DIRAC_PHASE_VECTOR, 1);

@@ -148,10 +148,13 @@ int apply_own_nout();
 bool apply_own_supported(const OpView& A);
 cudaError_t apply_own32_prepare();
 size_t residual_own_df_smem();
-void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
-                            const float4* v, const float2* psi32, const float* Wh, const float* Wl, double2* r,
-                            float2* b, float4* part_r, float4* part_b, const int* need_b, double* pn_r,
-                            double* pn_b, int* err);
+void launch_residual_owner_df(cudaStream_t st, const OpView& A, const float4* u, const float2* psi32, const float* Wh,
+                              const float* Wl, double2* r, float2* b, float4* part_r, float4* part_b,
+                              const int* need_b, int* err);
+void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
+                               const float4* v, const float2* psi32, double2* r, const float2* b,
+                               const float4* part_r, const float4* part_b, const int* need_b, double* pn_r,
+                               double* pn_b);
 void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const float* H, int sign, const void* x,
                         const float* W, void* y, float4* part, const void* bsub, const void* dv, double2* pdot,
                         double* pnrm, const KState* skip, int* err);

@@ -664,14 +664,21 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
 
 size_t residual_own_df_smem() { return (size_t)NSTD * STAGE_DF * sizeof(float); }
 
-void launch_residual_own_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
-                            const float4* v, const float2* psi32, const float* Wh, const float* Wl, double2* r,
-                            float2* b, float4* part_r, float4* part_b, const int* need_b, double* pn_r,
-                            double* pn_b, int* err)
+void launch_residual_owner_df(cudaStream_t st, const OpView& A, const float4* u, const float2* psi32, const float* Wh,
+                              const float* Wl, double2* r, float2* b, float4* part_r, float4* part_b,
+                              const int* need_b, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
     k_residual_own_df<<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b,
                                                                     need_b, err);
+}
+
+void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
+                               const float4* v, const float2* psi32, double2* r, const float2* b,
+                               const float4* part_r, const float4* part_b, const int* need_b, double* pn_r,
+                               double* pn_b)
+{
+    dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
     k_residual_gather_df<<<grid, NT, 0, st>>>(A, S, Ht, u, v, psi32, r, b, part_r, part_b, need_b, pn_r, pn_b);
 }
 
