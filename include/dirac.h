@@ -303,6 +303,16 @@ dirac_status dirac_op_set_factorised(dirac_op* op, int enable);
  * Synchronises the op's stream.  DIRAC_E_ARG on bad arguments. */
 dirac_status dirac_selftest_wait(dirac_op* op, double limit_cycles, int* timed_out);
 
+/* Index-check word of a debug build (the library compiled with -DDG_BOUNDS): the owner and gather
+ * passes and the grouped assembly test every computed global index of the coupling values, the
+ * vectors and the partial products against the buffers' sizes before using it, skip the access
+ * (or copy from the buffer's start) when it fails and set bit k of the word for check site k
+ * (0 coupling rows of a copy, 1 vector window of a copy, 2 partial store, 3 partial read, 4
+ * assembled coupling store).  *word receives the bits seen since the last call (then cleared);
+ * *checked is 1 in a debug build, 0 in a release build (where the word stays 0).  Synchronises
+ * the op's stream.  DIRAC_E_ARG on NULL arguments. */
+dirac_status dirac_bounds_word(dirac_op* op, unsigned int* word, int* checked);
+
 const char* dirac_last_error(void);
 
 #ifdef __cplusplus

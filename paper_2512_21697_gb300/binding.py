@@ -10,7 +10,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libdirac_gb300.so")
+# DIRAC_BOUNDS_CHECK=1 selects the debug build (index checks compiled in, build(debug=True))
+LIB_PATH = os.path.join(HERE, "libdirac_gb300_dbg.so" if os.environ.get("DIRAC_BOUNDS_CHECK") == "1"
+                        else "libdirac_gb300.so")
 
 DIRAC_OK, DIRAC_E_ARG, DIRAC_E_NOMEM, DIRAC_E_CUDA, DIRAC_E_NOCONV, DIRAC_E_BREAKDOWN, DIRAC_E_NUMERIC, \
     DIRAC_E_STATE = range(8)
@@ -82,6 +84,7 @@ SIGNATURES = {
     "dirac_op_set_overlap": (C.c_int, [_VP, C.c_int]),
     "dirac_op_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
     "dirac_selftest_wait": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int)]),
+    "dirac_bounds_word": (C.c_int, [_VP, C.POINTER(C.c_uint), C.POINTER(C.c_int)]),
     "dirac_op_set_factorised": (C.c_int, [_VP, C.c_int]),
     "dirac_op_get_schedule": (C.c_int, [_VP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
@@ -93,7 +96,7 @@ def lib():
     global _lib
     if _lib is None:
         if not os.path.exists(LIB_PATH):
-            raise ImportError("libdirac_gb300.so is not built (run __graft_entry__.build()); "
+            raise ImportError("%s is not built (run __graft_entry__.build()); " % os.path.basename(LIB_PATH) +
                               "there is no CPU fallback")
         L = C.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
@@ -236,6 +239,13 @@ class Operator:
     def set_factorised(self, enable=True):
         """dirac_op_set_factorised: factorised complex64 apply in the inner solve."""
         _check(lib().dirac_op_set_factorised(self._h, int(bool(enable))), "dirac_op_set_factorised")
+
+    def bounds_word(self):
+        """dirac_bounds_word: (bits of failed index checks since the last call, 1 if the library
+        checks indexes -- a debug build -- else 0)."""
+        w, c = C.c_uint(0), C.c_int(0)
+        _check(lib().dirac_bounds_word(self._h, C.byref(w), C.byref(c)), "dirac_bounds_word")
+        return int(w.value), int(c.value)
 
     def selftest_wait(self, limit_cycles):
         """dirac_selftest_wait: 1 if a wait on a never-completed mbarrier ran out of time."""

@@ -405,6 +405,25 @@ extern "C" dirac_status dirac_selftest_wait(dirac_op* op, double limit_cycles, i
     return DIRAC_OK;
 }
 
+extern "C" dirac_status dirac_bounds_word(dirac_op* op, unsigned int* word, int* checked)
+{
+    if (!op || !word || !checked) {
+        set_error("dirac_bounds_word: bad argument");
+        return DIRAC_E_ARG;
+    }
+#ifdef DG_BOUNDS
+    *checked = 1;
+#else
+    *checked = 0;
+#endif
+    unsigned int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, op->bounds_err, sizeof(h), cudaMemcpyDeviceToHost, op->st));
+    CUDA_TRY(cudaStreamSynchronize(op->st));
+    CUDA_TRY(cudaMemsetAsync(op->bounds_err, 0, sizeof(h), op->st));
+    *word = h;
+    return DIRAC_OK;
+}
+
 // the error word of kernels with bounded waits (synchronises the stream); cleared after reading
 dirac_status check_dev_err(dirac_op* op, const char* what)
 {
@@ -963,7 +982,9 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     TRY(dev_alloc(op, &op->part_n, (size_t)np));
     TRY(dev_alloc(op, &op->part_n2, (size_t)np));
     TRY(dev_alloc(op, &op->dev_err, 1));
-    if (cudaMemsetAsync(op->dev_err, 0, sizeof(int), op->st) != cudaSuccess) {
+    TRY(dev_alloc(op, &op->bounds_err, 1));
+    if (cudaMemsetAsync(op->dev_err, 0, sizeof(int), op->st) != cudaSuccess ||
+        cudaMemsetAsync(op->bounds_err, 0, sizeof(unsigned int), op->st) != cudaSuccess) {
         set_error("dirac_operator_setup: cudaMemsetAsync failed");
         dirac_op_free(op);
         return DIRAC_E_CUDA;
@@ -986,6 +1007,9 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
     o.pair_a = dpa; o.pair_b = dpb; o.term_start = dts; o.term_l = dtl; o.term_coef = dtc;
     o.nkeys = (int)keyl.size(); o.key_l = dkl; o.key_mono = dkm; o.term_kd = dkd; o.term_kt = dkt;
     o.term_cab = dcab; o.pair_order = dpo;
+    o.bounds_err = op->bounds_err;
+    o.nb_part = op->part_own ? (int64_t)op->npairs * grid_for(n1, apply_own_tile()) * apply_own_nout() : 0;
+    o.nb_coup = (int64_t)op->npairs * n1 * bd * 4;
     o.kb = kb; o.luU = dU; o.luL = dL; o.luP = dP; o.prec_order = dord;
     PulseView& pv = op->pv;
     pv.L = P.L; pv.T = P.T; pv.amp = P.amp; pv.t0 = pulse->t0; pv.dt = opts->dt;

@@ -50,7 +50,25 @@ struct OpView {
     const double2* luL;       // [2 kappa_max][2 n1][kb]
     const int* luP;           // [2 kappa_max][2 n1]
     const int* prec_order;    // channels sorted by radial block
+    // bounds checking (debug builds, -DDG_BOUNDS): the allocated sizes the checks compare with and
+    // a word collecting one bit per kind of violation (null: no checking)
+    unsigned int* bounds_err;
+    int64_t nb_part;          // owner/gather partial slots as allocated (one float4 each)
+    int64_t nb_coup;          // stored coupling values per buffer (floats or doubles)
 };
+
+// DG_INB(A, cond, bit): true if cond holds; in a debug build a failed check also records bit in the
+// op's bounds word, and the caller skips (or redirects) the access.  Release builds: always true.
+#ifdef DG_BOUNDS
+__device__ __forceinline__ bool dg_inb(const OpView& A, bool ok, int bit)
+{
+    if (!ok && A.bounds_err) atomicOr(A.bounds_err, 1u << bit);
+    return ok;
+}
+#define DG_INB(A, cond, bit) dg_inb((A), (cond), (bit))
+#else
+#define DG_INB(A, cond, bit) true
+#endif
 
 // One chunk of a (kappa_a, kappa_b) pair group for the grouped double-float assembly: pairs
 // first .. first + count - 1 of the group-ordered pair list and the group's nl multipoles

@@ -212,6 +212,7 @@ __device__ __forceinline__ void assemble_grp_body(const OpView& A, const AsmChun
             ll[k] = (w[k].s - hh[k]) + w[k].c;
         }
         int64_t o = (p * nrd + idx) * 4;
+        if (!DG_INB(A, o + 4 <= A.nb_coup, 4)) continue;
         *reinterpret_cast<float4*>(Wh + o) = make_float4(hh[0], hh[1], hh[2], hh[3]);
         *reinterpret_cast<float4*>(Wl + o) = make_float4(ll[0], ll[1], ll[2], ll[3]);
     }

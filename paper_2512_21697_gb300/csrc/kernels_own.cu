@@ -195,10 +195,13 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
                 const int nb = A.own_nbr[own0 + k];
                 float* st = wring + s * STAGE32;
                 spair[s] = p;   // published by the arrive below
+                // debug builds: copy from the buffers' starts instead of past their ends
+                const int64_t pw = DG_INB(A, (p * n1 + r0 + rows) * ROWF <= A.nb_coup, 0) ? p : 0;
+                const int nbw = DG_INB(A, ((int64_t)nb * n1 + hi) * 2 <= (int64_t)A.nch * n1 * 2, 1) ? nb : 0;
                 fence_proxy_async();
                 mbar_expect_tx(&full[s], bytes + xbytes);
-                bulk_load(st, W + (p * n1 + r0) * ROWF, bytes, &full[s]);
-                bulk_load(st + TR * ROWF + xoff, x + ((int64_t)nb * n1 + lo) * 2, xbytes, &full[s]);
+                bulk_load(st, W + (pw * n1 + r0) * ROWF, bytes, &full[s]);
+                bulk_load(st + TR * ROWF + xoff, x + ((int64_t)nbw * n1 + lo) * 2, xbytes, &full[s]);
                 issued = k + 1;
             }
         }
@@ -261,7 +264,8 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
                     t1.x = fmaf(w.y, xv.x, t1.x); t1.x = fmaf(w.w, xv.z, t1.x);
                     t1.y = fmaf(w.y, xv.y, t1.y); t1.y = fmaf(w.w, xv.w, t1.y);
                 }
-                pp[j] = make_float4(t0.x, t0.y, t1.x, t1.y);
+                if (DG_INB(A, ((int64_t)p * ntile + tile) * NOUT + j < A.nb_part, 2))
+                    pp[j] = make_float4(t0.x, t0.y, t1.x, t1.y);
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
@@ -308,14 +312,19 @@ __global__ void __launch_bounds__(NT) k_apply_gather32(OpView A, int sign, float
         float4 yv = *reinterpret_cast<const float4*>(y + o);
         float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int e = A.in_start[ch]; e < A.in_start[ch + 1]; e++) {
-            const float4* pp = part + (int64_t)A.in_pair[e] * ntile * NOUT;
-            float4 v = pp[(int64_t)tile * NOUT + tid + HO];
+            const int64_t pb0 = (int64_t)A.in_pair[e] * ntile * NOUT;
+            const float4* pp = part + pb0;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int64_t i0 = (int64_t)tile * NOUT + tid + HO;
+            float4 v = DG_INB(A, pb0 + i0 < A.nb_part, 3) ? pp[i0] : z4;
             if (tid < HO && tile > 0) {
-                float4 u = pp[(int64_t)(tile - 1) * NOUT + TR + HO + tid];
+                const int64_t i1 = (int64_t)(tile - 1) * NOUT + TR + HO + tid;
+                float4 u = DG_INB(A, pb0 + i1 < A.nb_part, 3) ? pp[i1] : z4;
                 v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
             }
             if (tid >= TR - HO && tile + 1 < ntile) {   // tid < TR here
-                float4 u = pp[(int64_t)(tile + 1) * NOUT + tid - TR + HO];
+                const int64_t i2 = (int64_t)(tile + 1) * NOUT + tid - TR + HO;
+                float4 u = DG_INB(A, pb0 + i2 < A.nb_part, 3) ? pp[i2] : z4;
                 v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
             }
             t.x += v.x; t.y += v.y; t.z += v.z; t.w += v.w;
@@ -450,11 +459,14 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 float* st = wring + s * stage_f;
                 spair[s] = p;   // published by the arrive below
                 snbr[s] = nb;
+                // debug builds: copy from the buffers' starts instead of past their ends
+                const int64_t pw = DG_INB(A, (p * n1 + r0 + rows) * ROWF <= A.nb_coup, 0) ? p : 0;
+                const int nbw = DG_INB(A, ((int64_t)nb * n1 + hi) * 2 <= (int64_t)A.nch * n1 * 2, 1) ? nb : 0;
                 fence_proxy_async();
                 mbar_expect_tx(&full[s], 2 * bytes + ubytes);
-                bulk_load(st, Wh + (p * n1 + r0) * ROWF, bytes, &full[s]);
-                bulk_load(st + TR * ROWF, Wl + (p * n1 + r0) * ROWF, bytes, &full[s]);
-                bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nb * n1 + lo) * 2, ubytes, &full[s]);
+                bulk_load(st, Wh + (pw * n1 + r0) * ROWF, bytes, &full[s]);
+                bulk_load(st + TR * ROWF, Wl + (pw * n1 + r0) * ROWF, bytes, &full[s]);
+                bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nbw * n1 + lo) * 2, ubytes, &full[s]);
                 issued = k + 1;
             }
         }
@@ -495,6 +507,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 float4* pr = part_r + (((int64_t)p * ntile + tile) * NOUT) * 2;
                 float4* pbp = part_b + ((int64_t)p * ntile + tile) * NOUT;
                 const int j = lt;   // one output row per thread (NOUT == NT)
+                const bool slot_ok = DG_INB(A, ((int64_t)p * ntile + tile) * NOUT + j < A.nb_part, 2);
                 DfAcc tt[4];
                 for (int q = 0; q < 4; q++) df_zero(tt[q]);
                 float tb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -520,9 +533,11 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                         tb[3] += wh.y * q.y + wh.w * q.w;
                     }
                 }
-                pr[2 * j] = make_float4(tt[0].s, tt[0].c, tt[1].s, tt[1].c);
-                pr[2 * j + 1] = make_float4(tt[2].s, tt[2].c, tt[3].s, tt[3].c);
-                if (need_b) pbp[j] = make_float4(tb[0], tb[1], tb[2], tb[3]);
+                if (slot_ok) {
+                    pr[2 * j] = make_float4(tt[0].s, tt[0].c, tt[1].s, tt[1].c);
+                    pr[2 * j + 1] = make_float4(tt[2].s, tt[2].c, tt[3].s, tt[3].c);
+                    if (need_b) pbp[j] = make_float4(tb[0], tb[1], tb[2], tb[3]);
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
@@ -638,6 +653,7 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
             if (tid >= TR - HO && tile + 1 < ntile) { js[nj] = tid - TR + HO; ts[nj++] = tile + 1; }
             for (int q = 0; q < nj; q++) {
                 int64_t i = (int64_t)ts[q] * NOUT + js[q];
+                if (!DG_INB(A, p * ntile * NOUT + i < A.nb_part, 3)) continue;
                 float4 a = pr[2 * i], c = pr[2 * i + 1];
                 DfAcc t0 = {a.x, a.y}, t1 = {a.z, a.w}, t2 = {c.x, c.y}, t3 = {c.z, c.w};
                 df_add(acc[0], t0, -1.f);

@@ -99,6 +99,7 @@ struct dirac_op {
     float* gfield = nullptr;     // its six field factors (device) and, in a graph, the gate flag
     int* ggate = nullptr;
     int* dev_err = nullptr;      // set by kernels whose bounded waits ran out
+    unsigned int* bounds_err = nullptr;   // bit per check site, set by debug (DG_BOUNDS) builds only
     double2* part_d2 = nullptr;
     double2* psi0_g = nullptr;   // ground state of the kappa=-1 mu=+1/2 channel (2 n1)
     double* bvec = nullptr;      // bound eigenvectors per kappa slot, [vector][2 n1] (built on first use)
