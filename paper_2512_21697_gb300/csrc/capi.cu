@@ -503,6 +503,7 @@ extern "C" void dirac_op_free(dirac_op* op)
         cudaEventDestroy(pe.second.first);
         cudaEventDestroy(pe.second.second);
     }
+    if (op->ev_res) cudaEventDestroy(op->ev_res);
     for (int i = 0; i < 2; i++) {
         if (op->ev_asm[i]) cudaEventDestroy(op->ev_asm[i]);
         if (op->ev_use[i]) cudaEventDestroy(op->ev_use[i]);
@@ -1145,6 +1146,7 @@ extern "C" dirac_status dirac_op_set_overlap(dirac_op* op, int enable)
             (e = dev_alloc(op, &a.Wl, (size_t)std::max<int64_t>(op->npairs, 1) * be)))
             return e;
         CUDA_TRY(cudaStreamCreateWithFlags(&op->st_asm, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&op->ev_res, cudaEventDisableTiming));
         for (int i = 0; i < 2; i++) {
             CUDA_TRY(cudaEventCreateWithFlags(&op->ev_asm[i], cudaEventDisableTiming));
             CUDA_TRY(cudaEventCreateWithFlags(&op->ev_use[i], cudaEventDisableTiming));
@@ -1184,14 +1186,22 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
         } else {
             CUDA_TRY(cudaStreamWaitEvent(op->st, op->ev_asm[op->acur], 0));
         }
-        if (ovl && step + 1 < n_steps) {
+        // the next step's assembly starts once this step's first residual pass is done, so that it
+        // runs beside the memory- and latency-bound inner solve rather than the FP32-bound residual
+        bool next_launched = !(ovl && step + 1 < n_steps);
+        auto launch_next = [&]() -> dirac_status {
+            if (next_launched) return DIRAC_OK;
+            next_launched = true;
             const int nx = 1 - op->acur;
+            CUDA_TRY(cudaEventRecord(op->ev_res, op->st));
+            CUDA_TRY(cudaStreamWaitEvent(op->st_asm, op->ev_res, 0));
             CUDA_TRY(cudaStreamWaitEvent(op->st_asm, op->ev_use[nx], 0));
             k_set_step_time<<<1, 1, 0, op->st_asm>>>(op->aset[nx].t_eval, t_start, step + 1, o.dt, t_off);
             op->launches++;
             launch_assemble_set(op, op->st_asm, op->aset[nx]);
             CUDA_TRY(cudaEventRecord(op->ev_asm[nx], op->st_asm));
-        }
+            return DIRAC_OK;
+        };
         // b = A_- psi, ||b||^2 (precision 2 forms them inside the residual passes)
         if (o.precision == 0) {
             apply_accurate(op, -1, psi, K.b, nullptr, op->part_n);
@@ -1224,6 +1234,8 @@ extern "C" dirac_status dirac_step(dirac_op* op, void* psi_dev, void* hist_dev, 
             for (;;) {
                 // true residual r = b - A x accurate to double precision; done when ||r|| <= tol ||b||
                 residual_accurate(op, psi);
+                e = launch_next();
+                if (e) return e;
                 e = read_state(op, K, hs);
                 if (e) return e;
                 if (hs.done || hs.status) break;

@@ -122,6 +122,7 @@ struct dirac_op {
     int acur = 0;                        // the set op->Wh / op->Wl currently point to
     cudaStream_t st_asm = nullptr;
     cudaEvent_t ev_asm[2] = {nullptr, nullptr}, ev_use[2] = {nullptr, nullptr};
+    cudaEvent_t ev_res = nullptr;        // the current step's first residual pass, done
 };
 
 namespace dg {
