@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and ``bench.py``'s cpu_baseline /
 reference arm are the only callers.  The arithmetic lives in ``oracle.c`` (plain C, double
-precision); this module only builds it with gcc and marshals numpy arrays through ctypes.
+precision); this module builds it with gcc and marshals numpy arrays through ctypes.  The
+photoelectron spectrum (Eq. dPdE) is numpy post-processing of the C routines' eigenpairs.
 It shares no code with the CUDA library in ``paper_2512_21697_gb300``.
 
 Vectors are complex128 in "paper order": channel-major, nb = 2(N+1) coefficients per channel,
@@ -287,6 +288,60 @@ class Oracle:
         out = np.zeros(4)
         self.lib.or_observables(self._h, _dp(psi.view(np.float64)), _dp(out))
         return dict(norm=out[0], energy=out[1], p_ground=out[2], p_bound=out[3])
+
+    # -- photoelectron spectrum (Sec. 4.3, Eq. dPdE): numpy post-processing of the eigenpairs above --
+
+    def spectrum_levels(self, psi, e_lo, e_hi):
+        """Discrete spectrum of psi per kappa in use: the eigenvalues E_j of H0 v = E S v with
+        e_lo < E_j <= e_hi (ascending) and q_j = sum over the channels (kappa, mu) of
+        |v_j^T S psi_{kappa mu}|^2 (v_j normalised v^T S v = 1).  Returns {kappa: (E, q)}."""
+        psi = np.asarray(psi, dtype=np.complex128)
+        out = {}
+        for kappa in sorted(set(int(k) for k in self.kappa)):
+            E, V = self.eigen(kappa)
+            S, _ = self.radial(kappa)
+            sel = (E > e_lo) & (E <= e_hi)
+            Vs = V[sel]
+            q = np.zeros(int(sel.sum()))
+            for a in np.nonzero(self.kappa == kappa)[0]:
+                c = Vs @ (S @ psi[a * self.nb:(a + 1) * self.nb])
+                q += c.real ** 2 + c.imag ** 2
+            out[kappa] = (E[sel].copy(), q)
+        return out
+
+    @staticmethod
+    def level_spacing(E):
+        """Local level spacing of ascending levels: (E_{j+1} - E_{j-1}) / 2 inside, the one-sided
+        difference at the two ends.  The box-normalised eigenvectors become energy-normalised
+        continuum states when divided by its square root (density of states 1 / dE)."""
+        E = np.asarray(E, dtype=np.float64)
+        d = np.empty_like(E)
+        d[1:-1] = 0.5 * (E[2:] - E[:-2])
+        d[0] = E[1] - E[0]
+        d[-1] = E[-1] - E[-2]
+        return d
+
+    def spectrum(self, psi, e_lo, e_hi, grid):
+        """dP/dE (Eq. dPdE) on an energy grid: per kappa the densities q_j / dE_j at its levels,
+        linearly interpolated in E (zero outside the kappa's first and last level in the window;
+        a kappa with fewer than two levels there contributes nothing), summed over kappa."""
+        grid = np.asarray(grid, dtype=np.float64)
+        P = np.zeros(len(grid))
+        for kappa, (E, q) in self.spectrum_levels(psi, e_lo, e_hi).items():
+            if len(E) < 2:
+                continue
+            P += np.interp(grid, E, q / self.level_spacing(E), left=0.0, right=0.0)
+        return P
+
+    @staticmethod
+    def spectrum_error(grid, p_n, p_m, e1, e2):
+        """Err_{n,m} = integral over [e1, e2] of |P_n(E) - P_m(E)|^2 dE (Sec. 4.3), by the trapezoid
+        rule over the grid points inside [e1, e2] (ascending grid)."""
+        grid = np.asarray(grid, dtype=np.float64)
+        sel = (grid >= e1) & (grid <= e2)
+        e = grid[sel]
+        f = np.abs(np.asarray(p_n)[sel] - np.asarray(p_m)[sel]) ** 2
+        return float(np.sum(0.5 * (f[1:] + f[:-1]) * (e[1:] - e[:-1]))) if len(e) > 1 else 0.0
 
     def active_mask(self):
         """Boolean mask over the full vector: True where a basis function is used."""
