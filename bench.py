@@ -46,6 +46,8 @@ def parse():
                     help="train the learned initial guess on production trajectories, then time guess=2 vs guess=1")
     ap.add_argument("--factorised", action="store_true",
                     help="factorised complex64 apply in the inner solve (coupling never stored)")
+    ap.add_argument("--spectrum", action="store_true",
+                    help="also time the photoelectron spectrum dP/dE of the final state (window (0, 2] a.u.)")
     ap.add_argument("--overlap", action="store_true",
                     help="precision 2: assemble the next step during the current solve (same arithmetic)")
     return ap.parse_args()
@@ -534,6 +536,36 @@ def batch_bench(args, world, rank, local, dist):
         dist.destroy_process_group()
 
 
+def spectrum_measure(op, bas, psi, e_hi=2.0, n_grid=2001, reps=5):
+    """dP/dE (Eq. dPdE) of the state on [0, e_hi]: the first call's wall time (eigenpairs of the
+    window, once per window) and the device time of later calls (projection, densities, grid)
+    with CUDA events on the op's stream; the projection kernel's FP64 work against the FP64 peak."""
+    import time
+    import numpy as np
+    import torch
+    grid = np.linspace(0.0, e_hi, n_grid)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    P, nl, nq = op.spectrum(psi, 0.0, e_hi, grid, counts=True)
+    setup_s = time.perf_counter() - t0
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(op.stream)
+    for _ in range(reps):
+        op.spectrum(psi, 0.0, e_hi, grid)
+    ev1.record(op.stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / reps
+    ns = 2 * (bas.n // (2 * bas.nch))
+    # per projection: a real eigenvector against complex S psi, 2 FMA = 4 flops per entry; plus S psi
+    # per channel (2 n1 rows x 13 block-diagonals x 2 x 2 FMA)
+    flops = 4.0 * nq * ns + bas.nch * ns * 13 * 2 * 4.0
+    return {"window": [0.0, e_hi], "grid_points": n_grid, "levels": nl, "projections": nq,
+            "eigen_setup_s": setup_s, "ms_per_call": ms, "calls_per_s": 1e3 / ms,
+            "max_dpde": float(np.max(P)), "fp64_flops_per_call": flops,
+            "fp64_tflops": flops / (ms * 1e-3) / 1e12,
+            "note": "call time includes the grid copy in and the result copy out; eigenpairs kept"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -644,6 +676,7 @@ def main():
             dist.destroy_process_group()
         return
     obs = op.observables(psi)
+    spec = spectrum_measure(op, bas, psi) if args.spectrum else None
     fp64 = None
     if args.precision != 0 and not args.no_fp64_compare:
         fp64 = fp64_compare(bas, cfg, psi0_h, t0, args, stream, dev)
@@ -670,6 +703,8 @@ def main():
         "clocks": ck,
         "observables": obs,
     }
+    if spec:
+        line["spectrum"] = spec
     if roof32 and roof32 is not roof:
         line["roofline_spmv32"] = roof32
     if fp64:

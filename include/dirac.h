@@ -303,6 +303,33 @@ dirac_status dirac_op_set_factorised(dirac_op* op, int enable);
  * Synchronises the op's stream.  DIRAC_E_ARG on bad arguments. */
 dirac_status dirac_selftest_wait(dirac_op* op, double limit_cycles, int* timed_out);
 
+/* Differential photoelectron energy spectrum (Sec. 4.3, Eq. dPdE) of the device state psi_dev
+ * (complex128, the library's layout, length n as in dirac_step):
+ *   dP/dE = sum over the channels (kappa, mu) of |<psi_{kappa mu E} | psi>|^2.
+ * The continuum states of a kappa are its eigenvectors v_j of H0_kappa v = E S_kappa v with
+ * e_lo < E_j <= e_hi (v^T S v = 1); dividing by the square root of the local level spacing dE_j
+ * (central difference of the neighbouring levels, one-sided at the window's ends) energy-normalises
+ * them, so at a kappa's levels its density is sum over mu |v_j^T S psi_{kappa mu}|^2 / dE_j.
+ * dpde[g] (host, n_grid doubles) = the sum over kappa of those densities linearly interpolated at
+ * e_grid[g] (host; zero outside a kappa's first and last level in the window; a kappa with fewer
+ * than two levels there adds nothing).  counts (may be NULL) receives two numbers: the levels in
+ * the window over every kappa in use, and the projections formed (the sum over the channels of
+ * their kappa's levels).  Energies in the shifted convention (bound states below 0).
+ * The first call for a window computes the eigenpairs (cuSOLVER, per kappa; allocates, so not
+ * inside a stream capture) and keeps them on the op; later calls with the same window reuse them.
+ * Synchronises the op's stream.  DIRAC_E_ARG for a NULL op or state, non-finite or empty windows
+ * (e_lo >= e_hi), n_grid < 0 or > 2^26, NULL grid arrays with n_grid > 0 or non-finite grid
+ * energies; DIRAC_E_NUMERIC if the eigensolver fails. */
+dirac_status dirac_spectrum(dirac_op* op, const void* psi_dev, double e_lo, double e_hi, int n_grid,
+                            const double* e_grid, double* dpde, int64_t* counts);
+
+/* Error of a spectrum against a reference (Sec. 4.3): *err = integral over [e1, e2] of
+ * |p_n(E) - p_m(E)|^2 dE by the trapezoid rule over the grid points inside [e1, e2].  Host arrays of
+ * n_grid doubles, e_grid strictly ascending.  DIRAC_E_ARG on NULL arrays, e1 > e2 or a grid that
+ * does not ascend.  No GPU work. */
+dirac_status dirac_spectrum_error(int n_grid, const double* e_grid, const double* p_n, const double* p_m,
+                                  double e1, double e2, double* err);
+
 /* Index-check word of a debug build (the library compiled with -DDG_BOUNDS): the owner and gather
  * passes and the grouped assembly test every computed global index of the coupling values, the
  * vectors and the partial products against the buffers' sizes before using it, skip the access

@@ -85,6 +85,8 @@ SIGNATURES = {
     "dirac_op_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
     "dirac_selftest_wait": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int)]),
     "dirac_bounds_word": (C.c_int, [_VP, C.POINTER(C.c_uint), C.POINTER(C.c_int)]),
+    "dirac_spectrum": (C.c_int, [_VP, _VP, C.c_double, C.c_double, C.c_int, _DP, _DP, C.POINTER(C.c_int64)]),
+    "dirac_spectrum_error": (C.c_int, [C.c_int, _DP, _DP, _DP, C.c_double, C.c_double, _DP]),
     "dirac_op_set_factorised": (C.c_int, [_VP, C.c_int]),
     "dirac_op_get_schedule": (C.c_int, [_VP, C.c_int]),
     "dirac_last_error": (C.c_char_p, []),
@@ -239,6 +241,16 @@ class Operator:
     def set_factorised(self, enable=True):
         """dirac_op_set_factorised: factorised complex64 apply in the inner solve."""
         _check(lib().dirac_op_set_factorised(self._h, int(bool(enable))), "dirac_op_set_factorised")
+
+    def spectrum(self, psi, e_lo, e_hi, grid, counts=False):
+        """dirac_spectrum: (dP/dE on the host grid, levels in the window) or, with counts=True,
+        (dP/dE, levels, channel-level projections formed)."""
+        g = np.ascontiguousarray(grid, dtype=np.float64)
+        out = np.zeros(len(g))
+        cn = (C.c_int64 * 2)()
+        _check(lib().dirac_spectrum(self._h, _ptr(psi), float(e_lo), float(e_hi), len(g), _dp(g), _dp(out), cn),
+               "dirac_spectrum")
+        return (out, int(cn[0]), int(cn[1])) if counts else (out, int(cn[0]))
 
     def bounds_word(self):
         """dirac_bounds_word: (bits of failed index checks since the last call, 1 if the library
@@ -424,6 +436,19 @@ def _stream_ptr(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+def spectrum_error(grid, p_n, p_m, e1, e2):
+    """dirac_spectrum_error: trapezoid integral of |p_n - p_m|^2 over the grid points in [e1, e2]."""
+    g = np.ascontiguousarray(grid, dtype=np.float64)
+    a = np.ascontiguousarray(p_n, dtype=np.float64)
+    b = np.ascontiguousarray(p_m, dtype=np.float64)
+    if not (len(a) == len(b) == len(g)):
+        raise ValueError("grid and spectra differ in length")
+    err = C.c_double(0)
+    _check(lib().dirac_spectrum_error(len(g), _dp(g), _dp(a), _dp(b), float(e1), float(e2), C.byref(err)),
+           "dirac_spectrum_error")
+    return float(err.value)
 
 
 def guess_features(op, states, t_next, x, s):

@@ -82,7 +82,7 @@ __global__ void k_pbound(OpView A, const double2* __restrict__ psi, const double
     do {                                                                                           \
         cudaError_t e_ = (call);                                                                   \
         if (e_ != cudaSuccess) {                                                                   \
-            set_error(std::string("bound states: ") + #call + ": " + cudaGetErrorString(e_));       \
+            set_error(std::string("eigenpairs: ") + #call + ": " + cudaGetErrorString(e_));         \
             ok = DIRAC_E_CUDA;                                                                     \
             goto done;                                                                             \
         }                                                                                          \
@@ -91,24 +91,27 @@ __global__ void k_pbound(OpView A, const double2* __restrict__ psi, const double
     do {                                                                                           \
         cusolverStatus_t s_ = (call);                                                              \
         if (s_ != CUSOLVER_STATUS_SUCCESS) {                                                       \
-            set_error(std::string("bound states: ") + #call + " failed with status " +             \
+            set_error(std::string("eigenpairs: ") + #call + " failed with status " +               \
                       std::to_string((int)s_));                                                    \
             ok = DIRAC_E_NUMERIC;                                                                  \
             goto done;                                                                             \
         }                                                                                          \
     } while (0)
 
-// Bound eigenvectors of every kappa in use, into op->bvec / op->bstart (device), once.
-dirac_status bound_setup(dirac_op* op)
+// Eigenpairs of H0_kappa v = E S_kappa v with vl < E <= vu for every kappa slot in use: cuSOLVER's
+// dense generalised symmetric-definite solver restricted to the window, on the functions the kappa
+// uses (v^T S v = 1), the vectors expanded to the library's slot order.  Host results: hvec
+// [vector][2 n1], hE [vector] (ascending within a slot), hstart [2 kappa_max + 1].
+dirac_status eig_window(dirac_op* op, double vl, double vu, std::vector<double>& hvec, std::vector<double>& hE,
+                        std::vector<int>& hstart)
 {
-    if (op->bvec) return DIRAC_OK;
     const Basis& B = op->B;
     int n1 = B.n1, ns = 2 * n1, nk2 = 2 * B.p.kappa_max;
-    double c2 = B.p.c * B.p.c;
     std::vector<int> used(nk2, 0);
     for (int ch = 0; ch < B.nch; ch++) used[kappa_slot(B.kap[ch])] = 1;
-    std::vector<int> hstart(nk2 + 1, 0);
-    std::vector<double> hvec;
+    hstart.assign(nk2 + 1, 0);
+    hvec.clear();
+    hE.clear();
     dirac_status ok = DIRAC_OK;
     cusolverDnHandle_t h = nullptr;
     double *dA = nullptr, *dB = nullptr, *dW = nullptr, *work = nullptr;
@@ -143,7 +146,7 @@ dirac_status bound_setup(dirac_op* op)
         BTRY(cudaMemcpyAsync(dB, hB.data(), sizeof(double) * m * m, cudaMemcpyHostToDevice, op->st));
         int meig = 0, lwork = 0;
         STRY(cusolverDnDsygvdx_bufferSize(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_V,
-                                          CUBLAS_FILL_MODE_LOWER, m, dA, m, dB, m, -c2, 0.0, 0, 0, &meig, dW,
+                                          CUBLAS_FILL_MODE_LOWER, m, dA, m, dB, m, vl, vu, 0, 0, &meig, dW,
                                           &lwork));
         if (lwork > lwork_cap) {
             if (work) cudaFree(work);
@@ -152,7 +155,7 @@ dirac_status bound_setup(dirac_op* op)
             lwork_cap = lwork;
         }
         STRY(cusolverDnDsygvdx(h, CUSOLVER_EIG_TYPE_1, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_V,
-                               CUBLAS_FILL_MODE_LOWER, m, dA, m, dB, m, -c2, 0.0, 0, 0, &meig, dW, work, lwork,
+                               CUBLAS_FILL_MODE_LOWER, m, dA, m, dB, m, vl, vu, 0, 0, &meig, dW, work, lwork,
                                dinfo));
         int info = 0;
         std::vector<double> Ew(std::max(meig, 1));
@@ -164,16 +167,48 @@ dirac_status bound_setup(dirac_op* op)
         }
         BTRY(cudaStreamSynchronize(op->st));
         if (info != 0) {
-            set_error("bound states: generalised eigensolver info " + std::to_string(info) + " for kappa " +
+            set_error("eigenpairs: generalised eigensolver info " + std::to_string(info) + " for kappa " +
                       std::to_string(kappa));
             ok = DIRAC_E_NUMERIC;
             goto done;
         }
         for (int e = 0; e < meig; e++) {
-            if (!(Ew[e] > -c2 && Ew[e] < 0)) continue;
+            if (!(Ew[e] > vl && Ew[e] <= vu)) continue;
             size_t o = hvec.size();
             hvec.resize(o + ns, 0.0);
             for (int i = 0; i < m; i++) hvec[o + act[i]] = hV[(size_t)e * m + i];
+            hE.push_back(Ew[e]);
+            hstart[ks + 1]++;
+        }
+    }
+done:
+    if (h) cusolverDnDestroy(h);
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dW);
+    cudaFree(work);
+    cudaFree(dinfo);
+    return ok;
+}
+
+// Bound eigenvectors of every kappa in use (-c^2 < E < 0), into op->bvec / op->bstart (device), once.
+dirac_status bound_setup(dirac_op* op)
+{
+    if (op->bvec) return DIRAC_OK;
+    const Basis& B = op->B;
+    int nk2 = 2 * B.p.kappa_max, ns = 2 * B.n1;
+    double c2 = B.p.c * B.p.c;
+    std::vector<double> wvec, wE;
+    std::vector<int> wstart;
+    dirac_status ok = eig_window(op, -c2, 0.0, wvec, wE, wstart);
+    if (ok) return ok;
+    std::vector<int> hstart(nk2 + 1, 0);
+    std::vector<double> hvec;
+    for (int ks = 0; ks < nk2; ks++) {
+        hstart[ks + 1] = hstart[ks];
+        for (int v = wstart[ks]; v < wstart[ks + 1]; v++) {
+            if (!(wE[v] < 0)) continue;
+            hvec.insert(hvec.end(), wvec.begin() + (size_t)v * ns, wvec.begin() + (size_t)(v + 1) * ns);
             hstart[ks + 1]++;
         }
     }
@@ -199,12 +234,6 @@ dirac_status bound_setup(dirac_op* op)
         op->nbound = nvec;
     }
 done:
-    if (h) cusolverDnDestroy(h);
-    cudaFree(dA);
-    cudaFree(dB);
-    cudaFree(dW);
-    cudaFree(work);
-    cudaFree(dinfo);
     return ok;
 }
 

@@ -503,6 +503,7 @@ extern "C" void dirac_op_free(dirac_op* op)
         cudaEventDestroy(pe.second.first);
         cudaEventDestroy(pe.second.second);
     }
+    spec_free(op);
     if (op->ev_res) cudaEventDestroy(op->ev_res);
     for (int i = 0; i < 2; i++) {
         if (op->ev_asm[i]) cudaEventDestroy(op->ev_asm[i]);

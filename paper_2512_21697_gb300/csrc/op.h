@@ -38,6 +38,8 @@ struct AsmSet {
 
 }  // namespace dg
 
+namespace dg { struct SpecState; }
+
 struct dirac_op {
     dg::Basis B;                 // host copy of the basis data the operator needs
     dirac_pulse pulse{};
@@ -123,6 +125,7 @@ struct dirac_op {
     cudaStream_t st_asm = nullptr;
     cudaEvent_t ev_asm[2] = {nullptr, nullptr}, ev_use[2] = {nullptr, nullptr};
     cudaEvent_t ev_res = nullptr;        // the current step's first residual pass, done
+    dg::SpecState* spec = nullptr;       // photoelectron spectrum: eigenpairs of one window (first use)
 };
 
 namespace dg {
@@ -151,6 +154,9 @@ void bicgstab_begin(dirac_op* op, const Krylov& K, int max_iter, bool rel_start 
 void set_error(const std::string& msg);
 void graph_free(dirac_op* op);
 dirac_status bound_population(dirac_op* op, const double2* psi, double* out);
+dirac_status eig_window(dirac_op* op, double vl, double vu, std::vector<double>& hvec, std::vector<double>& hE,
+                        std::vector<int>& hstart);
+void spec_free(dirac_op* op);
 dirac_status guess_buffers(dirac_op* op);
 dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, const double2* h2, const double2* h3,
                         double t_start, int step, double2* x, const int* gate, cudaStream_t st,

@@ -43,6 +43,23 @@ def test_argument_validation(libdirac):
     assert libdirac.dirac_basis_build(C.byref(p), C.byref(h), None, None) == B.DIRAC_E_ARG
     assert libdirac.dirac_basis_dim(None) == -1
     assert libdirac.dirac_step(None, None, None, None, 1, 0.0, None, None) == B.DIRAC_E_ARG
+    assert libdirac.dirac_spectrum(None, None, 0.0, 1.0, 0, None, None, None) == B.DIRAC_E_ARG
+
+
+def test_spectrum_error_matches_oracle(libdirac, oracle_mod):
+    # host-only entry point: the trapezoid error integral against the oracle's, on closed forms too
+    g = np.concatenate([np.linspace(0.0, 1.0, 11), np.linspace(1.05, 3.0, 40)])
+    rng = np.random.default_rng(5)
+    pn, pm = rng.random(len(g)), rng.random(len(g))
+    for e1, e2 in [(0.0, 3.0), (0.33, 2.71), (1.0, 1.0), (5.0, 6.0)]:
+        a = B.spectrum_error(g, pn, pm, e1, e2)
+        b = oracle_mod.Oracle.spectrum_error(g, pn, pm, e1, e2)
+        assert abs(a - b) <= 1e-14 * max(1.0, abs(b)), (e1, e2)
+    assert abs(B.spectrum_error(g, pn + 0.3, pn, 0.0, 1.0) - 0.09) <= 1e-14
+    with pytest.raises(B.DiracError):
+        B.spectrum_error(g[::-1], pn, pm, 0.0, 3.0)      # a grid that does not ascend
+    with pytest.raises(B.DiracError):
+        B.spectrum_error(g, pn, pm, 2.0, 1.0)
 
 
 def test_no_gpu_reports_state_error(libdirac):
