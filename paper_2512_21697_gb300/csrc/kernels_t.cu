@@ -925,23 +925,34 @@ template void launch_update_xr_t<float>(int, cudaStream_t, int64_t, const KState
 
 // ---------------------------------------------------------------------------------------------
 // Precision conversions of the refinement loop: d32 = r64 / ||r|| (scaled inner right-hand side)
-// and x64 += ||r|| d32.  scale_src holds ||r||^2 (the outer KState's rnorm2).
+// and x64 += ||r|| d32.  The outer KState's rnorm2 holds ||r||^2.  The scale is formed once per
+// block: an FP64 square root and division per element would make these copies FP64-bound.
 // ---------------------------------------------------------------------------------------------
 __global__ void k_to_float_scaled(int64_t n, const double2* a, const KState* st, float2* b)
 {
+    __shared__ double sc;
+    if (threadIdx.x == 0) sc = st->rnorm2 > 0 ? 1.0 / sqrt(st->rnorm2) : 0.0;
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = st->rnorm2 > 0 ? 1.0 / sqrt(st->rnorm2) : 0.0;
-    b[i] = make_float2((float)(a[i].x * s), (float)(a[i].y * s));
+    const double s = sc;
+    const double2 v = a[i];
+    b[i] = make_float2((float)(v.x * s), (float)(v.y * s));
 }
 
 __global__ void k_add_float_scaled(int64_t n, const float2* d, const KState* st, double2* x)
 {
+    __shared__ double sc;
+    if (threadIdx.x == 0) sc = sqrt(st->rnorm2);
+    __syncthreads();
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double s = sqrt(st->rnorm2);
-    x[i].x += s * (double)d[i].x;
-    x[i].y += s * (double)d[i].y;
+    const double s = sc;
+    const float2 dv = d[i];
+    double2 xv = x[i];
+    xv.x += s * (double)dv.x;
+    xv.y += s * (double)dv.y;
+    x[i] = xv;
 }
 
 __global__ void k_copy32(int64_t n, const float2* a, float2* b)
