@@ -7,27 +7,36 @@
 namespace dg {
 
 // Sum a (complex, real) pair over the block in a fixed order and store the block's partials.
-// Every thread of the block must call it.  Block size must be a multiple of 32, <= 1024.
+// Every thread of the block must call it.  Block size must be a multiple of 32, <= 1024.  A part
+// whose output is NULL is not reduced (FP64 adds are scarce on this part: a norm-only reduction
+// costs a third of a full one); the parts kept are summed in the same order either way.
 __device__ __forceinline__ void block_reduce_store(double2 d, double n, double2* out_d, double* out_n, int64_t slot)
 {
     __shared__ double2 wd[32];
     __shared__ double wn[32];
+    const bool want_d = out_d != nullptr, want_n = out_n != nullptr;   // uniform over the block
     for (int off = 16; off > 0; off >>= 1) {
-        d.x += __shfl_down_sync(0xffffffffu, d.x, off);
-        d.y += __shfl_down_sync(0xffffffffu, d.y, off);
-        n += __shfl_down_sync(0xffffffffu, n, off);
+        if (want_d) {
+            d.x += __shfl_down_sync(0xffffffffu, d.x, off);
+            d.y += __shfl_down_sync(0xffffffffu, d.y, off);
+        }
+        if (want_n) n += __shfl_down_sync(0xffffffffu, n, off);
     }
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { wd[warp] = d; wn[warp] = n; }
+    if (lane == 0) {
+        if (want_d) wd[warp] = d;
+        if (want_n) wn[warp] = n;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         double2 sd = make_double2(0, 0);
         double sn = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-            sd.x += wd[w].x; sd.y += wd[w].y; sn += wn[w];
+            if (want_d) { sd.x += wd[w].x; sd.y += wd[w].y; }
+            if (want_n) sn += wn[w];
         }
-        if (out_d) out_d[slot] = sd;
-        if (out_n) out_n[slot] = sn;
+        if (want_d) out_d[slot] = sd;
+        if (want_n) out_n[slot] = sn;
     }
     __syncthreads();
 }
