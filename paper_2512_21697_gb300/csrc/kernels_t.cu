@@ -881,42 +881,55 @@ template void launch_precond_sm_t<float>(cudaStream_t, const OpView&, const void
 
 // ---------------------------------------------------------------------------------------------
 // x += alpha ph + omega sh;  r = s - omega t;  partials <rh, r>, ||r||^2.  After the s-check ended
-// the solve (done == 2): x += alpha ph only.
+// the solve (done == 2): x += alpha ph only.  A block of UXR_T threads covers 2 UXR_T elements (two
+// per thread, a warp's loads contiguous), so the FP64 block reduction is paid once per two.
 // ---------------------------------------------------------------------------------------------
+constexpr int UXR_T = 128;
+
 template <class T>
-__global__ void k_update_xr(int64_t n, const KState* st, c2<T>* x, c2<T>* r, const c2<T>* ph, const c2<T>* sh,
-                            const c2<T>* s, const c2<T>* t, const c2<T>* rh, double2* part_dot, double* part_nrm)
+__global__ void __launch_bounds__(UXR_T) k_update_xr(int64_t n, const KState* st, c2<T>* x, c2<T>* r,
+                                                     const c2<T>* ph, const c2<T>* sh, const c2<T>* s,
+                                                     const c2<T>* t, const c2<T>* rh, double2* part_dot,
+                                                     double* part_nrm)
 {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * (2 * UXR_T) + threadIdx.x;
     double2 dsum = make_double2(0, 0);
     double nsum = 0;
-    if (i < n && st->status == 0) {
-        c2<T> a = cm<T>(from_d<T>(st->alpha), ph[i]);
-        if (st->done == 2) {
-            x[i].x += a.x;
-            x[i].y += a.y;
-        } else if (!st->done) {
-            c2<T> w = cm<T>(from_d<T>(st->omega), sh[i]);
+    if (st->status == 0 && st->done != 1) {
+        const c2<T> al = from_d<T>(st->alpha), om = from_d<T>(st->omega);
+        const bool only_x = st->done == 2;
+        for (int k = 0; k < 2; k++) {
+            const int64_t i = base + k * UXR_T;
+            if (i >= n) break;
+            c2<T> a = cm<T>(al, ph[i]);
+            if (only_x) {
+                x[i].x += a.x;
+                x[i].y += a.y;
+                continue;
+            }
+            c2<T> w = cm<T>(om, sh[i]);
             x[i].x += a.x + w.x;
             x[i].y += a.y + w.y;
-            c2<T> ot = cm<T>(from_d<T>(st->omega), t[i]);
+            c2<T> ot = cm<T>(om, t[i]);
             c2<T> rn = mk<T>(s[i].x - ot.x, s[i].y - ot.y);
             r[i] = rn;
             c2<T> h = rh[i];
-            dsum.x = (double)h.x * rn.x + (double)h.y * rn.y;
-            dsum.y = (double)h.x * rn.y - (double)h.y * rn.x;
-            nsum = (double)rn.x * rn.x + (double)rn.y * rn.y;
+            dsum.x += (double)h.x * rn.x + (double)h.y * rn.y;
+            dsum.y += (double)h.x * rn.y - (double)h.y * rn.x;
+            nsum += (double)rn.x * rn.x + (double)rn.y * rn.y;
         }
     }
     block_reduce_store(dsum, nsum, part_dot, part_nrm, blockIdx.x);
 }
 
+// blocks = the partial slots of the vector kernels: one per 256 elements
 template <class T>
 void launch_update_xr_t(int blocks, cudaStream_t st, int64_t n, const KState* ks, void* x, void* r, const void* ph,
                         const void* sh, const void* s, const void* t, const void* rh, double2* pd, double* pn)
 {
-    k_update_xr<T><<<blocks, 256, 0, st>>>(n, ks, (c2<T>*)x, (c2<T>*)r, (const c2<T>*)ph, (const c2<T>*)sh,
-                                           (const c2<T>*)s, (const c2<T>*)t, (const c2<T>*)rh, pd, pn);
+    static_assert(2 * UXR_T == 256, "one block per 256 elements, as the other vector kernels");
+    k_update_xr<T><<<blocks, UXR_T, 0, st>>>(n, ks, (c2<T>*)x, (c2<T>*)r, (const c2<T>*)ph, (const c2<T>*)sh,
+                                             (const c2<T>*)s, (const c2<T>*)t, (const c2<T>*)rh, pd, pn);
 }
 template void launch_update_xr_t<double>(int, cudaStream_t, int64_t, const KState*, void*, void*, const void*,
                                          const void*, const void*, const void*, const void*, double2*, double*);
