@@ -2,7 +2,8 @@
 completeness of the eigenvectors in the S inner product (the projections over every level add up
 to the norm computed by the C oracle), the bound window against the C oracle's bound population,
 a single eigenstate (a spike of height 1 / dE at its level, linear in between), closed-form level
-spacings, and closed-form values of the error integral."""
+spacings, the semiclassical density of continuum levels in a box, and closed-form values of the
+error integral."""
 import numpy as np
 import pytest
 
@@ -102,3 +103,23 @@ def test_error_integral_closed_forms():
     # for f = E^2 on [0, 2] with h = 0.1 is 2 * 0.01 / 6 on top of 8 / 3
     err = oracle.Oracle.spectrum_error(g, p + g, p, 0.0, 2.0)
     assert abs(err - (8.0 / 3.0 + 0.02 / 6.0)) <= 1e-12
+
+
+def test_continuum_level_spacing_follows_the_box_law():
+    # continuum levels of a box of radius R: k R + ln(2 k R) / k (Coulomb phase, Z = 1) advances by
+    # pi from one level to the next, so dE = k dk = pi k / (R + (1 - ln(2 k R)) / k^2) (the
+    # nonrelativistic semiclassical law; k^2 = 2E(1 + E / 2c^2)).  A dropped factor in the spacing,
+    # or levels from the wrong branch, miss it by far more than the 15 % allowed here.
+    cfg = W.SMALL
+    o = oracle.Oracle(**W.oracle_params(cfg))
+    R, c = cfg["R"], cfg["c"]
+    for kappa in (-1, 1, -2):
+        E, _ = o.eigen(kappa)
+        Ep = E[(E > 0.0) & (E < 3.0)]
+        d = oracle.Oracle.level_spacing(Ep)[1:-1]
+        Ei = Ep[1:-1]
+        k = np.sqrt(2 * Ei * (1 + Ei / (2 * c * c)))
+        pred = np.pi * k / (R + (1 - np.log(2 * k * R)) / k ** 2)
+        sel = Ei > 0.2
+        assert sel.sum() >= 20
+        assert np.max(np.abs(d[sel] / pred[sel] - 1)) <= 0.15, kappa
