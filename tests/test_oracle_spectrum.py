@@ -2,8 +2,8 @@
 completeness of the eigenvectors in the S inner product (the projections over every level add up
 to the norm computed by the C oracle), the bound window against the C oracle's bound population,
 a single eigenstate (a spike of height 1 / dE at its level, linear in between), closed-form level
-spacings, the semiclassical density of continuum levels in a box, and closed-form values of the
-error integral."""
+spacings, the semiclassical density of continuum levels in a box, a library eigensolver on the
+same dense matrices, and closed-form values of the error integral."""
 import numpy as np
 import pytest
 
@@ -123,3 +123,25 @@ def test_continuum_level_spacing_follows_the_box_law():
         sel = Ei > 0.2
         assert sel.sum() >= 20
         assert np.max(np.abs(d[sel] / pred[sel] - 1)) <= 0.15, kappa
+
+
+def test_levels_and_projections_match_a_library_eigensolver(orc):
+    # the C oracle's eigenpairs against scipy's generalised symmetric-definite solver on the same
+    # dense S and H0 (only the functions the kappa uses): levels, and |v^T S psi|^2 (sign-free)
+    import scipy.linalg as sl
+    x = _state(orc, 6)
+    lv = orc.spectrum_levels(x, -np.inf, np.inf)
+    nb, N = orc.nb, orc.N
+    for kappa, (E, q) in lv.items():
+        S, H = orc.radial(kappa)
+        act = np.ones(nb, bool)
+        act[0] = kappa == -1
+        act[N + 1] = kappa == 1
+        Es, Vs = sl.eigh(H[np.ix_(act, act)], S[np.ix_(act, act)])
+        assert np.allclose(E, Es, rtol=1e-10, atol=1e-10 * np.max(np.abs(Es)))
+        qs = np.zeros(len(Es))
+        for a in np.nonzero(orc.kappa == kappa)[0]:
+            xa = x[a * nb:(a + 1) * nb][act]
+            c = Vs.T @ (S[np.ix_(act, act)] @ xa)
+            qs += np.abs(c) ** 2
+        assert np.allclose(q, qs, rtol=1e-8, atol=1e-12)
