@@ -74,7 +74,7 @@ def test_no_gpu_reports_state_error(libdirac):
     assert st == B.DIRAC_E_STATE
 
 
-@pytest.fixture(scope="module", params=["small", "slice"])
+@pytest.fixture(scope="module", params=["small", "slice", "order5", "wide_l"])
 def pair(request, oracle_mod, libdirac):
     cfg = W.WORKLOADS[request.param]
     return cfg, B.Basis(cfg), oracle_mod.Oracle(**W.oracle_params(cfg))
