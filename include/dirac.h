@@ -184,6 +184,32 @@ dirac_status dirac_observables(dirac_op* op, const void* psi_dev, double* out, i
  * (no reassembly).  Same buffers and errors as dirac_apply. */
 dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, void* y_dev);
 
+/* The operator of the mixed-precision inner solve alone: y = A_sign(t) x (Eq. solPsi with the
+ * coupling of Eq. fullH) in complex64 arithmetic, exactly as the inner BiCGSTAB applies it --
+ * FP32 copies of S and H0 per kappa, FP32 coupling values (precision 1: the FP32 rounding of the
+ * FP64 assembly; precision 2: the hi words of the double-float assembly), and the kernel the
+ * solve uses: the owner/gather passes for order-7 splines, the factorised apply when
+ * dirac_op_set_factorised is on, else the per-row kernel.  Assembles the coupling values for t
+ * first.  x_dev, y_dev: device complex64[n] (interleaved re, im floats, library order), must not
+ * alias.  Synchronises the op's stream (it reads the error word of the bounded bulk-copy waits).
+ * Errors: DIRAC_E_ARG (NULL, aliasing, sign not +-1, precision 0), DIRAC_E_CUDA. */
+dirac_status dirac_apply32(dirac_op* op, int sign, double t, const void* x_dev, void* y_dev);
+
+/* z = M^-1 r in complex64 with the inner solve's current preconditioner schedule
+ * (dirac_op_set_schedule(op, 1, ...)), M = S + i dt/2 H0 (Eq. matrixM) factored in FP64 and rounded
+ * to FP32.  r_dev, z_dev: device complex64[n], must not alias.  DIRAC_E_ARG for precision 0. */
+dirac_status dirac_precond_apply32(dirac_op* op, const void* r_dev, void* z_dev);
+
+/* The refinement residual of a step, r = A_-(t) psi - A_+(t) x (Eq. solPsi), computed as the step
+ * computes it: precision 2 in double-float by the owner/gather passes (order-7 splines) or the
+ * per-row residual kernel, precision 0 and 1 in FP64 (b = A_- psi, then r = b - A_+ x).
+ * Assembles the coupling values for t first.  psi_dev, x_dev, r_dev: device complex128[n]; r_dev
+ * must alias neither.  bnorm (host, nullable) receives ||A_- psi||_2 as the step's tolerance test
+ * uses it (precision 2: from FP32 products).  Synchronises the op's stream.  Errors: DIRAC_E_ARG,
+ * DIRAC_E_CUDA. */
+dirac_status dirac_residual(dirac_op* op, double t, const void* psi_dev, const void* x_dev, void* r_dev,
+                            double* bnorm);
+
 /* Kernel-phase timers.  dirac_profile(op, 1) resets and starts timing every launch group with a
  * pair of CUDA events on the op's stream (0 stops); dirac_profile_read synchronises the stream and
  * returns, per phase, the summed milliseconds and the number of timed launch groups, plus the
@@ -205,20 +231,24 @@ dirac_status dirac_apply_assembled(dirac_op* op, int sign, const void* x_dev, vo
 dirac_status dirac_profile(dirac_op* op, int enable);
 dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_t* launches);
 
-/* dirac_observables with no allocation in the call (the paper has no counterpart; this serves
- * callers that cannot allocate GPU memory at that point: code running while a stream is captured
- * into a CUDA graph, real-time or monitoring threads that must not hit the implicit device
- * synchronisation of cudaMalloc/cudaFree, processes whose device footprint is fixed after setup).
- * Same arguments, outputs and errors as dirac_observables, except n_out <= 3 (the bound-state
- * population needs its eigenvectors set up, which allocates).  Its scratch (block partials and the
- * final sums) is a library-static device array of 2 DIRAC_STATIC_MAX_PARTIALS + 2 complex128
- * values (about 2 MB), held by every GPU that loads the library until the process exits; it
- * supports systems with channels x ceil((N+1)/128) <= DIRAC_STATIC_MAX_PARTIALS and returns
- * DIRAC_E_ARG beyond that.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share the
- * one array: calls whose work overlaps on the GPU (other streams, other host threads on the same
- * device) race on it and must be serialised by the caller.  It calls no cudaMalloc, cudaFree or
- * other allocating routine.  The op's device must be current. */
+/* dirac_observables with no allocation in the call (the paper has no counterpart).  It serves
+ * callers that cannot allocate GPU memory when they read the observables: real-time or monitoring
+ * threads that must not hit the implicit device synchronisation of cudaMalloc/cudaFree, and
+ * processes whose device footprint is fixed once setup is done.  Same arguments, outputs and errors
+ * as dirac_observables, except n_out <= 3 (the bound-state population needs its eigenvectors set
+ * up, which allocates).  Its scratch (block partials and the final sums) is a library-static device
+ * array of 2 DIRAC_STATIC_MAX_PARTIALS + 2 complex128 values (about 2 MB): the driver allocates it
+ * when it loads the library's module on a device (at the module's first use there, at the latest in
+ * dirac_operator_setup), and that GPU holds it until the process exits.  dirac_operator_setup looks
+ * up the array's device address (cudaGetSymbolAddress, with the op's device current), so this call
+ * does no set-up; the address is kept for the life of the process, so the library must not be used
+ * across a cudaDeviceReset.  It supports systems with channels x ceil((N+1)/128) <=
+ * DIRAC_STATIC_MAX_PARTIALS and returns DIRAC_E_ARG beyond that, DIRAC_E_ARG for n_out outside 1..3
+ * and DIRAC_E_STATE if the current device is not the op's.  All calls share the one array, which
+ * keeps the last call's contents (every slot a call reads is written earlier in the same call):
+ * calls whose work overlaps on the GPU (other streams, other host threads on the same device) race
+ * on it and must be serialised by the caller.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine, and it synchronises the op's stream before returning the values. */
 #define DIRAC_STATIC_MAX_PARTIALS 65536
 dirac_status dirac_observables_static(dirac_op* op, const void* psi_dev, double* out, int n_out);
 

@@ -20,7 +20,7 @@
  *     BiCGSTAB (preconditioner: dense LU of M = S + i dt/2 H0, Eq. matrixM) and, for tiny
  *     bases, by a dense LU solve.
  *
- * Readings of the paper where it is silent or garbled (all listed in the design notes):
+ * Readings of the paper where it is silent or garbled:
  *   - p = -i grad (the printed "p = i grad" is a sign slip; with -i grad the DKB pairing of
  *     Eq. dualkinetic is the kinetic-balance one and no spurious states appear).
  *   - alpha_i = [[0, sigma_i], [sigma_i, 0]] (the printed lower block "-sigma_i" is not Hermitian).
@@ -29,9 +29,19 @@
  *   - V(r) in "-I_4 V(r)" is the attractive Coulomb potential Z/r, so the potential energy is -Z/r.
  *   - "Degree d = 7" is read as B-spline order k (the order is a parameter here).
  *   - The first two and the last two B-splines are removed (zero value and first derivative at
- *     r = 0, "a similar choice" at r_max).
+ *     r = 0, "a similar choice" at r_max).  B_1, the first one kept, is nonzero in slope at r = 0;
+ *     it is used only where both radial components of the DKB pair still vanish there: the large
+ *     type of kappa = -1 (P = B_1, Q = (B_1' - B_1/r)/2c, both zero at r = 0) and the small type of
+ *     kappa = +1; every other slot built on B_1 is left out (identity in S, zero in H).  Without it
+ *     the 1s level misses its closed form.
  *   - Polarisation x, propagation z (sigma_x and Y_l0(z) in Eq. Htheta).  The pulse is switched
  *     on for 0 <= t <= T globally and its separable form is used at every r inside that window.
+ *   - H(t) in a step is taken at the midpoint t + dt/2 (the derivation of Sec. 2.4); the printed
+ *     H(t + dt) of Eq. solPsi is the time_eval = 1 option.
+ *   - The LU of M (Eq. matrixM) uses partial pivoting (M is complex symmetric, not Hermitian);
+ *     the preconditioner changes iteration counts only, never the converged step.
+ *   - The stopping test is the true relative residual ||b - A_+ x||_2 <= tol ||b||_2, BiCGSTAB
+ *     right-preconditioned with shadow vector r0.
  */
 #include "oracle.h"
 #include <complex.h>

@@ -63,6 +63,9 @@ SIGNATURES = {
     "dirac_observables": (C.c_int, [_VP, _VP, _DP, C.c_int]),
     "dirac_run": (C.c_int, [_VP, _VP, _VP, _IP, C.c_int, C.c_double, _IP, _DP]),
     "dirac_apply_assembled": (C.c_int, [_VP, C.c_int, _VP, _VP]),
+    "dirac_apply32": (C.c_int, [_VP, C.c_int, C.c_double, _VP, _VP]),
+    "dirac_precond_apply32": (C.c_int, [_VP, _VP, _VP]),
+    "dirac_residual": (C.c_int, [_VP, C.c_double, _VP, _VP, _VP, _DP]),
     "dirac_profile": (C.c_int, [_VP, C.c_int]),
     "dirac_profile_read": (C.c_int, [_VP, _DP, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "dirac_observables_static": (C.c_int, [_VP, _VP, _DP, C.c_int]),
@@ -135,6 +138,14 @@ def _ptr(t):
     import torch
     if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex128):
         raise ValueError("expected a contiguous complex128 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ptr32(t):
+    """Device pointer of a contiguous complex64 CUDA tensor."""
+    import torch
+    if not (t.is_cuda and t.is_contiguous() and t.dtype == torch.complex64):
+        raise ValueError("expected a contiguous complex64 CUDA tensor")
     return C.c_void_p(t.data_ptr())
 
 
@@ -282,6 +293,20 @@ class Operator:
 
     def apply(self, sign, t, x, y):
         _check(lib().dirac_apply(self._h, int(sign), float(t), _ptr(x), _ptr(y)), "dirac_apply")
+
+    def apply32(self, sign, t, x, y):
+        """dirac_apply32: the inner solve's complex64 operator (x, y complex64 CUDA tensors)."""
+        _check(lib().dirac_apply32(self._h, int(sign), float(t), _ptr32(x), _ptr32(y)), "dirac_apply32")
+
+    def precond32(self, r, z):
+        """dirac_precond_apply32: the inner solve's complex64 preconditioner (current schedule)."""
+        _check(lib().dirac_precond_apply32(self._h, _ptr32(r), _ptr32(z)), "dirac_precond_apply32")
+
+    def residual(self, t, psi, x, r):
+        """dirac_residual: r = A_-(t) psi - A_+(t) x as the step computes it; returns ||A_- psi||."""
+        bn = C.c_double(0)
+        _check(lib().dirac_residual(self._h, float(t), _ptr(psi), _ptr(x), _ptr(r), C.byref(bn)), "dirac_residual")
+        return bn.value
 
     def apply_assembled(self, sign, x, y):
         _check(lib().dirac_apply_assembled(self._h, int(sign), _ptr(x), _ptr(y)), "dirac_apply_assembled")

@@ -1029,6 +1029,12 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         if (!ts && mixed) ts = tune_precond(op, op->k32);
         if (ts) { dirac_op_free(op); return ts; }
     }
+    {
+        // the device address of dirac_observables_static's scratch, looked up here so that call
+        // does no set-up; a failure is reported by that call (it retries), not by the setup
+        double2* scratch = nullptr;
+        if (obs_scratch_address(op->device, &scratch) != DIRAC_OK) cudaGetLastError();
+    }
     *out = op;
 #undef TRY
     return DIRAC_OK;
@@ -1062,6 +1068,66 @@ extern "C" dirac_status dirac_precond_apply(dirac_op* op, const void* r_dev, voi
     if (!op || !r_dev || !z_dev || r_dev == z_dev) { set_error("dirac_precond_apply: bad argument"); return DIRAC_E_ARG; }
     k_precond_launch(op, op->k64, 0, nullptr, r_dev, nullptr, nullptr, z_dev, nullptr);
     return check_launch("dirac_precond_apply");
+}
+
+extern "C" dirac_status dirac_apply32(dirac_op* op, int sign, double t, const void* x_dev, void* y_dev)
+{
+    if (!op || !x_dev || !y_dev || x_dev == y_dev || (sign != 1 && sign != -1)) {
+        set_error("dirac_apply32: bad argument");
+        return DIRAC_E_ARG;
+    }
+    if (op->opts.precision == 0 || !op->k32.ks) {
+        set_error("dirac_apply32: the complex64 operator exists in precision 1 and 2 only");
+        return DIRAC_E_ARG;
+    }
+    k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, t);
+    op->launches++;
+    launch_assemble(op);
+    k_apply_launch(op, op->k32, sign, x_dev, y_dev, nullptr, nullptr, nullptr, nullptr, nullptr);
+    dirac_status e = check_launch("dirac_apply32");
+    if (e) return e;
+    return check_dev_err(op, "dirac_apply32");
+}
+
+extern "C" dirac_status dirac_precond_apply32(dirac_op* op, const void* r_dev, void* z_dev)
+{
+    if (!op || !r_dev || !z_dev || r_dev == z_dev) { set_error("dirac_precond_apply32: bad argument"); return DIRAC_E_ARG; }
+    if (op->opts.precision == 0 || !op->k32.ks) {
+        set_error("dirac_precond_apply32: the complex64 preconditioner exists in precision 1 and 2 only");
+        return DIRAC_E_ARG;
+    }
+    k_precond_launch(op, op->k32, 0, nullptr, r_dev, nullptr, nullptr, z_dev, nullptr);
+    return check_launch("dirac_precond_apply32");
+}
+
+extern "C" dirac_status dirac_residual(dirac_op* op, double t, const void* psi_dev, const void* x_dev, void* r_dev,
+                                       double* bnorm)
+{
+    if (!op || !psi_dev || !x_dev || !r_dev || r_dev == psi_dev || r_dev == x_dev) {
+        set_error("dirac_residual: bad argument");
+        return DIRAC_E_ARG;
+    }
+    Krylov& K = op->k64;
+    k_set_time<<<1, 1, 0, op->st>>>(op->t_eval, t);
+    op->launches++;
+    launch_assemble(op);
+    vcopy(op, K, x_dev, K.x);
+    // b = A_- psi and ||b||^2 (precision 2 forms both inside the residual pass), then r = b - A_+ x
+    if (op->opts.precision == 0) {
+        apply_accurate(op, -1, psi_dev, K.b, nullptr, op->part_n);
+        finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
+    } else {
+        rhs_accurate(op, psi_dev);
+    }
+    residual_accurate(op, psi_dev);
+    vcopy(op, K, K.r, r_dev);
+    dirac_status e = check_launch("dirac_residual");
+    if (e) return e;
+    KState hs;
+    e = read_state(op, K, hs);
+    if (e) return e;
+    if (bnorm) *bnorm = std::sqrt(hs.bnorm2);
+    return check_dev_err(op, "dirac_residual");
 }
 
 extern "C" dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched)
@@ -1360,24 +1426,27 @@ extern "C" dirac_status dirac_observables(dirac_op* op, const void* psi_dev, dou
 // ---------------------------------------------------------------------------------------------
 // Observables with library-static scratch (no allocation in the call).
 //
-// Some callers cannot allocate GPU memory when they need the observables: code that runs while a
-// stream is being captured into a CUDA graph (an allocation there is either forbidden or breaks
-// the capture), real-time or monitoring threads that must not hit the implicit device
-// synchronisation of cudaMalloc/cudaFree, and hosts that fix the process's device footprint
-// after setup.  dirac_observables_static serves them: its block partials and the final sums live
-// in the file-scope array below, which every GPU that loads the library holds until the process
-// exits.  No cudaMalloc, cudaFree or other allocating routine is called, on the device or the host.
+// Some callers cannot allocate GPU memory when they need the observables: real-time or monitoring
+// threads that must not hit the implicit device synchronisation of cudaMalloc/cudaFree, and hosts
+// that fix the process's device footprint after setup.  dirac_observables_static serves them: its
+// block partials and the final sums live in the file-scope array below, which the driver places
+// in device memory when it loads this module on a device (at the module's first use there, e.g. in
+// dirac_operator_setup) and which that GPU holds until the process exits.  The call itself calls no
+// cudaMalloc, cudaFree or other allocating routine, on the device or the host.
 // ---------------------------------------------------------------------------------------------
 static __device__ __align__(256) double2 g_obs_scratch[2 * DIRAC_STATIC_MAX_PARTIALS + 2];
 
 namespace dg {
 
-// device address of g_obs_scratch, looked up once per device (host code must not use the symbol
-// itself as a device address)
+// device address of g_obs_scratch, looked up once per device with that device current (host code
+// must not use the symbol itself as a device address: in host code it names a host-side stand-in).
+// dirac_operator_setup looks it up, so the observables call does no set-up of its own.  The address
+// is kept for the life of the process; after a cudaDeviceReset the module is loaded again, possibly
+// elsewhere, so the library must not be used across a device reset.
 static std::mutex g_obs_mutex;
 static void* g_obs_addr[64] = {nullptr};
 
-static dirac_status obs_scratch_address(int device, double2** out)
+dirac_status obs_scratch_address(int device, double2** out)
 {
     if (device < 0 || device >= 64) { set_error("dirac_observables_static: device index beyond 63"); return DIRAC_E_ARG; }
     std::lock_guard<std::mutex> lock(g_obs_mutex);

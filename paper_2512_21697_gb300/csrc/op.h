@@ -157,6 +157,7 @@ dirac_status bound_population(dirac_op* op, const double2* psi, double* out);
 dirac_status eig_window(dirac_op* op, double vl, double vu, std::vector<double>& hvec, std::vector<double>& hE,
                         std::vector<int>& hstart);
 void spec_free(dirac_op* op);
+dirac_status obs_scratch_address(int device, double2** out);   // static scratch of dirac_observables_static
 dirac_status guess_buffers(dirac_op* op);
 dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, const double2* h2, const double2* h3,
                         double t_start, int step, double2* x, const int* gate, cudaStream_t st,

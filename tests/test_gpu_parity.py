@@ -11,6 +11,15 @@ Tolerances (double precision everywhere):
    random-state step checks solve to 1e-13 (the physical-state full run uses the workload's 1e-12).
 """
 STEP_TOL = 1e-13
+# Mixed-precision steps (refinement passes and inner iterations).  From psi_n as the guess, a random
+# state's first residual is O(||b||); each inner complex64 solve reduces it by tol_inner = 1e-5 (the
+# FP32 operator's own error, ~1e-6 relative, is below that), so STEP_TOL = 1e-13 needs
+# ceil(13 / 5) = 3 inner solves and 4 accurate residual passes per step, the bound asserted.  A
+# wrong inner operator (relative error e) reduces the residual by about max(e, tol_inner) per pass
+# instead, so an error above ~1e-5 needs a fifth pass and fails.  The inner iterations are bounded by
+# twice the oracle's own preconditioned BiCGSTAB count to 1e-14 (14 decades against the inner
+# solves' 15) plus 8.
+MAX_PASSES_PER_STEP = 4
 import math
 
 import numpy as np
@@ -19,6 +28,25 @@ import pytest
 from paper_2512_21697_gb300 import binding as B, layout, workloads as W
 
 pytestmark = pytest.mark.gpu
+
+
+def refinement_counts(op, fn):
+    """Run fn() with the op's phase counters on; returns the accurate residual passes (timed launch
+    groups of the 'apply' phase: in precision 1 one more per step forms b = A_- psi)."""
+    op.profile(True)
+    fn()
+    _, cnt, _ = op.profile_read()
+    op.profile(False)
+    return int(cnt["apply"])
+
+
+def check_refinement(op, precision, nsteps, passes, its, oracle_its):
+    rhs = nsteps if precision == 1 else 0
+    per_step = (passes - rhs) / nsteps
+    assert per_step <= MAX_PASSES_PER_STEP, (passes, nsteps)
+    for k, (a, b) in enumerate(zip(its, oracle_its)):
+        assert a <= 2 * b + 8, ("inner iterations", k, a, b)
+    return per_step
 
 
 class Case:
@@ -109,12 +137,18 @@ def test_mixed_step_each_precond_schedule(oracle_mod, name, sched):
     psi0 = c.random(21)
     t0 = 0.5 * c.T()
     psid = c.to_dev(psi0)
-    its, res, _ = c.op.step(psid, 2, t0)
+    out = {}
+    passes = refinement_counts(c.op, lambda: out.update(r=c.op.step(psid, 2, t0)))
+    its, res, _ = out["r"]
     ref = psi0.copy()
+    oits = []
     for s in range(2):
-        ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        ref, it, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        oits.append(it)
     assert np.all(res <= STEP_TOL)
     assert np.linalg.norm(c.from_dev(psid) - ref) <= 1e-10 * np.linalg.norm(ref)
+    pps = check_refinement(c.op, 2, 2, passes, its, oits)
+    print("mixed %s sched %d: passes/step %.1f, inner %s, oracle %s" % (name, sched, pps, list(its), oits))
     if sched in (2, 3):
         c2 = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
         c2.op.set_schedule(True, 1)
@@ -213,13 +247,19 @@ def test_mixed_precision_step_matches_oracle(oracle_mod, name):
     t0 = 0.5 * c.T()
     n = 3
     psid = c.to_dev(psi0)
-    its, res, _ = c.op.step(psid, n, t0)
+    out = {}
+    passes = refinement_counts(c.op, lambda: out.update(r=c.op.step(psid, n, t0)))
+    its, res, _ = out["r"]
     ref = psi0.copy()
+    oits = []
     for s in range(n):
-        ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        ref, it, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        oits.append(it)
     got = c.from_dev(psid)
     assert np.all(res <= STEP_TOL)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    pps = check_refinement(c.op, 1, n, passes, its, oits)
+    print("precision 1 %s: passes/step %.1f, inner %s, oracle %s" % (name, pps, list(its), oits))
 
 
 @pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail", "wide_l", "order5"])
@@ -247,13 +287,19 @@ def test_double_float_step_matches_oracle(oracle_mod, name):
     t0 = 0.5 * c.T()
     n = 3
     psid = c.to_dev(psi0)
-    its, res, _ = c.op.step(psid, n, t0)
+    out = {}
+    passes = refinement_counts(c.op, lambda: out.update(r=c.op.step(psid, n, t0)))
+    its, res, _ = out["r"]
     ref = psi0.copy()
+    oits = []
     for s in range(n):
-        ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        ref, it, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        oits.append(it)
     got = c.from_dev(psid)
     assert np.all(res <= STEP_TOL)
     assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    pps = check_refinement(c.op, 2, n, passes, its, oits)
+    print("precision 2 %s: passes/step %.1f, inner %s, oracle %s" % (name, pps, list(its), oits))
 
 
 @pytest.mark.parametrize("name", ["small", "tail"])
@@ -315,12 +361,18 @@ def test_factorised_inner_apply_step_matches_oracle(oracle_mod, name):
     t0 = 0.5 * c.T()
     psid = c.to_dev(psi0)
     hist = torch.zeros(2 * c.bas.n, dtype=torch.complex128, device="cuda")
-    its, res, _ = c.op.step(psid, 2, t0, hist=hist, n_hist=0)
+    out = {}
+    passes = refinement_counts(c.op, lambda: out.update(r=c.op.step(psid, 2, t0, hist=hist, n_hist=0)))
+    its, res, _ = out["r"]
     ref = psi0.copy()
+    oits = []
     for s in range(2):
-        ref, _, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        ref, it, _ = c.orc.step(ref, t0 + s * cfg["dt"], tol=1e-14)
+        oits.append(it)
     assert np.all(res <= STEP_TOL)
     assert np.linalg.norm(c.from_dev(psid) - ref) <= 1e-10 * np.linalg.norm(ref)
+    pps = check_refinement(c.op, 2, 2, passes, its, oits)
+    print("factorised %s: passes/step %.1f, inner %s, oracle %s" % (name, pps, list(its), oits))
     c2 = Case(cfg, oracle_mod, tol=STEP_TOL, max_iter=1000, precision=2, tol_inner=1e-5, max_outer=30)
     c2.op.set_factorised(True)
     pd2 = c2.to_dev(psi0)
