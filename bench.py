@@ -50,6 +50,13 @@ def parse():
                     help="also time the photoelectron spectrum dP/dE of the final state (window (0, 2] a.u.)")
     ap.add_argument("--overlap", action="store_true",
                     help="precision 2: assemble the next step during the current solve (same arithmetic)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="time the headline on the host-driven loop (dirac_step) instead of the graph driver")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the comparison legs (peak-field window, precision 1, learned guess, batch)")
+    ap.add_argument("--no-batch-leg", action="store_true", help="skip the batch leg of the comparison")
+    ap.add_argument("--train-n", type=int, default=12, help="training trajectories of the learned guess")
+    ap.add_argument("--train-steps", type=int, default=10, help="steps per training trajectory")
     return ap.parse_args()
 
 
@@ -229,27 +236,77 @@ def replica_rate(steps, ms, world):
     return sps, sps * world
 
 
-def fp64_compare(bas, cfg, psi0_h, t0, args, stream, dev):
-    """Plain FP64 BiCGSTAB on the same steps from the same state, to the same tolerance."""
+def window_run(B, torch, bas, cfg, psi0_h, t0, warmup, steps, stream, dev, precision, guess=1, net=None,
+               host_loop=False):
+    """W warm-up steps (they fill the history and capture the graph) then K timed steps from psi0 at
+    t0, on the graph driver (dirac_run) or the host loop (dirac_step); CUDA events on the op's stream.
+    Returns (stats, final state, op)."""
     import numpy as np
-    import torch
-    from paper_2512_21697_gb300 import binding as B
-    op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=0, max_iter=1000)
+    op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=precision, max_iter=1000, tol_inner=1e-5,
+                    max_outer=20, guess=guess)
+    if net is not None:
+        B.set_guess(op, net)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)
-        hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev)
-    _, _, nh = op.step(psi, args.warmup, t0, hist=hist, n_hist=0)
+        hist = torch.zeros((3 if guess == 2 else 2) * bas.n, dtype=torch.complex128, device=dev)
+    run = (lambda n, t, nh: op.step(psi, n, t, hist=hist, n_hist=nh)) if host_loop else \
+        (lambda n, t, nh: op.run(psi, n, t, hist, n_hist=nh))
+    _, _, nh = run(warmup, t0, 0)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    its, res, _ = op.step(psi, args.steps, t0 + args.warmup * cfg["dt"], hist=hist, n_hist=nh)
+    its, res, nh = run(steps, t0 + warmup * cfg["dt"], nh)
     ev1.record(stream)
     torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    out = {"value": args.steps / (ms / 1000.0), "unit": "steps/s", "ms_per_step": ms / args.steps,
-           "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)), "dtype": "f64"}
-    del op
-    return out
+    out = {"value": steps / (ms / 1000.0), "unit": "steps/s", "ms_per_step": ms / steps,
+           "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)),
+           "dtype": ["f64", "c64+f64", "c64+df64"][precision], "driver": "dirac_step" if host_loop else "dirac_run"}
+    return out, psi, op
+
+
+def state_errors(obs_op, ref, psi, ref_obs=None):
+    """Per-result errors of a state against the plain FP64 state at the same time: wavefunction
+    relative L2, and the absolute differences of the norm, <H0>, ground and bound populations."""
+    import torch
+    o_ref = ref_obs if ref_obs is not None else obs_op.observables(ref, bound=True)
+    o = obs_op.observables(psi, bound=True)
+    out = {"psi_rel_l2": (torch.linalg.norm(psi - ref) / torch.linalg.norm(ref)).item()}
+    for k in ("norm", "energy", "p_ground", "p_bound"):
+        out[k] = abs(o[k] - o_ref[k])
+    return out, o_ref
+
+
+def train_guess(B, torch, bas, cfg, precision, n_train, train_steps, per_step=65536, iters=1500):
+    """Learned initial guess: trajectories of the method itself (extrapolated guess) for seeded pulses
+    at seeded times on the workload's basis give (features, target) samples, drawn with probability
+    proportional to s^2; the network is trained by the library's kernels.  Returns (net, note)."""
+    from paper_2512_21697_gb300 import learned as L, workloads as W
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    X, Tg = [], []
+    t_data = time.time()
+    for pc in L.pulse_variants(cfg, range(1000, 1000 + n_train)):
+        tr = L.Trajectory(bas, pc, train_steps, precision=precision, tol=cfg["tol"])
+        x, t, sc = L.samples(tr)
+        xs, ts = L.importance_subsample(x, t, sc, per_step * (train_steps - 4), g)
+        X.append(xs)
+        Tg.append(ts)
+        del tr, x, t, sc
+        torch.cuda.empty_cache()
+    X, Tg = torch.cat(X), torch.cat(Tg)
+    n_samples = int(X.shape[0])
+    t_data = time.time() - t_data
+    net = B.GuessNet(8192, W.guess_net_init(7))
+    t_train = time.time()
+    losses = L.train(net, X, Tg, iters, batch=8192, lr=1e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.time() - t_train
+    del X, Tg
+    note = ("%d seeded pulses (seeds 1000..%d) x %d steps (extrapolated guess), %d samples drawn with probability "
+            "proportional to s^2, %d Adam steps of 8192; data %.1f s, training %.1f s; loss %.3g -> %.3g" %
+            (n_train, 999 + n_train, train_steps, n_samples, iters, t_data, t_train, losses[0], losses[-1]))
+    return net, note
 
 
 def hbm_peak():
@@ -319,81 +376,35 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
-def learned_bench(args, world, rank, local, dist, n_train=12, train_steps=10, per_step=65536, iters=1500):
-    """Learned initial guess at the production size: trajectories of the method itself (extrapolated
-    guess) for seeded pulses on the production basis give (features, target) samples; the network
-    is trained with the library's kernels; then the same K steps at peak field are timed with the
-    extrapolated guess and with the learned one (both solve to the same tolerance)."""
-    import numpy as np
+def learned_bench(args, world, rank, local, dist):
+    """--learned: train the learned initial guess on trajectories of the workload's basis, then time
+    the same K steps at peak field (or --t0) with the extrapolated guess and with the learned one
+    (both on the graph driver, both solving to the same tolerance)."""
     import torch
-    from paper_2512_21697_gb300 import binding as B, learned as L, workloads as W
+    from paper_2512_21697_gb300 import binding as B, workloads as W
     dev = torch.device("cuda", local)
     cfg = dict(W.WORKLOADS[args.workload])
-    cfg["precision"] = args.precision
     bas = B.Basis(cfg)
-    npos = bas.nch * (cfg["N"] + 1)
-    g = torch.Generator(device=dev)
-    g.manual_seed(0)
-    X, Tg = [], []
-    t_data = time.time()
-    for pc in L.pulse_variants(cfg, range(1000, 1000 + n_train)):
-        tr = L.Trajectory(bas, pc, train_steps, precision=args.precision, tol=cfg["tol"])
-        x, t, sc = L.samples(tr)
-        xs, ts = L.importance_subsample(x, t, sc, per_step * (train_steps - 4), g)
-        X.append(xs)
-        Tg.append(ts)
-        del tr, x, t, sc
-        torch.cuda.empty_cache()
-    X, Tg = torch.cat(X), torch.cat(Tg)
-    n_samples = int(X.shape[0])
-    t_data = time.time() - t_data
-    net = B.GuessNet(8192, W.guess_net_init(7))
-    t_train = time.time()
-    losses = L.train(net, X, Tg, iters, batch=8192, lr=1e-3, seed=1)
-    torch.cuda.synchronize()
-    t_train = time.time() - t_train
-    del X, Tg
+    net, note = train_guess(B, torch, bas, cfg, args.precision, args.train_n, args.train_steps)
     T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
     t0 = args.t0 if args.t0 is not None else 0.5 * T
     psi0, _ = bas.initial_state()
     res = {}
     for guess in (1, 2):
         stream = torch.cuda.Stream()
-        op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=args.precision, max_iter=1000,
-                        tol_inner=1e-5, max_outer=20, guess=guess)
-        if guess == 2:
-            B.set_guess(op, net)
-        with torch.cuda.stream(stream):
-            psi = torch.from_numpy(psi0).to(dev)
-            hist = torch.zeros(3 * bas.n, dtype=torch.complex128, device=dev)
-        _, _, nh = op.step(psi, args.warmup + 3, t0, hist=hist, n_hist=0)   # fills the history
-        tcur = t0 + (args.warmup + 3) * cfg["dt"]
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        op.profile(True)
         clocks = ClockSampler(local)
         clocks.start()
-        ev0.record(stream)
-        its, rr, _ = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        ck = clocks.stop()
-        phase_ms, phase_n, _ = op.profile_read()
-        op.profile(False)
-        ms = ev0.elapsed_time(ev1)
-        res[guess] = {"value": args.steps / (ms / 1000.0), "ms_per_step": ms / args.steps,
-                      "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(rr)),
-                      "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()}, "clocks": ck}
+        r, _, op = window_run(B, torch, bas, cfg, psi0, t0, args.warmup, args.steps, stream, dev, args.precision,
+                              guess=guess, net=net if guess == 2 else None, host_loop=args.host_loop)
+        r["clocks"] = clocks.stop()
+        res[guess] = r
         del op
-    line = {"metric": METRIC, "value": res[2]["value"], "unit": "steps/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": res[2]["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "c64+f64", "c64+df64"][args.precision],
-            "data": "synthetic",
+    line = {"metric": METRIC, "value": res[2]["value"] * world, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res[2]["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ["f64", "c64+f64", "c64+df64"][args.precision], "data": "synthetic",
             "config": {"workload": workload_desc(args.workload, cfg) + "; learned initial guess, start at t=%.2f" % t0,
-                       "training": "%d seeded pulses x %d steps (extrapolated guess), %d samples drawn with "
-                                   "probability proportional to s^2, %d Adam steps of "
-                                   "8192; data %.1f s, training %.1f s; loss %.3g -> %.3g" %
-                                   (n_train, train_steps, n_samples, iters, t_data, t_train, losses[0], losses[-1])},
+                       "training": note},
             "learned": res[2], "extrapolated": res[1], "speedup_vs_extrapolated": res[2]["value"] / res[1]["value"],
             "clocks": res[2]["clocks"]}
     if rank == 0:
@@ -432,24 +443,22 @@ def _batch_time(B, torch, ops, used, dev, args, t0s, window, hist_len):
     return time.perf_counter() - w0, its, res
 
 
-def batch_bench(args, world, rank, local, dist):
+def batch_measure(args, world, local, n_req, learned, peak, fp64=True):
     """Batched workload: independent instances (own pulse and radial size) stepped concurrently by
     dirac_solve_batch with the window and preconditioner schedule picked by dirac_batch_tune.
-    Value: instance-steps per second of the mixed-precision batch (with --learned: with the learned
-    guess, trained first on trajectories of the batch's own instances, and the instances start at
-    their peak field).  Beside it, unless --no-fp64-compare: the same instances in plain FP64."""
+    Returns ({"mixed", "mixed_learned", "fp64": instance-steps/s ...}, config, clocks).  With
+    learned, the network is trained first on trajectories of the batch's own instances; with peak,
+    the instances start at their peak field."""
     import concurrent.futures as cf
-    import math
     import numpy as np
     import torch
     from paper_2512_21697_gb300 import binding as B, learned as L, workloads as W
     dev = torch.device("cuda", local)
-    cfgs = W.batch_instances(args.batch_n, seed0=0)
+    cfgs = W.batch_instances(n_req, seed0=0)
+    t_setup = time.time()
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         bases = list(ex.map(B.Basis, cfgs))
-    peak = args.learned or args.t0 is not None
-    t_setup = time.time()
-    ops, used = _batch_ops(B, torch, cfgs, bases, dev, args.precision, 2 if args.learned else 1)
+    ops, used = _batch_ops(B, torch, cfgs, bases, dev, args.precision, 2 if learned else 1)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
     n_inst = len(ops)
@@ -469,7 +478,7 @@ def batch_bench(args, world, rank, local, dist):
     out["mixed"] = {"value": n_inst * args.steps / wall * world, "iters_per_step": float(np.mean(its)),
                     "max_resid": float(np.max(res))}
     train_note = None
-    if args.learned:
+    if learned:
         # training data: trajectories of the first instances at seeded times inside their pulses
         g = torch.Generator(device=dev)
         g.manual_seed(0)
@@ -500,7 +509,7 @@ def batch_bench(args, world, rank, local, dist):
                                 "max_resid": float(np.max(res_l))}
     del ops
     torch.cuda.empty_cache()
-    if not args.no_fp64_compare:
+    if fp64:
         ops64, used64 = _batch_ops(B, torch, [c for c, _ in used], [b for _, b in used], dev, 0, 1)
         n64 = len(ops64)
         t064 = t0s[:n64]
@@ -509,27 +518,39 @@ def batch_bench(args, world, rank, local, dist):
                        "iters_per_step": float(np.mean(its64)), "max_resid": float(np.max(res64))}
         del ops64
     head = out.get("mixed_learned", out["mixed"])
+    if "fp64" in out:
+        out["speedup_vs_fp64"] = head["value"] / out["fp64"]["value"]   # instance-steps/s against instance-steps/s
+    config = {"workload": "batch: %d instances (of %d requested), E0 log-uniform [0.02, 0.2], wavelength "
+                          "[400, 1600] nm, 2-6 cycles, N 400-1000, |kappa|<=20, l<=2, R=300, dt=0.005, "
+                          "tol=1e-10, start %s" % (n_inst, n_req, "at each instance's peak field"
+                                                   if peak else "at the pulse start"),
+              "instances": n_inst, "unknowns": int(sum(b.n for _, b in used)), "window": best,
+              "precond_schedule": "tuned (one lane per channel, or one warp per channel with rows fixed to lanes)",
+              "tune_ms": {"windows": cand, "lanes": tune_ms[0].tolist(), "warps": tune_ms[1].tolist()},
+              "setup_s": t_setup, "timing": "host wall clock around the batch call (many streams)",
+              "steps": args.steps, "warmup": args.warmup}
+    if train_note:
+        config["training"] = train_note
+    return out, config, ck
+
+
+def batch_bench(args, world, rank, local, dist):
+    """--workload batch: the batch measurement as the bench line (value: instance-steps/s of the
+    mixed-precision batch, with --learned of the mixed + learned one)."""
+    peak = args.learned or args.t0 is not None
+    out, config, ck = batch_measure(args, world, local, args.batch_n, args.learned, peak,
+                                    fp64=not args.no_fp64_compare)
+    head = out.get("mixed_learned", out["mixed"])
+    n_inst = config["instances"]
+    config["parallelism"] = "replicas x%d" % world
     line = {
         "metric": METRIC, "value": head["value"], "unit": "instance-steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": n_inst * 1000.0 / head["value"] * world, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": ["f64", "c64+f64", "c64+df64"][args.precision],
-        "data": "synthetic",
-        "config": {"workload": "batch: %d instances (of %d requested), E0 log-uniform [0.02, 0.2], wavelength "
-                               "[400, 1600] nm, 2-6 cycles, N 400-1000, |kappa|<=20, l<=2, R=300, dt=0.005, "
-                               "tol=1e-10, start %s" % (n_inst, args.batch_n, "at each instance's peak field"
-                                                        if peak else "at the pulse start"),
-                   "unknowns": int(sum(b.n for _, b in used)), "window": best,
-                   "precond_schedule": "tuned (one lane per channel, or one warp per channel with rows fixed to lanes)",
-                   "tune_ms": {"windows": cand, "lanes": tune_ms[0].tolist(), "warps": tune_ms[1].tolist()},
-                   "setup_s": t_setup, "timing": "host wall clock around the batch call (many streams)",
-                   "parallelism": "replicas x%d" % world},
-        "batch": out,
-        "clocks": ck,
+        "data": "synthetic", "config": config, "batch": out, "clocks": ck,
     }
-    if train_note:
-        line["config"]["training"] = train_note
-    if "fp64" in out:
-        line["speedup_vs_fp64"] = head["value"] / out["fp64"]["value"]   # instance-steps/s against instance-steps/s
+    if "speedup_vs_fp64" in out:
+        line["speedup_vs_fp64"] = out["speedup_vs_fp64"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -592,6 +613,9 @@ def main():
     cfg = dict(W.WORKLOADS[args.workload])
     T = cfg["n_cycles"] * 2 * math.pi / cfg["omega"]
     t0 = args.t0 if args.t0 is not None else 0.0
+    dt = cfg["dt"]
+    dev = torch.device("cuda", local)
+    t_wall0 = time.time()
 
     bas = B.Basis(cfg)
     psi0_h, e0 = bas.initial_state()
@@ -602,63 +626,76 @@ def main():
         op.set_overlap(True)   # next step's assembly overlaps the current solve (same arithmetic)
     if args.precision == 2 and args.factorised:
         op.set_factorised(True)
-    dev = torch.device("cuda", local)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)
         hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev)
-    nh = 0
-    tcur = t0
-    # warm-up steps
-    _, _, nh = op.step(psi, args.warmup, tcur, hist=hist, n_hist=nh)
-    tcur += args.warmup * cfg["dt"]
+    graph = not args.host_loop and not args.overlap   # the graph driver does not overlap the assembly
+    run = (lambda n, t, nh: op.run(psi, n, t, hist, n_hist=nh)) if graph else \
+        (lambda n, t, nh: op.step(psi, n, t, hist=hist, n_hist=nh))
+    # warm-up steps (the first one captures the graph)
+    _, _, nh = run(args.warmup, t0, 0)
+    tcur = t0 + args.warmup * dt
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    op.profile(True)
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     ev0.record(stream)
-    its, res, nh = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
+    its, res, nh = run(args.steps, tcur, nh)
     ev1.record(stream)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    phase_ms, phase_n, launches = op.profile_read()
-    op.profile(False)
-    tcur += args.steps * cfg["dt"]
+    tcur += args.steps * dt
     ms = max_over_ranks(ms, dist, dev)
     sps, value = replica_rate(args.steps, ms, world)
+    psi_head = psi.clone()          # the state after W + K steps from t0, for the per-result errors
 
-    # end to end through the C ABI with host buffers: H2D of the state, K steps, D2H of the result
+    # the same kernels on the host-driven loop with the library's phase timers (CUDA events on the
+    # op's stream around every launch group; event records are not allowed inside the graph's
+    # conditional bodies): per-phase times, the dominant kernel's launch time for the roofline, and
+    # the launch count per step
+    op.profile(True)
+    hl0, hl1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    hl0.record(stream)
+    its_h, res_h, nh = op.step(psi, args.steps, tcur, hist=hist, n_hist=nh)
+    hl1.record(stream)
+    torch.cuda.synchronize()
+    ms_host = hl0.elapsed_time(hl1)
+    phase_ms, phase_n, launches = op.profile_read()
+    op.profile(False)
+    tcur += args.steps * dt
+
+    # end to end through the C ABI with host buffers: per step, the state in from pinned host memory,
+    # one dirac_run (or dirac_step) call, the state back out
     psi_h = torch.from_numpy(psi0_h).pin_memory()
     out_h = torch.empty_like(psi_h).pin_memory()
     ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with torch.cuda.stream(stream):
         psi_e = torch.empty_like(psi)
-    e2e_steps = max(2, min(args.steps, 5))
-    with torch.cuda.stream(stream):
         hist_e = torch.zeros_like(hist)
-    nh_e = 0
-    te = tcur
+    e2e_steps = max(2, min(args.steps, 5))
+    st_e = {"nh": 0, "t": tcur}
 
     def e2e_step(first):
-        # one user call per step: the state goes in from pinned host memory, comes back out, and the
-        # solver's own history (device-resident between calls) feeds the extrapolated guess
-        nonlocal nh_e, te
         with torch.cuda.stream(stream):
             psi_e.copy_(psi_h if first else out_h, non_blocking=True)
-        _, _, nh_e = op.step(psi_e, 1, te, hist=hist_e, n_hist=nh_e)
+        if graph:
+            _, _, st_e["nh"] = op.run(psi_e, 1, st_e["t"], hist_e, n_hist=st_e["nh"])
+        else:
+            _, _, st_e["nh"] = op.step(psi_e, 1, st_e["t"], hist=hist_e, n_hist=st_e["nh"])
         with torch.cuda.stream(stream):
             out_h.copy_(psi_e, non_blocking=True)
-        te += cfg["dt"]
+        st_e["t"] += dt
 
-    for s in range(args.warmup):   # untimed, as for the device-resident value: fills the history
-        e2e_step(s == 0)
+    for s_ in range(args.warmup):   # untimed, as for the device-resident value: fills the history
+        e2e_step(s_ == 0)
     torch.cuda.synchronize()
     ee0.record(stream)
-    for s in range(e2e_steps):
+    for s_ in range(e2e_steps):
         e2e_step(False)
     ee1.record(stream)
     torch.cuda.synchronize()
@@ -670,6 +707,8 @@ def main():
         if r and r["bound"] == "hbm":
             r["peak_source"] = "%s copy bandwidth %.1f GB/s" % ("measured" if peak_src == "measured" else
                                                               "fallback", peak_bw)
+    roof["timing"] = ("phase events around the kernel's launches during %d host-loop steps run right after the "
+                      "headline's graph-driven steps (same kernels, same window)" % args.steps)
     coup = bas.npairs * (cfg["N"] + 1) * (2 * cfg["order"] - 1) * 4
     if rank != 0:
         if dist:
@@ -677,9 +716,7 @@ def main():
         return
     obs = op.observables(psi)
     spec = spectrum_measure(op, bas, psi) if args.spectrum else None
-    fp64 = None
-    if args.precision != 0 and not args.no_fp64_compare:
-        fp64 = fp64_compare(bas, cfg, psi0_h, t0, args, stream, dev)
+    del op
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -688,12 +725,20 @@ def main():
                    "pairs": bas.npairs, "t_start": t0,
                    "precision": ["fp64", "mixed: c64 BiCGSTAB in FP64 refinement",
                                  "mixed: c64 BiCGSTAB in double-float refinement"][args.precision],
+                   "driver": ("dirac_run: the time loop as one CUDA graph with conditional WHILE/IF nodes, one "
+                              "graph launch and one status read-back per call" if graph else
+                              "dirac_step: host-driven loop"),
                    "assembly": "overlapped with the previous step's solve" if (args.precision == 2 and
                                                                                args.overlap) else "in step",
                    "l2": "inputs larger than L2: %.1f GB of coupling values streamed per operator apply" %
                          (8 * coup / 1e9),
                    "parallelism": "replicas x%d (independent instances, no collective)" % world},
         "iters_per_step": float(np.mean(its)), "max_resid": float(np.max(res)),
+        "host_loop": {"value": args.steps / (ms_host / 1000.0), "ms_per_step": ms_host / args.steps,
+                      "iters_per_step": float(np.mean(its_h)), "max_resid": float(np.max(res_h)),
+                      "launches_per_step": launches / args.steps,
+                      "note": "dirac_step on the same op, the next K steps: the graph driver replaces these "
+                              "launches and the per-step status read-back by one graph launch per call"},
         "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
         "spmv_gbs": (roof32 or roof)["gbs"],
         "roofline": roof,
@@ -707,14 +752,75 @@ def main():
         line["spectrum"] = spec
     if roof32 and roof32 is not roof:
         line["roofline_spmv32"] = roof32
-    if fp64:
+    if args.precision != 0 and not args.no_fp64_compare:
+        # plain FP64 on the same window and driver: the baseline of speedup_vs_fp64, and the per-result
+        # errors of the mixed state against it (same start state, same W + K steps)
+        fp64, psi64, op64 = window_run(B, torch, bas, cfg, psi0_h, t0, args.warmup, args.steps, stream, dev, 0,
+                                       host_loop=not graph)
+        errs, o64 = state_errors(op64, psi64, psi_head)
+        fp64["errors_of_headline_vs_fp64"] = errs
         line["fp64_baseline"] = fp64
         line["speedup_vs_fp64"] = value / (fp64["value"] * world)
+        if not args.no_compare:
+            comp = {"pulse_start": {"t_start": t0, "fp64": fp64,
+                                    "precision2": {"value": value, "ms_per_step": ms / args.steps,
+                                                   "iters_per_step": float(np.mean(its)),
+                                                   "max_resid": float(np.max(res)), "errors_vs_fp64": errs}}}
+            # precision 1: the literal form (FP64 refinement residual) on the same window
+            p1, psi1, op1 = window_run(B, torch, bas, cfg, psi0_h, t0, args.warmup, args.steps, stream, dev, 1,
+                                       host_loop=not graph)
+            del op1
+            p1["errors_vs_fp64"], _ = state_errors(op64, psi64, psi1, ref_obs=o64)
+            p1["speedup_vs_fp64"] = p1["value"] / fp64["value"]
+            comp["pulse_start"]["precision1"] = p1
+            del psi1, psi64
+            # peak-field window: plain FP64, precision 1, precision 2, precision 2 + learned guess
+            tp = 0.5 * T
+            peak = {"t_start": tp}
+            f64p, r64, _op = window_run(B, torch, bas, cfg, psi0_h, tp, args.warmup, args.steps, stream, dev, 0,
+                                        host_loop=not graph)
+            del _op
+            peak["fp64"] = f64p
+            o64p = op64.observables(r64, bound=True)
+            for name, prec in (("precision1", 1), ("precision2", 2)):
+                r, pp, _op = window_run(B, torch, bas, cfg, psi0_h, tp, args.warmup, args.steps, stream, dev, prec,
+                                        host_loop=not graph)
+                del _op
+                r["errors_vs_fp64"], _ = state_errors(op64, r64, pp, ref_obs=o64p)
+                r["speedup_vs_fp64"] = r["value"] / f64p["value"]
+                peak[name] = r
+                del pp
+            try:
+                net, note = train_guess(B, torch, bas, cfg, 2, args.train_n, args.train_steps)
+                r, pp, _op = window_run(B, torch, bas, cfg, psi0_h, tp, args.warmup, args.steps, stream, dev, 2,
+                                        guess=2, net=net, host_loop=not graph)
+                del _op
+                r["errors_vs_fp64"], _ = state_errors(op64, r64, pp, ref_obs=o64p)
+                r["speedup_vs_fp64"] = r["value"] / f64p["value"]
+                r["training"] = note
+                peak["precision2_learned"] = r
+                del pp, net
+            except Exception as e:   # reported, never required
+                peak["precision2_learned"] = {"error": str(e)}
+            comp["peak_field"] = peak
+            del r64
+            if not args.no_batch_leg:
+                del op64
+                torch.cuda.empty_cache()
+                try:
+                    bout, bconf, bck = batch_measure(args, world, local, args.batch_n, True, True)
+                    comp["batch_peak_field"] = {"result": bout, "config": bconf, "clocks": bck}
+                except Exception as e:
+                    comp["batch_peak_field"] = {"error": str(e)}
+                op64 = None
+            line["compare"] = comp
+        del op64
     if world == 1 and not args.no_cpu_baseline:
         try:
             line["cpu_baseline"] = cpu_baseline(cfg, float(np.mean(its)), args.cpu_seconds)
         except Exception as e:  # the baseline is reported, never required
             line["cpu_baseline"] = {"error": str(e)}
+    line["bench_wall_s"] = time.time() - t_wall0
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
