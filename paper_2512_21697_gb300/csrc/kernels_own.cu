@@ -378,6 +378,10 @@ constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8;   // floats: hi and lo words,
 // at a block barrier for every pair.
 constexpr int NTHR_OWN = 2 * NT + 32;
 
+// NEED_B: the pass also forms the FP32 products of b = A_- psi (a step's first pass).  The flag is
+// read on the device (a captured graph replays one launch for every pass), so both instantiations
+// are launched and the one that does not match the flag returns at once.
+template <bool NEED_B>
 __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const float4* __restrict__ u,
                                                              const float2* __restrict__ psi32,
                                                              const float* __restrict__ Wh, const float* __restrict__ Wl,
@@ -385,6 +389,8 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                                                              float4* __restrict__ part_r, float4* __restrict__ part_b,
                                                              const int* need_b_flag, int* err)
 {
+    if ((*need_b_flag != 0) != NEED_B) return;   // uniform over the grid
+    constexpr bool need_b = NEED_B;
     // ring stage: hi words, lo words of the TR coupling rows, then u_b rows r0 - h .. r0 + TR + h
     extern __shared__ __align__(128) float wring[];
     __shared__ float4 us[2 * TR];                    // u_a rows: (type 0, type 1) split complex
@@ -393,7 +399,6 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
     __shared__ int64_t spair[NSTD];                  // pair and partner channel of each stage
     __shared__ int snbr[NSTD];
     __shared__ int fail, issued;
-    const bool need_b = *need_b_flag != 0;
     const int n1 = A.n1, ntile = gridDim.y;
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
     const int rows = min(TR, n1 - r0);
@@ -421,7 +426,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         bool in = tid < rows;
         us[2 * tid] = in ? ua[2 * (r0 + tid)] : z;
         us[2 * tid + 1] = in ? ua[2 * (r0 + tid) + 1] : z;
-        ps[tid] = in ? *reinterpret_cast<const float4*>(pa + 2 * (r0 + tid)) : z;
+        if (need_b) ps[tid] = in ? *reinterpret_cast<const float4*>(pa + 2 * (r0 + tid)) : z;
     }
     // window rows outside the radial grid are never copied: zero them once in both stages, so the
     // direct products need no range test (the stored coupling is zero at those band positions)
@@ -685,8 +690,10 @@ void launch_residual_owner_df(cudaStream_t st, const OpView& A, const float4* u,
                               const int* need_b, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_residual_own_df<<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b,
-                                                                    need_b, err);
+    k_residual_own_df<true><<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r,
+                                                                          part_b, need_b, err);
+    k_residual_own_df<false><<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r,
+                                                                           part_b, need_b, err);
 }
 
 void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
@@ -709,7 +716,10 @@ cudaError_t apply_own32_prepare()
     cudaError_t e =
         cudaFuncSetAttribute(k_apply_own32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_own32_smem());
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_residual_own_df, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_residual_own_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)residual_own_df_smem());
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_residual_own_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)residual_own_df_smem());
 }
 
