@@ -279,8 +279,12 @@ dirac_status dirac_guess_features(dirac_op* op, const void* const* states, doubl
  * psi_{n+1}; t_dev float[nch n1][4]. */
 dirac_status dirac_guess_targets(dirac_op* op, const void* const* states, const void* psi_next, const float* s_dev,
                                  float* t_dev);
-/* out_dev float[M][4] = net(x_dev[M][32]); tensor_cores != 0: bf16 tensor-core kernel, else the
- * FP32 kernels of training (batches of max_batch). */
+/* out_dev float[M][4] = net(x_dev[M][32]).  tensor_cores 1: the bf16 kernel on the fifth-generation
+ * tensor cores (tcgen05.mma, FP32 accumulators in tensor memory; the kernel the learned guess of a
+ * step uses; this call then synchronises the stream to read the error word of its bounded waits and
+ * returns DIRAC_E_CUDA if one ran out); 2: the bf16 warp-level mma.sync kernel (same arithmetic up
+ * to FP32 summation order); 0: the FP32 kernels of training (batches of max_batch).  Input and
+ * activations are rounded to bfloat16 on the tensor-core paths.  DIRAC_E_ARG for other values. */
 dirac_status dirac_guess_forward(dirac_guess* net, const float* x_dev, int64_t M, float* out_dev, int tensor_cores,
                                  void* stream);
 /* Mean squared error over B samples (0 < B <= max_batch) and, if grad_host != NULL, its gradient

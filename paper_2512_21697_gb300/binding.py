@@ -432,7 +432,10 @@ class GuessNet:
         return a
 
     def forward(self, x, out, tensor_cores=True, stream=None):
-        _check(lib().dirac_guess_forward(self._h, _fptr(x), x.shape[0], _fptr(out), int(bool(tensor_cores)),
+        """dirac_guess_forward: tensor_cores True or 1 = tcgen05 kernel, 2 = mma.sync kernel, False or
+        0 = the FP32 kernels."""
+        tc = int(tensor_cores) if not isinstance(tensor_cores, bool) else int(tensor_cores)
+        _check(lib().dirac_guess_forward(self._h, _fptr(x), x.shape[0], _fptr(out), tc,
                                          _VP(_stream_ptr(stream))), "dirac_guess_forward")
 
     def loss_grad(self, x, t, stream=None):

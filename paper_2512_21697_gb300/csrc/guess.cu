@@ -45,6 +45,8 @@ struct dirac_guess {
     float* w = nullptr;             // FP32 master parameters
     float* wr = nullptr;            // the same with weights rounded to bf16 (biases unchanged)
     __nv_bfloat16* wb = nullptr;    // bf16 weights for the tensor-core forward (W1 padded, W4 padded to 8)
+    __nv_bfloat16* wt = nullptr;    // the same, transposed and packed in the tcgen05 kernel's chunk layout
+    int* err = nullptr;             // error word of the tcgen05 forward's bounded waits
     float *m = nullptr, *v = nullptr, *g = nullptr;
     float *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *out = nullptr;   // training activations
     float *d1 = nullptr, *d2 = nullptr, *dout = nullptr;                 // back-propagated errors
@@ -668,14 +670,19 @@ extern "C" dirac_status dirac_guess_create(int max_batch, dirac_guess** out)
     };
     al(&g->w, GN_PARAMS); al(&g->wr, GN_PARAMS); al(&g->m, GN_PARAMS); al(&g->v, GN_PARAMS); al(&g->g, GN_PARAMS);
     al(&g->wb, (size_t)GN_IN * GN_H + 2 * GN_H * GN_H + GN_H * 8);
+    al(&g->wt, (size_t)guess_tc05_packed());
+    al(&g->err, 1);
     al(&g->a1, act); al(&g->a2, act); al(&g->a3, act); al(&g->d1, act); al(&g->d2, act);
     al(&g->out, (size_t)max_batch * GN_OUT); al(&g->dout, (size_t)max_batch * GN_OUT);
     al(&g->part, (size_t)nc * GN_H * GN_H); al(&g->lpart, (size_t)nc + 1);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&g->hloss, sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(g->wb, 0, sizeof(__nv_bfloat16) * ((size_t)GN_IN * GN_H + 2 * GN_H * GN_H + GN_H * 8));
+    if (e == cudaSuccess) e = cudaMemset(g->wt, 0, sizeof(__nv_bfloat16) * (size_t)guess_tc05_packed());
+    if (e == cudaSuccess) e = cudaMemset(g->err, 0, sizeof(int));
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_guess_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)guess_forward_tc_smem());
+    if (e == cudaSuccess) e = guess_tc05_prepare();
     if (e != cudaSuccess) {
         set_error(std::string("dirac_guess_create: ") + cudaGetErrorString(e));
         dirac_guess_free(g);
@@ -689,7 +696,7 @@ extern "C" void dirac_guess_free(dirac_guess* g)
 {
     if (!g) return;
     cudaDeviceSynchronize();
-    for (void* p : {(void*)g->w, (void*)g->wr, (void*)g->wb, (void*)g->m, (void*)g->v, (void*)g->g, (void*)g->a1,
+    for (void* p : {(void*)g->w, (void*)g->wr, (void*)g->wb, (void*)g->wt, (void*)g->err, (void*)g->m, (void*)g->v, (void*)g->g, (void*)g->a1,
                     (void*)g->a2, (void*)g->a3, (void*)g->out, (void*)g->d1, (void*)g->d2, (void*)g->dout,
                     (void*)g->part, (void*)g->lpart})
         cudaFree(p);
@@ -705,6 +712,7 @@ extern "C" dirac_status dirac_guess_set_params(dirac_guess* g, const float* host
     GTRY(cudaMemset(g->v, 0, sizeof(float) * GN_PARAMS), "dirac_guess_set_params");
     g->step = 0;
     k_round_params<<<(GN_PARAMS + 255) / 256, 256>>>(g->w, g->wr, g->wb);
+    launch_pack_tc05(nullptr, g->wb, g->wt);
     GTRY(cudaDeviceSynchronize(), "dirac_guess_set_params");
     return DIRAC_OK;
 }
@@ -752,10 +760,28 @@ extern "C" dirac_status dirac_guess_targets(dirac_op* op, const void* const* sta
 extern "C" dirac_status dirac_guess_forward(dirac_guess* g, const float* x_dev, int64_t M, float* out_dev,
                                             int tensor_cores, void* stream)
 {
-    if (!g || !x_dev || !out_dev || M < 0) { set_error("dirac_guess_forward: bad argument"); return DIRAC_E_ARG; }
+    if (!g || !x_dev || !out_dev || M < 0 || tensor_cores < 0 || tensor_cores > 2) {
+        set_error("dirac_guess_forward: bad argument");
+        return DIRAC_E_ARG;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     if (M == 0) return DIRAC_OK;
-    if (tensor_cores) {
+    if (tensor_cores == 1) {
+        launch_guess_forward_tc05(st, M, x_dev, g->wt, g->wr + GO_B1, g->wr + GO_B2, g->wr + GO_B3, g->wr + GO_B4,
+                                  out_dev, nullptr, g->err);
+        dirac_status e = check_launch("dirac_guess_forward");
+        if (e) return e;
+        int h = 0;
+        GTRY(cudaMemcpyAsync(&h, g->err, sizeof(int), cudaMemcpyDeviceToHost, st), "dirac_guess_forward");
+        GTRY(cudaStreamSynchronize(st), "dirac_guess_forward");
+        if (h) {
+            GTRY(cudaMemsetAsync(g->err, 0, sizeof(int), st), "dirac_guess_forward");
+            set_error("dirac_guess_forward: a bounded wait of the tcgen05 forward ran out of time (results invalid)");
+            return DIRAC_E_CUDA;
+        }
+        return DIRAC_OK;
+    }
+    if (tensor_cores == 2) {
         k_guess_forward_tc<<<(unsigned)((M + FT_M - 1) / FT_M), FT_THREADS, guess_forward_tc_smem(), st>>>(
             M, x_dev, g->wb, g->wr, out_dev, nullptr);
         return check_launch("dirac_guess_forward");
@@ -807,6 +833,7 @@ extern "C" dirac_status dirac_guess_train_step(dirac_guess* g, const float* x_de
     float c1 = (float)(1.0 - std::pow(0.9, (double)g->step)), c2 = (float)(1.0 - std::pow(0.999, (double)g->step));
     k_adam<<<(GN_PARAMS + 255) / 256, 256, 0, st>>>(GN_PARAMS, g->w, g->m, g->v, g->g, (float)lr, b1, b2, 1e-8f, c1, c2);
     k_round_params<<<(GN_PARAMS + 255) / 256, 256, 0, st>>>(g->w, g->wr, g->wb);
+    launch_pack_tc05(st, g->wb, g->wt);
     dirac_status e = check_launch("dirac_guess_train_step");
     if (e) return e;
     if (loss) {
@@ -845,8 +872,8 @@ dirac_status guess_into(dirac_op* op, const double2* p0, const double2* h1, cons
     }
     k_guess_features<<<(unsigned)((npos + GF_THREADS - 1) / GF_THREADS), GF_THREADS, 0, st>>>(
         op->ov.nch, op->ov.n1, op->ov.ch_kappa, op->ch_two_mu, p0, h1, h2, h3, field, op->gx, op->gs, gate);
-    k_guess_forward_tc<<<(unsigned)((npos + FT_M - 1) / FT_M), FT_THREADS, guess_forward_tc_smem(), st>>>(
-        npos, op->gx, g->wb, g->wr, op->gout, gate);
+    launch_guess_forward_tc05(st, npos, op->gx, g->wt, g->wr + GO_B1, g->wr + GO_B2, g->wr + GO_B3, g->wr + GO_B4,
+                              op->gout, gate, op->dev_err);
     k_guess_apply<<<nb, 256, 0, st>>>(npos, p0, h1, h2, op->gs, op->gout, x, gate);
     op->launches += 3;
     return check_launch("learned guess");

@@ -1,5 +1,6 @@
 // kernels.h -- kernel declarations and the block reduction helper shared by the .cu files.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "device.h"
@@ -149,6 +150,16 @@ int fact_tile();
 void launch_fact32(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc, const float2* G, int L,
                    const float* S, const float* H, int sign, const void* x, float2* Z, const float4* cab, void* y,
                    const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip);
+
+// learned-guess network forward on the fifth-generation tensor cores (tcgen05, TMEM accumulators)
+size_t guess_forward_tc05_smem();
+int64_t guess_tc05_packed();
+int guess_tc05_rows();
+cudaError_t guess_tc05_prepare();
+void launch_pack_tc05(cudaStream_t st, const __nv_bfloat16* wb, __nv_bfloat16* wt);
+void launch_guess_forward_tc05(cudaStream_t st, int64_t M, const float* X, const __nv_bfloat16* wt,
+                               const float* b1, const float* b2, const float* b3, const float* b4, float* out,
+                               const int* gate, int* err);
 
 // complex64 apply with each coupling block read once (owner pass + gather pass, bd = 13)
 size_t apply_own32_smem();

@@ -79,13 +79,35 @@ def test_forward_fp32_and_tensor_cores_match_oracle():
     net.forward(xd, out, tensor_cores=False)
     got = out.cpu().numpy()
     assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref)) + 1e-6
-    # tensor cores keep the input and the activations in bfloat16: compare with that rounding
+    # tensor cores keep the input and the activations in bfloat16: compare with that rounding; both
+    # tensor-core kernels (1: tcgen05 with TMEM accumulators, 2: warp-level mma.sync)
     ref_b, _ = G.forward(p, x.astype(np.float64), act_bf16=True)
-    net.forward(xd, out, tensor_cores=True)
+    for tc in (1, 2):
+        out.zero_()
+        net.forward(xd, out, tensor_cores=tc)
+        got = out.cpu().numpy()
+        assert np.max(np.abs(got - ref_b)) <= 5e-3 * np.sqrt(np.mean(ref_b ** 2)), tc
+        # and the bfloat16 activations cost little against full precision
+        assert np.sqrt(np.mean((got - ref) ** 2)) <= 3e-2 * np.sqrt(np.mean(ref ** 2)), tc
+
+
+@pytest.mark.parametrize("M", [1, 127, 128, 129, 5000])
+def test_tcgen05_forward_sizes(M):
+    # the tcgen05 kernel's 128-position tiles with a ragged last tile, a single partial tile and an
+    # exact multiple; rows past M are neither read nor written
+    import torch
+    net, p, x, _, _, _ = _net_and_batch(M, 5)
+    xd = torch.from_numpy(x).cuda()
+    out = torch.full((M + 1, 4), 7.0, dtype=torch.float32, device="cuda")
+    net.forward(xd, out[:M], tensor_cores=1)
     got = out.cpu().numpy()
-    assert np.max(np.abs(got - ref_b)) <= 5e-3 * np.sqrt(np.mean(ref_b ** 2))
-    # and the bfloat16 activations cost little against full precision
-    assert np.sqrt(np.mean((got - ref) ** 2)) <= 3e-2 * np.sqrt(np.mean(ref ** 2))
+    ref_b, _ = G.forward(p, x.astype(np.float64), act_bf16=True)
+    assert np.max(np.abs(got[:M] - ref_b)) <= 5e-3 * np.sqrt(np.mean(ref_b ** 2))
+    assert np.all(got[M] == 7.0)
+    out2 = torch.empty((M, 4), dtype=torch.float32, device="cuda")
+    net.forward(xd, out2, tensor_cores=2)
+    # the two tensor-core kernels differ only in FP32 summation order and tanh rounding
+    assert np.max(np.abs(got[:M] - out2.cpu().numpy())) <= 5e-3 * np.sqrt(np.mean(ref_b ** 2))
 
 
 def test_loss_and_gradient_match_oracle():
