@@ -86,6 +86,8 @@ def test_forward_fp32_and_tensor_cores_match_oracle():
         out.zero_()
         net.forward(xd, out, tensor_cores=tc)
         got = out.cpu().numpy()
+        print("tensor_cores=%d: max|out - ref_b| / rms(ref_b) = %.3g" %
+              (tc, np.max(np.abs(got - ref_b)) / np.sqrt(np.mean(ref_b ** 2))))
         assert np.max(np.abs(got - ref_b)) <= 5e-3 * np.sqrt(np.mean(ref_b ** 2)), tc
         # and the bfloat16 activations cost little against full precision
         assert np.sqrt(np.mean((got - ref) ** 2)) <= 3e-2 * np.sqrt(np.mean(ref ** 2)), tc
