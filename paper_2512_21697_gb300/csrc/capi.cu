@@ -237,7 +237,7 @@ void residual_accurate(dirac_op* op, const void* psi)
         // owner/gather form: each coupling block read once
         {
             PhaseScope ps(op, DIRAC_PHASE_APPLY, 4);   // split, owner (two specialisations), gather
-            k_split_uv3<<<op->nparts_vec, 256, 0, op->st>>>(op->n, (const double2*)psi, (const double2*)K.x,
+            k_split_uv3<<<op->nparts_vec, 256, 0, op->st>>>(op->n, op->ov.n1, (const double2*)psi, (const double2*)K.x,
                                                            op->xsplit, op->vsplit, op->psi32);
             {
                 PhaseScope po(op, DIRAC_PHASE_OWNER, 0);   // the owner pass alone, inside the apply phase

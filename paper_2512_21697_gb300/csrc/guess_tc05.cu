@@ -57,10 +57,7 @@ __device__ __forceinline__ void bar_init(uint64_t* b, uint32_t n)
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(n) : "memory");
 }
 
-// non-blocking test of a phase.  The waits below poll it: a try_wait with a suspend-time hint can
-// leave the thread asleep well past the phase's completion, which costs more than polling here.
-// non-blocking test of a phase; the waits below poll it (a try_wait with a suspend-time hint can
-// leave a thread asleep past the phase's completion)
+// non-blocking test of a phase; the waits below poll it
 __device__ __forceinline__ bool bar_test(uint64_t* b, uint32_t parity)
 {
     uint32_t ok;

@@ -76,7 +76,9 @@ void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float
 // (cA hi, cA lo, cB hi, cB lo) per pair
 void launch_assemble_grp_df(cudaStream_t st, const OpView& A, const AsmChunk* chunks, int nchunks, const int* gpair,
                             const float4* gcoef, const float2* G, float* Wh, float* Wl);
-__global__ void k_split_uv3(int64_t n, const double2* psi, const double2* x, float4* u, float4* v, float2* psi32);
+// type-major split vectors ([channel][DKB type][slot]) of the owner/gather residual passes
+__global__ void k_split_uv3(int64_t n, int n1, const double2* psi, const double2* x, float4* u, float4* v,
+                            float2* psi32);
 __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
                            float4* __restrict__ u, float4* __restrict__ v);
 void launch_residual_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,

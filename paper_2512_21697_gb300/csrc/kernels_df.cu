@@ -267,16 +267,22 @@ __global__ void k_split_uv(int64_t n, const double2* __restrict__ psi, const dou
     v[i] = make_float4(c.x, c.y, d.x, d.y);
 }
 
-// u = psi + x, v = psi - x (split) and psi rounded to FP32
-__global__ void k_split_uv3(int64_t n, const double2* __restrict__ psi, const double2* __restrict__ x,
+// u = psi + x, v = psi - x (split) and psi rounded to FP32.  u and v are stored type-major within
+// each channel, [channel][DKB type][radial slot] (n1 = slots per channel), so that each type's rows
+// are 16 B apart: the owner pass copies a type's window as one contiguous range and its threads
+// read consecutive rows without shared-memory bank conflicts.  psi32 keeps the state's order.
+__global__ void k_split_uv3(int64_t n, int n1, const double2* __restrict__ psi, const double2* __restrict__ x,
                             float4* __restrict__ u, float4* __restrict__ v, float2* __restrict__ psi32)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 p = psi[i], q = x[i];
     float2 a = df_split(p.x + q.x), b = df_split(p.y + q.y), c = df_split(p.x - q.x), d = df_split(p.y - q.y);
-    u[i] = make_float4(a.x, a.y, b.x, b.y);
-    v[i] = make_float4(c.x, c.y, d.x, d.y);
+    const int64_t ch = i / (2 * n1);
+    const int rem = (int)(i - ch * 2 * n1), r = rem >> 1, t = rem & 1;
+    const int64_t o = (ch * 2 + t) * n1 + r;
+    u[o] = make_float4(a.x, a.y, b.x, b.y);
+    v[o] = make_float4(c.x, c.y, d.x, d.y);
     psi32[i] = make_float2((float)p.x, (float)p.y);
 }
 

@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(NT) k_apply_gather32(OpView A, int sign, float
 
 // ---------------------------------------------------------------------------------------------
 // Refinement residual r = A_- psi - A_+ x = S (psi - x) - i tau H0 (psi + x) + (W - W^T)(psi + x)
-// in double-float, from u = psi + x and v = psi - x split into (re hi, re lo, im hi, im lo), and,
+// in double-float, from u = psi + x and v = psi - x split into (re hi, re lo, im hi, im lo) and stored
+// type-major ([channel][DKB type][slot], so a type's rows are contiguous 16 B records), and,
 // when *need_b is set (the first pass of a step), b = A_- psi in FP32 products for the tolerance
 // scale ||b||.  Owner pass: the direct coupling sums W_ab u_b of channel a to r_out (W_ab psi_b to
 // b_out); partials of the transposed products to part_r (the unnormalised double-float accumulators
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
     constexpr bool need_b = NEED_B;
     // ring stage: hi words, lo words of the TR coupling rows, then u_b rows r0 - h .. r0 + TR + h
     extern __shared__ __align__(128) float wring[];
-    __shared__ float4 us[2 * TR];                    // u_a rows: (type 0, type 1) split complex
+    __shared__ float4 us0[TR], us1[TR];              // u_a rows of DKB type 0 and 1 (split complex)
     __shared__ float4 ps[TR];                        // psi_a rows in FP32: (p0.re, p0.im, p1.re, p1.im)
     __shared__ uint64_t full[NSTD], empty[NSTD];
     __shared__ int64_t spair[NSTD];                  // pair and partner channel of each stage
@@ -408,8 +409,9 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
     const int stage_f = STAGE_DF;
     // u_b window: rows [lo, hi) land at window index lo - (r0 - h)
     const int lo = max(0, r0 - HO), hi = min(n1, r0 + TR + HO);
-    const uint32_t ubytes = (uint32_t)(hi - lo) * 32;
-    const int uoff = (lo - (r0 - HO)) * 8;   // floats
+    // u is type-major ([channel][type][slot]): a type's window is one contiguous copy of 16 B rows
+    const uint32_t ubytes = (uint32_t)(hi - lo) * 16;
+    const int uoff = (lo - (r0 - HO)) * 4;   // floats
     if (tid == 0) {
         for (int q = 0; q < NSTD; q++) {
             mbar_init(&full[q], 1);
@@ -419,13 +421,14 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         issued = 0;
         mbar_fence_init();
     }
-    const float4* ua = u + (int64_t)ch * 2 * n1;
+    const float4* ua0 = u + (int64_t)ch * 2 * n1;   // type 0 rows of channel ch, then type 1
+    const float4* ua1 = ua0 + n1;
     const float2* pa = psi32 + (int64_t)ch * 2 * n1;
     if (tid < TR) {
         float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         bool in = tid < rows;
-        us[2 * tid] = in ? ua[2 * (r0 + tid)] : z;
-        us[2 * tid + 1] = in ? ua[2 * (r0 + tid) + 1] : z;
+        us0[tid] = in ? ua0[r0 + tid] : z;
+        us1[tid] = in ? ua1[r0 + tid] : z;
         if (need_b) ps[tid] = in ? *reinterpret_cast<const float4*>(pa + 2 * (r0 + tid)) : z;
     }
     // window rows outside the radial grid are never copied: zero them once in both stages, so the
@@ -436,9 +439,9 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
         for (int i = tid; i < NSTD * NOUT; i += NTHR_OWN) {
             int sg = i / NOUT, w = i - sg * NOUT;
             if (w < wlo || w >= whi) {
-                float4* Uz = reinterpret_cast<float4*>(wring + sg * stage_f + 2 * TR * ROWF);
-                Uz[2 * w] = z;
-                Uz[2 * w + 1] = z;
+                float4* Uz = reinterpret_cast<float4*>(wring + sg * stage_f + 2 * TR * ROWF);   // [type][window]
+                Uz[w] = z;
+                Uz[NOUT + w] = z;
             }
         }
     }
@@ -466,12 +469,13 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 snbr[s] = nb;
                 // debug builds: copy from the buffers' starts instead of past their ends
                 const int64_t pw = DG_INB(A, (p * n1 + r0 + rows) * ROWF <= A.nb_coup, 0) ? p : 0;
-                const int nbw = DG_INB(A, ((int64_t)nb * n1 + hi) * 2 <= (int64_t)A.nch * n1 * 2, 1) ? nb : 0;
+                const int nbw = DG_INB(A, ((int64_t)nb * 2 + 1) * n1 + hi <= (int64_t)A.nch * n1 * 2, 1) ? nb : 0;
                 fence_proxy_async();
-                mbar_expect_tx(&full[s], 2 * bytes + ubytes);
+                mbar_expect_tx(&full[s], 2 * bytes + 2 * ubytes);
                 bulk_load(st, Wh + (pw * n1 + r0) * ROWF, bytes, &full[s]);
                 bulk_load(st + TR * ROWF, Wl + (pw * n1 + r0) * ROWF, bytes, &full[s]);
-                bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nbw * n1 + lo) * 2, ubytes, &full[s]);
+                bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nbw * 2) * n1 + lo, ubytes, &full[s]);
+                bulk_load(st + 2 * TR * ROWF + NOUT * 4 + uoff, u + ((int64_t)nbw * 2 + 1) * n1 + lo, ubytes, &full[s]);
                 issued = k + 1;
             }
         }
@@ -481,7 +485,8 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
             if (!mbar_wait(&full[s], (uint32_t)((k / NSTD) & 1))) { fail = 1; break; }
             const float* Hs = wring + s * stage_f;
             const float* Ls = Hs + TR * ROWF;
-            const float4* Us = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window][2]
+            const float4* Us0 = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window], type 0
+            const float4* Us1 = Us0 + NOUT;                                             // type 1
             if (((k + grp) & 1) == 0) {
                 if (direct_row) {
                     const float2* pb = psi32 + (int64_t)snbr[s] * 2 * n1;
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                     for (int d = 0; d < BDO; d++) {
                         // window index of row rr = r + d - h: rr - (r0 - h) = lt + d; rows outside the
                         // grid are zero in the window and in W
-                        float4 x0 = Us[2 * (lt + d)], x1 = Us[2 * (lt + d) + 1];
+                        float4 x0 = Us0[lt + d], x1 = Us1[lt + d];
                         float4 wh = *reinterpret_cast<const float4*>(Hs + lt * ROWF + d * 4);
                         float4 wl = *reinterpret_cast<const float4*>(Ls + lt * ROWF + d * 4);
                         // W[t][u] = (w.x, w.y ; w.z, w.w)
@@ -524,7 +529,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                     const int lr = j - d;
                     float4 wh = *reinterpret_cast<const float4*>(Hs + lr * ROWF + d * 4);
                     float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
-                    float4 x0 = us[2 * lr], x1 = us[2 * lr + 1];
+                    float4 x0 = us0[lr], x1 = us1[lr];
                     // (W^T)[t][u] = W[u][t]
                     df_fma(tt[0], wh.x, wl.x, x0.x, x0.y); df_fma(tt[0], wh.z, wl.z, x1.x, x1.y);
                     df_fma(tt[1], wh.x, wl.x, x0.z, x0.w); df_fma(tt[1], wh.z, wl.z, x1.z, x1.w);
@@ -604,7 +609,7 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
     if (tid < TR && r < n1) {
         int64_t o = (int64_t)ch * 2 * n1 + 2 * r;
         // diagonal block: S (psi - x) - i tau H0 (psi + x), and b's FP32 part (S - i tau H0) psi
-        const float4* ua = u + (int64_t)ch * 2 * n1;
+        const float4* ua = u + (int64_t)ch * 2 * n1;   // type-major: type 0 rows, then type 1 rows
         const float4* va = v + (int64_t)ch * 2 * n1;
         const float2* pa = psi32 + (int64_t)ch * 2 * n1;
         int ks = A.ch_kslot[ch];
@@ -617,7 +622,7 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
         for (int d = 0; d < BDO; d++) {
             int rr = r + d - HO;
             if (rr < 0 || rr >= n1) continue;
-            float4 u0 = ua[2 * rr], u1 = ua[2 * rr + 1], v0 = va[2 * rr], v1 = va[2 * rr + 1];
+            float4 u0 = ua[rr], u1 = ua[n1 + rr], v0 = va[rr], v1 = va[n1 + rr];
             float4 pv = need_b ? *reinterpret_cast<const float4*>(pa + 2 * rr) : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int t = 0; t < 2; t++) {
                 float2 s0 = Sk[d * 4 + 2 * t], s1 = Sk[d * 4 + 2 * t + 1];
