@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-batch-leg", action="store_true", help="skip the batch leg of the comparison")
     ap.add_argument("--train-n", type=int, default=12, help="training trajectories of the learned guess")
     ap.add_argument("--train-steps", type=int, default=10, help="steps per training trajectory")
+    ap.add_argument("--guess-forward", type=int, default=0, metavar="M",
+                    help="time only the learned-guess network forward on M seeded random positions (tcgen05 "
+                         "kernel against the mma.sync kernel) and print one JSON line")
     return ap.parse_args()
 
 
@@ -140,11 +143,11 @@ FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x
 # on the medium workload (6944 pairs x 601 radial slots), scaled to the production launch by the
 # units processed (pairs x slots: x 9.817); the summaries under profiles/ give the commands and the
 # raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
-TRAFFIC_MEDIUM = {"df": (1.762372e9 + 0.155071e9, "profiles/k_residual_own_df_medium.md"),
-                  "df_owner": (1.762372e9 + 0.155071e9, "profiles/k_residual_own_df_medium.md"),
+TRAFFIC_MEDIUM = {"df": (1.758447e9 + 0.155287e9, "profiles/k_residual_own_df_medium.md"),
+                  "df_owner": (1.758447e9 + 0.155287e9, "profiles/k_residual_own_df_medium.md"),
                   "f32": (0.886455e9 + 0.075098e9, "profiles/k_apply_own32_medium.md")}
 MEDIUM_UNITS = 6944 * 601
-DF_OPS_PER_FMA = 12                 # FP32 operations of one double-float multiply-add (TwoProd + TwoSum)
+DF_OPS_PER_FMA = 10                 # FP32 operations of one double-float multiply-add (df64.cuh df_fma)
 
 
 def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
@@ -174,16 +177,20 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
                     "flops_per_apply": flops, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                     "frac": gbs / hbm_peak})
     elif kind == "df_owner":
-        # the owner pass alone: each stored value twice (W u_b, W^T u_a) on re and im
+        # the owner pass alone: it streams the hi and lo words of every stored coupling value once
+        # (HBM), and forms each value's two uses (W u_b, W^T u_a) on re and im in double-float
+        # (FP32 issue); against the two peaks it sits closer to the HBM one, which is reported as
+        # the bound, with the FP32-issue view beside it
         dfma = 4 * coup
         ops = dfma * DF_OPS_PER_FMA
         tops = ops / t / 1e12
         peak = FP32_LANE_OPS / 1e3
         out.update({"kernel": "k_residual_own_df (double-float refinement residual, owner pass)",
-                    "df_fma_per_apply": dfma, "ops_per_apply": ops, "bound": "alu", "achieved": tops, "peak": peak,
-                    "unit": "T FP32-lane-ops/s", "frac": tops / peak,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (1 op per lane per clock); "
-                                   "12 ops per double-float multiply-add"})
+                    "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                    "alu_view": {"df_fma_per_apply": dfma, "ops_per_apply": ops, "achieved": tops, "peak": peak,
+                                 "unit": "T FP32-lane-ops/s", "frac": tops / peak,
+                                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (1 op per lane per "
+                                                "clock); 10 FP32 ops per double-float multiply-add"}})
     else:
         # double-float multiply-adds: each stored value twice (W u_b, W^T u_a) on re and im, the
         # diagonal blocks S and tau H0 on both u and v (4 per entry and channel)
@@ -196,7 +203,7 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
                               "residual)", "df_fma_per_apply": dfma, "ops_per_apply": ops, "bound": "alu",
                     "achieved": tops, "peak": peak, "unit": "T FP32-lane-ops/s", "frac": tops / peak,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (1 op per lane per clock); "
-                                   "12 ops per double-float multiply-add"})
+                                   "10 ops per double-float multiply-add"})
     return out
 
 
@@ -374,6 +381,41 @@ def reference_arm(args):
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "steps/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def guess_forward_bench(args, reps=20):
+    """The network forward alone (dirac_guess_forward) on M seeded random feature rows with the
+    workload module's seeded initial weights: the tcgen05 kernel (tensor_cores=1) and the warp-level
+    mma.sync kernel (tensor_cores=2), CUDA events around `reps` launches each, after a warm-up."""
+    import torch
+    from paper_2512_21697_gb300 import binding as B, workloads as W
+    M = args.guess_forward
+    net = B.GuessNet(8192, W.guess_net_init(7))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn((M, 32), generator=g, device="cuda", dtype=torch.float32)
+    out = torch.empty((M, 4), device="cuda", dtype=torch.float32)
+    flop = 2.0 * M * (32 * 256 + 2 * 256 * 256 + 256 * 4)
+    peak = 1906.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except Exception:
+        pass
+    res = {}
+    for tc in (1, 2):
+        net.forward(x, out, tensor_cores=tc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.forward(x, out, tensor_cores=tc)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[["", "tcgen05", "mma_sync"][tc]] = {"ms": ms, "tflops": flop / ms / 1e9, "frac_bf16_peak": flop / ms / 1e9 / peak}
+    print(json.dumps({"guess_forward": {"positions": M, "flop_per_forward": flop, "bf16_peak_tflops": peak, **res}}),
+          flush=True)
 
 
 def learned_bench(args, world, rank, local, dist):
@@ -604,6 +646,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.guess_forward:
+        if rank == 0:
+            guess_forward_bench(args)
+        return
     if args.workload == "batch":
         batch_bench(args, world, rank, local, dist)
         return

@@ -369,7 +369,10 @@ __global__ void __launch_bounds__(NT) k_apply_gather32(OpView A, int sign, float
 // ---------------------------------------------------------------------------------------------
 namespace {
 constexpr int NSTD = 2;          // ring depth of the double-float pass
-constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8;   // floats: hi and lo words, u_b row window
+// floats per stage: hi and lo words of the TR coupling rows, the u_b row window (type 0, type 1) and,
+// on a step's first pass, the FP32 psi_b row window (both types per 16-byte row)
+constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8 + NOUT * 4;
+constexpr int PS_OFF = 2 * TR * ROWF + NOUT * 8;      // psi_b window offset in a stage (floats)
 }
 
 // Warp roles: two groups of four consumer warps alternate the direct products (row r0 + lt) and the
@@ -397,8 +400,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
     __shared__ float4 us0[TR], us1[TR];              // u_a rows of DKB type 0 and 1 (split complex)
     __shared__ float4 ps[TR];                        // psi_a rows in FP32: (p0.re, p0.im, p1.re, p1.im)
     __shared__ uint64_t full[NSTD], empty[NSTD];
-    __shared__ int64_t spair[NSTD];                  // pair and partner channel of each stage
-    __shared__ int snbr[NSTD];
+    __shared__ int64_t spair[NSTD];                  // pair of each stage
     __shared__ int fail, issued;
     const int n1 = A.n1, ntile = gridDim.y;
     const int ch = blockIdx.x, tile = blockIdx.y, r0 = tile * TR;
@@ -442,6 +444,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 float4* Uz = reinterpret_cast<float4*>(wring + sg * stage_f + 2 * TR * ROWF);   // [type][window]
                 Uz[w] = z;
                 Uz[NOUT + w] = z;
+                Uz[2 * NOUT + w] = z;   // psi_b window
             }
         }
     }
@@ -466,16 +469,17 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 const int nb = A.own_nbr[own0 + k];
                 float* st = wring + s * stage_f;
                 spair[s] = p;   // published by the arrive below
-                snbr[s] = nb;
                 // debug builds: copy from the buffers' starts instead of past their ends
                 const int64_t pw = DG_INB(A, (p * n1 + r0 + rows) * ROWF <= A.nb_coup, 0) ? p : 0;
                 const int nbw = DG_INB(A, ((int64_t)nb * 2 + 1) * n1 + hi <= (int64_t)A.nch * n1 * 2, 1) ? nb : 0;
                 fence_proxy_async();
-                mbar_expect_tx(&full[s], 2 * bytes + 2 * ubytes);
+                mbar_expect_tx(&full[s], 2 * bytes + (need_b ? 3 : 2) * ubytes);
                 bulk_load(st, Wh + (pw * n1 + r0) * ROWF, bytes, &full[s]);
                 bulk_load(st + TR * ROWF, Wl + (pw * n1 + r0) * ROWF, bytes, &full[s]);
                 bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nbw * 2) * n1 + lo, ubytes, &full[s]);
                 bulk_load(st + 2 * TR * ROWF + NOUT * 4 + uoff, u + ((int64_t)nbw * 2 + 1) * n1 + lo, ubytes, &full[s]);
+                if (need_b)   // psi_b rows [lo, hi): 16 B each (both types), the state's own order
+                    bulk_load(st + PS_OFF + uoff, psi32 + ((int64_t)nbw * n1 + lo) * 2, ubytes, &full[s]);
                 issued = k + 1;
             }
         }
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
             const float4* Us1 = Us0 + NOUT;                                             // type 1
             if (((k + grp) & 1) == 0) {
                 if (direct_row) {
-                    const float2* pb = psi32 + (int64_t)snbr[s] * 2 * n1;
+                    const float4* Ps = reinterpret_cast<const float4*>(Hs + PS_OFF);   // psi_b window
 #pragma unroll
                     for (int d = 0; d < BDO; d++) {
                         // window index of row rr = r + d - h: rr - (r0 - h) = lt + d; rows outside the
@@ -502,9 +506,8 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                         df_fma(dd[1], wh.x, wl.x, x0.z, x0.w); df_fma(dd[1], wh.y, wl.y, x1.z, x1.w);
                         df_fma(dd[2], wh.z, wl.z, x0.x, x0.y); df_fma(dd[2], wh.w, wl.w, x1.x, x1.y);
                         df_fma(dd[3], wh.z, wl.z, x0.z, x0.w); df_fma(dd[3], wh.w, wl.w, x1.z, x1.w);
-                        const int rr = r + d - HO;
-                        if (need_b && rr >= 0 && rr < n1) {
-                            float4 q = *reinterpret_cast<const float4*>(pb + 2 * rr);
+                        if (need_b) {   // psi_b window rows outside the grid are zero, as u_b's
+                            float4 q = Ps[lt + d];
                             db[0] += wh.x * q.x + wh.y * q.z;
                             db[1] += wh.x * q.y + wh.y * q.w;
                             db[2] += wh.z * q.x + wh.w * q.z;
