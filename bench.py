@@ -143,8 +143,8 @@ FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x
 # on the medium workload (6944 pairs x 601 radial slots), scaled to the production launch by the
 # units processed (pairs x slots: x 9.817); the summaries under profiles/ give the commands and the
 # raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
-TRAFFIC_MEDIUM = {"df": (1.758447e9 + 0.155287e9, "profiles/k_residual_own_df_medium.md"),
-                  "df_owner": (1.758447e9 + 0.155287e9, "profiles/k_residual_own_df_medium.md"),
+TRAFFIC_MEDIUM = {"df": (1.758372e9 + 0.155325e9, "profiles/k_residual_own_df_medium.md"),
+                  "df_owner": (1.758372e9 + 0.155325e9, "profiles/k_residual_own_df_medium.md"),
                   "f32": (0.886455e9 + 0.075098e9, "profiles/k_apply_own32_medium.md")}
 MEDIUM_UNITS = 6944 * 601
 DF_OPS_PER_FMA = 10                 # FP32 operations of one double-float multiply-add (df64.cuh df_fma)
