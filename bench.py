@@ -143,18 +143,23 @@ FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x
 # on the medium workload (6944 pairs x 601 radial slots), scaled to the production launch by the
 # units processed (pairs x slots: x 9.817); the summaries under profiles/ give the commands and the
 # raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
-TRAFFIC_MEDIUM = {"df": (1.758372e9 + 0.155325e9, "profiles/k_residual_own_df_medium.md"),
-                  "df_owner": (1.758372e9 + 0.155325e9, "profiles/k_residual_own_df_medium.md"),
+TRAFFIC_MEDIUM = {"df": (1.768965e9 + 0.155458e9, "profiles/k_residual_own_df_medium.md"),
+                  "df_owner": (1.768965e9 + 0.155458e9, "profiles/k_residual_own_df_medium.md"),
                   "f32": (0.886455e9 + 0.075098e9, "profiles/k_apply_own32_medium.md")}
 MEDIUM_UNITS = 6944 * 601
 DF_OPS_PER_FMA = 10                 # FP32 operations of one double-float multiply-add (df64.cuh df_fma)
+DF_OPS_PER_FMA_OFF = 6              # ... in the fixed-binade form (df_fma_off), tolerances >= 1e-11
+OFFSET_TOL = 1e-11                  # the library picks the fixed-binade form at tolerances >= this
 
 
 def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
     """Roofline of one operator-apply launch group, timed live by the library's event timers.
 
     kind 'f64': FP64 apply (FP64 ALU bound), 'f32': complex64 owner/gather apply (HBM bound),
-    'df': double-float refinement residual pass (FP32 ALU/issue bound), 'df_owner': its owner pass."""
+    'df': double-float refinement residual pass (FP32 ALU/issue bound), 'df_owner': its owner pass.
+    The owner pass's coupling products take DF_OPS_PER_FMA_OFF operations at tolerances >= 1e-11
+    (the library's automatic choice), DF_OPS_PER_FMA below; the gather's diagonal blocks always ten."""
+    cops = DF_OPS_PER_FMA_OFF if cfg["tol"] >= OFFSET_TOL else DF_OPS_PER_FMA
     coup, flops, bytes_ = operator_counts(bas, cfg, "df" if kind == "df_owner" else kind)
     t = ms / cnt / 1000.0
     gbs = bytes_ / t / 1e9
@@ -182,7 +187,7 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
         # (FP32 issue); against the two peaks it sits closer to the HBM one, which is reported as
         # the bound, with the FP32-issue view beside it
         dfma = 4 * coup
-        ops = dfma * DF_OPS_PER_FMA
+        ops = dfma * cops
         tops = ops / t / 1e12
         peak = FP32_LANE_OPS / 1e3
         out.update({"kernel": "k_residual_own_df (double-float refinement residual, owner pass)",
@@ -190,20 +195,22 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
                     "alu_view": {"df_fma_per_apply": dfma, "ops_per_apply": ops, "achieved": tops, "peak": peak,
                                  "unit": "T FP32-lane-ops/s", "frac": tops / peak,
                                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (1 op per lane per "
-                                                "clock); 10 FP32 ops per double-float multiply-add"}})
+                                                "clock); %d FP32 ops per double-float multiply-add (%s)" %
+                                                (cops, "fixed-binade accumulators" if cops == DF_OPS_PER_FMA_OFF
+                                                 else "Dot2 accumulators")}})
     else:
         # double-float multiply-adds: each stored value twice (W u_b, W^T u_a) on re and im, the
         # diagonal blocks S and tau H0 on both u and v (4 per entry and channel)
         n1, bd = cfg["N"] + 1, 2 * cfg["order"] - 1
         dfma = 4 * coup + 4 * bas.nch * n1 * bd * 4
-        ops = dfma * DF_OPS_PER_FMA
+        ops = 4 * coup * cops + 4 * bas.nch * n1 * bd * 4 * DF_OPS_PER_FMA
         tops = ops / t / 1e12
         peak = FP32_LANE_OPS / 1e3
         out.update({"kernel": "k_split_uv3 + k_residual_own_df + k_residual_gather_df (double-float refinement "
                               "residual)", "df_fma_per_apply": dfma, "ops_per_apply": ops, "bound": "alu",
                     "achieved": tops, "peak": peak, "unit": "T FP32-lane-ops/s", "frac": tops / peak,
                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (1 op per lane per clock); "
-                                   "10 ops per double-float multiply-add"})
+                                   "%d ops per coupling multiply-add, 10 per diagonal-block one" % cops})
     return out
 
 

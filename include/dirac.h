@@ -310,6 +310,17 @@ dirac_status dirac_op_set_guess(dirac_op* op, dirac_guess* net);
  * and a stream.  dirac_run and dirac_solve_batch do not overlap.  DIRAC_E_ARG if precision != 2. */
 dirac_status dirac_op_set_overlap(dirac_op* op, int enable);
 
+/* Accumulation of the double-float refinement residual's coupling sums (precision 2, order-7
+ * splines; Eq. solPsi's r = A_- psi - A_+ x): mode 1 the Dot2 form (ten FP32 operations per
+ * double-float multiply-add, error of order 2^-48 times each running sum); mode 2 the fixed-binade
+ * form (six operations: every accumulator starts from an offset 1.5 * 2^k with 2^(k-2) at least a
+ * bound of its sum of |products|, formed each pass from the coupling's static envelopes, the
+ * pulse factors and the current vectors; error of order 2^-48 times the offset, so about
+ * 1e-13 ||b|| on strong-field random states); mode 0 (the default) takes mode 2 when the solver
+ * tolerance is at least 1e-11 and mode 1 below.  Both end on the same accurate residual test.
+ * DIRAC_E_ARG for other modes. */
+dirac_status dirac_op_set_residual_mode(dirac_op* op, int mode);
+
 /* Preconditioner schedule of the complex128 (complex64 = 0) or complex64 (complex64 = 1) solve:
  * 0 one lane per channel (complex64 only; the channels of one kappa share the factor rows),
  * 1 one warp per channel, 2 one warp per channel with the vector and the factor rows staged

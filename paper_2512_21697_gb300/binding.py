@@ -85,6 +85,7 @@ SIGNATURES = {
     "dirac_guess_train_step": (C.c_int, [_VP, _VP, _VP, C.c_int, C.c_double, _DP, _VP]),
     "dirac_op_set_guess": (C.c_int, [_VP, _VP]),
     "dirac_op_set_overlap": (C.c_int, [_VP, C.c_int]),
+    "dirac_op_set_residual_mode": (C.c_int, [_VP, C.c_int]),
     "dirac_op_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
     "dirac_selftest_wait": (C.c_int, [_VP, C.c_double, C.POINTER(C.c_int)]),
     "dirac_bounds_word": (C.c_int, [_VP, C.POINTER(C.c_uint), C.POINTER(C.c_int)]),
@@ -287,6 +288,10 @@ class Operator:
     def set_overlap(self, enable=True):
         """dirac_op_set_overlap: assemble the next step's coupling values during the current solve."""
         _check(lib().dirac_op_set_overlap(self._h, int(bool(enable))), "dirac_op_set_overlap")
+
+    def set_residual_mode(self, mode):
+        """dirac_op_set_residual_mode: 0 automatic (by tolerance), 1 Dot2, 2 fixed-binade offsets."""
+        _check(lib().dirac_op_set_residual_mode(self._h, int(mode)), "dirac_op_set_residual_mode")
 
     def device_bytes(self):
         return lib().dirac_op_device_bytes(self._h)

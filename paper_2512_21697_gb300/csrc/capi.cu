@@ -222,6 +222,13 @@ void rhs_accurate(dirac_op* op, const void* psi)
     finish(op, K.ks, 0, op->nparts_apply, nullptr, op->part_n, op->opts.max_iter);
 }
 
+// the owner pass's accumulators: fixed-binade form (offsets) or Dot2 (dirac_op_set_residual_mode)
+static bool residual_offsets(const dirac_op* op)
+{
+    if (!op->own_sig) return false;
+    return op->resid_mode == 2 || (op->resid_mode == 0 && op->opts.tol >= 1e-11);
+}
+
 // Refinement residual r = b - A_+ x, accurate to double precision, into k64.r, with the
 // convergence check on k64.ks.  Precision 2: r = S (psi - x) - i tau H0 (psi + x) + (W - W^T)(psi + x)
 // in one double-float pass, which also refreshes ||b||^2 = ||A_- psi||^2 (FP32 products).
@@ -236,13 +243,19 @@ void residual_accurate(dirac_op* op, const void* psi)
     if (op->part_rdf) {
         // owner/gather form: each coupling block read once
         {
-            PhaseScope ps(op, DIRAC_PHASE_APPLY, 4);   // split, owner (two specialisations), gather
+            const bool off = residual_offsets(op);
+            PhaseScope ps(op, DIRAC_PHASE_APPLY, off ? 6 : 4);   // split, [u sums, offsets,] owner (two), gather
             k_split_uv3<<<op->nparts_vec, 256, 0, op->st>>>(op->n, op->ov.n1, (const double2*)psi, (const double2*)K.x,
                                                            op->xsplit, op->vsplit, op->psi32);
+            if (off)
+                launch_residual_offsets(op->st, op->ov, op->asm_chunks, op->asm_nchunks, op->asm_gpair,
+                                        op->asm_gcoef, op->s, op->own_E, op->own_Ew, op->own_US, op->own_sig,
+                                        op->xsplit);
             {
                 PhaseScope po(op, DIRAC_PHASE_OWNER, 0);   // the owner pass alone, inside the apply phase
-                launch_residual_owner_df(op->st, op->ov, op->xsplit, op->psi32, op->Wh, op->Wl, (double2*)K.r,
-                                         op->b32, op->part_rdf, op->part_bdf, op->need_b, op->dev_err);
+                launch_residual_owner_df(op->st, op->ov, off, op->own_sig, op->xsplit, op->psi32, op->Wh, op->Wl,
+                                         (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b,
+                                         op->dev_err);
             }
             launch_residual_gather_df(op->st, op->ov, op->Sdf, op->Htdf, op->xsplit, op->vsplit, op->psi32,
                                       (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b, op->part_n,
@@ -953,6 +966,42 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
             if (dfloat) {
                 TRY(dev_alloc(op, &op->part_rdf, 2 * nslot));
                 TRY(dev_alloc(op, &op->part_bdf, nslot));
+                // envelopes for the owner pass's accumulator offsets (grouped assembly only):
+                // E[l][n][r] = the largest |M_lcn| entry (over c and the 2 x 2 block) of row r and of
+                // column r (rows rr with rr + d - h = r); Ew = its maximum over rows r - h .. r + h.
+                // Rounded up.
+                if (op->asm_chunks) {
+                    std::vector<float> hE((size_t)P.L * 4 * n1, 0.f), hEw(hE.size(), 0.f);
+                    for (int l = 0; l < P.L; l++)
+                        for (int nn = 0; nn < 4; nn++) {
+                            std::vector<double> env(n1, 0.0);
+                            for (int cc = 0; cc < 3; cc++) {
+                                const double* g = hM.data() + ((size_t)(l * 3 + cc) * 4 + nn) * be;
+                                for (int r = 0; r < n1; r++)
+                                    for (int d = 0; d < bd; d++) {
+                                        double m = 0;
+                                        for (int e = 0; e < 4; e++)
+                                            m = std::max(m, std::fabs(g[((size_t)r * bd + d) * 4 + e]));
+                                        env[r] = std::max(env[r], m);
+                                        int rr = r + d - half;
+                                        if (rr >= 0 && rr < n1) env[rr] = std::max(env[rr], m);
+                                    }
+                            }
+                            float* Er = hE.data() + ((size_t)l * 4 + nn) * n1;
+                            float* Ewr = hEw.data() + ((size_t)l * 4 + nn) * n1;
+                            for (int r = 0; r < n1; r++) Er[r] = (float)(env[r] * (1.0 + 1e-6));
+                            for (int r = 0; r < n1; r++) {
+                                float m = 0.f;
+                                for (int rr = std::max(0, r - half); rr <= std::min(n1 - 1, r + half); rr++)
+                                    m = std::max(m, Er[rr]);
+                                Ewr[r] = m;
+                            }
+                        }
+                    TRY(upload(op, &op->own_E, hE));
+                    TRY(upload(op, &op->own_Ew, hEw));
+                    TRY(dev_alloc(op, &op->own_US, (size_t)B.nch * n1));
+                    TRY(dev_alloc(op, &op->own_sig, (size_t)op->npairs * ntile * residual_sig_bytes()));
+                }
                 TRY(dev_alloc(op, &op->psi32, (size_t)op->n));
                 TRY(dev_alloc(op, &op->b32, (size_t)op->n));
                 TRY(dev_alloc(op, &op->need_b, 1));
@@ -1193,6 +1242,19 @@ static void select_set(dirac_op* op, int c)
     op->k32.W = a.Wh;
     op->acur = c;
     op->config_gen++;   // captured graphs hold the old pointers
+}
+
+extern "C" dirac_status dirac_op_set_residual_mode(dirac_op* op, int mode)
+{
+    if (!op || mode < 0 || mode > 2) {
+        set_error("dirac_op_set_residual_mode: bad argument (mode 0, 1 or 2)");
+        return DIRAC_E_ARG;
+    }
+    if (mode != op->resid_mode) {
+        op->resid_mode = mode;
+        op->config_gen++;   // captured graphs hold the other launch sequence
+    }
+    return DIRAC_OK;
 }
 
 extern "C" dirac_status dirac_op_set_overlap(dirac_op* op, int enable)

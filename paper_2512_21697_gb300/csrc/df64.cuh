@@ -46,6 +46,45 @@ __device__ __forceinline__ void df_fma(DfAcc& a, float wh, float wl, float xh, f
     a.c = c + (ar + br);
 }
 
+// a += (wh + wl) (xh + xl) in six FP32 operations, for an accumulator whose float part a.s holds a
+// fixed offset sigma = 1.5 * 2^k plus the running sum of the rounded products, where the caller
+// guarantees sum |wh xh| <= 2^(k-2) over everything the accumulator will take.  Then a.s stays in
+// [1.25, 1.75] * 2^k, one binade with the fixed unit 2^(k-23): t = fl(a.s + wh xh) (one FMA) and
+// d = t - a.s are exact (Sterbenz: both in the binade), and the part of the product that did not
+// fit the grid, wh xh - d (|.| <= 2^(k-24)), is formed by a second FMA with one rounding of
+// relative size 2^-24.  That residue and the cross terms wh xl, wl xh go into a.c.  This is
+// Dekker's Fast2Sum, whose condition |a.s| >= |wh xh| the offset makes hold for every term, with
+// the summand taken straight from the FMA (the offset is the error-free extraction idea of Rump,
+// Ogita and Oishi, "Accurate floating-point summation part I", SIAM J. Sci. Comput. 31 (2008)).
+// The value is (a.s - sigma) + a.c, a.s - sigma exact.  Error for m terms: m 2^-48 2^k from the
+// residues plus the roundings of a.c (|a.c| <= m 2^(k-24) + the cross terms), at most about
+// 3 m^2 2^-48 2^k: the Dot2 form of df_fma (m^2 u^2 sum |p|, u = 2^-24) with 2^k <= 8 times the
+// caller's bound in place of sum |p|, for six operations instead of ten.
+__device__ __forceinline__ void df_fma_off(DfAcc& a, float wh, float wl, float xh, float xl)
+{
+    float t = fmaf(wh, xh, a.s);
+    float d = t - a.s;
+    float e = fmaf(wh, xh, -d);
+    float c = a.c + e;
+    c = fmaf(wh, xl, c);
+    a.c = fmaf(wl, xh, c);
+    a.s = t;
+}
+
+// the offset sigma = 1.5 * 2^k of df_fma_off from its biased exponent byte (k + 127)
+__device__ __forceinline__ float df_offset(unsigned int eb) { return __int_as_float((int)((eb << 23) | 0x400000u)); }
+
+// biased exponent byte of the offset for a bound B >= sum |wh xh| (B >= 0): the least k with
+// 2^(k-2) >= 1.0625 B (the factor covers the bound's own FP32 roundings).  B below 1e-30, zero or
+// not a number gives a tiny normal offset (the products are then zero).
+__device__ __forceinline__ unsigned int df_offset_byte(float B)
+{
+    float bm = B * 1.0625f;
+    if (!(bm >= 1e-30f)) bm = 1e-30f;
+    unsigned int eb = ((unsigned int)__float_as_int(bm) >> 23) & 0xffu;   // bm < 2^(eb - 126)
+    return eb + 3u > 254u ? 254u : eb + 3u;
+}
+
 // a = (wh + wl) (xh + xl): the first product of a sum (TwoSum with an empty accumulator returns
 // the product itself)
 __device__ __forceinline__ void df_mul(DfAcc& a, float wh, float wl, float xh, float xl)

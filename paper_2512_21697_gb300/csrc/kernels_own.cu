@@ -373,6 +373,125 @@ constexpr int NSTD = 2;          // ring depth of the double-float pass
 // on a step's first pass, the FP32 psi_b row window (both types per 16-byte row)
 constexpr int STAGE_DF = 2 * TR * ROWF + NOUT * 8 + NOUT * 4;
 constexpr int PS_OFF = 2 * TR * ROWF + NOUT * 8;      // psi_b window offset in a stage (floats)
+// offset bytes of one (pair, tile): direct rows r0 + [0, TR) at [0, TR), transposed output rows
+// r0 - h + [0, NOUT) at [NOUT, 2 NOUT); the stage keeps them after its floats
+constexpr int SIG_BYTES = 2 * NOUT;
+constexpr int STAGE_DFS = STAGE_DF + SIG_BYTES / 4;   // floats per stage with the offset bytes
+}
+
+// Window sums of the split vector u = psi + x for the offsets of the owner pass:
+// US[ch][r] = sum over rows rr in [r - h, r + h] of max(|re hi|, |im hi|) over both DKB types of
+// u_ch(rr).  Every product of a row's direct sum (or of a transposed output row's sum) takes one u
+// factor from that window, so US bounds the u side of the sum of |products|.
+__global__ void __launch_bounds__(128) k_usum(OpView A, const float4* __restrict__ u, float* __restrict__ US)
+{
+    __shared__ float m[128 + 2 * HO];
+    const int n1 = A.n1, ch = blockIdx.y, r0 = blockIdx.x * 128;
+    const float4* u0 = u + (int64_t)ch * 2 * n1;   // type-major: type 0 rows, then type 1 rows
+    const float4* u1 = u0 + n1;
+    for (int i = threadIdx.x; i < 128 + 2 * HO; i += 128) {
+        const int rr = r0 - HO + i;
+        float v = 0.f;
+        if (rr >= 0 && rr < n1) {
+            const float4 a = u0[rr], b = u1[rr];
+            v = fmaxf(fmaxf(fabsf(a.x), fabsf(a.z)), fmaxf(fabsf(b.x), fabsf(b.z)));
+        }
+        m[i] = v;
+    }
+    __syncthreads();
+    const int r = r0 + threadIdx.x;
+    if (r < n1) {
+        float sum = 0.f;
+        for (int d = 0; d < BDO; d++) sum += m[threadIdx.x + d];
+        US[(int64_t)ch * n1 + r] = sum;
+    }
+}
+
+// Offsets of the owner pass's accumulators (df_fma_off): for every pair p and radial tile, one
+// byte per direct row r (the sum of W_p(r, .) u_b over the row's band) and per transposed output
+// row R (the sum of W_p(., .)^T u_a reaching R).  The bound of the sum of |products|:
+//  - W_p = sum over its multipoles l of cA_l K_l + cB_l KT_l (the grouped assembly's coefficients)
+//    with K_l = sum_n m_n G^n_l and G^n_l = sum_c s_lc(t) M_lcn (the static pulse matrices); so
+//    every entry of row r of W_p is at most Mb(r) = sum_l S_l (|cA_l| eA_l(r) + |cB_l| eB_l(r)),
+//    S_l = sum_c |s_lc(t)|, eA_l = sum_n |m_n| E_ln, eB_l = sum_n |m'_n| E_ln (m = (1, ka, kb, ka kb),
+//    m' = (1, kb, ka, ka kb): one pair group shares them) and E_ln(r) the largest |M_lcn| entry of
+//    row r and of column r over c (KT reads G at the transposed position, i.e. along column r);
+//  - a direct row takes two entries of each of its band positions, against u_b in [r - h, r + h]:
+//    B = 2 Mb(r) US_b(r); a transposed output row R takes two entries of rows R - h .. R + h against
+//    u_a on those rows: B = 2 max_{|lr - R| <= h} Mb(lr) US_a(R), the max taken from Ew, the
+//    13-row window maxima of E.
+// All factors are rounded up or carry the 1.0625 of df_offset_byte.  Grid: (tiles, chunks of the
+// grouped assembly); a block forms its rows' eA, eB once and then spends a few FMAs per pair.
+__global__ void __launch_bounds__(SIG_BYTES) k_own_sigma(OpView A, const AsmChunk* __restrict__ chunks, int nchunks,
+                                                          const int* __restrict__ gpair,
+                                                          const float4* __restrict__ gcoef,
+                                                          const double* __restrict__ s, const float* __restrict__ E,
+                                                          const float* __restrict__ Ew, const float* __restrict__ US,
+                                                          unsigned char* __restrict__ sig)
+{
+    __shared__ int sp[ASM_CHUNK], sa[ASM_CHUNK], sb[ASM_CHUNK];
+    __shared__ float2 scf[ASM_CHUNK * ASM_MAX_NL];   // (|cA_l| S_l, |cB_l| S_l)
+    const int n1 = A.n1, tile = blockIdx.x, ntile = gridDim.x, slot = threadIdx.x;
+    const bool direct = slot < TR;
+    const int row = direct ? tile * TR + slot : tile * TR - HO + (slot - NOUT);
+    const bool valid = (direct || slot >= NOUT) && row >= 0 && row < n1;
+    const float* Et = (direct ? E : Ew) + (valid ? row : 0);
+    for (int c = blockIdx.y; c < nchunks; c += gridDim.y) {
+        const AsmChunk ch = chunks[c];
+        __syncthreads();   // the previous chunk's staged values are no longer read
+        for (int i = slot; i < ch.count; i += blockDim.x) {
+            const int p = gpair[ch.first + i];
+            sp[i] = p;
+            sa[i] = A.pair_a[p];
+            sb[i] = A.pair_b[p];
+        }
+        for (int i = slot; i < ch.count * ASM_MAX_NL; i += blockDim.x) {
+            const int l = ch.l[i % ASM_MAX_NL];
+            const float S = (float)((fabs(s[3 * l]) + fabs(s[3 * l + 1]) + fabs(s[3 * l + 2])) * (1.0 + 1e-6));
+            const float4 cf = gcoef[(int64_t)ch.first * ASM_MAX_NL + i];   // (cA hi, lo, cB hi, lo)
+            scf[i] = make_float2(fabsf(cf.x) * S, fabsf(cf.z) * S);
+        }
+        __syncthreads();
+        const float fa = fabsf((float)ch.ka), fb = fabsf((float)ch.kb);
+        const float mk[4] = {1.f, fa, fb, fa * fb}, mt[4] = {1.f, fb, fa, fa * fb};
+        float eA[ASM_MAX_NL], eB[ASM_MAX_NL];
+#pragma unroll
+        for (int j = 0; j < ASM_MAX_NL; j++) {
+            eA[j] = 0.f;
+            eB[j] = 0.f;
+            if (valid && j < ch.nl) {
+                const float* El = Et + (int64_t)ch.l[j] * 4 * n1;
+#pragma unroll
+                for (int n = 0; n < 4; n++) {
+                    const float v = El[(int64_t)n * n1];
+                    eA[j] = fmaf(mk[n], v, eA[j]);
+                    eB[j] = fmaf(mt[n], v, eB[j]);
+                }
+            }
+        }
+        // eight pairs at a time, their u-window sums loaded together (L2 latency once per eight)
+        for (int q0 = 0; q0 < ch.count; q0 += 8) {
+            float uw[8];
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int q = q0 + i;
+                uw[i] = (valid && q < ch.count) ? US[(int64_t)(direct ? sb[q] : sa[q]) * n1 + row] : 0.f;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; i++) {
+                const int q = q0 + i;
+                if (q >= ch.count) break;
+                float Mb = 0.f;
+#pragma unroll
+                for (int j = 0; j < ASM_MAX_NL; j++) {
+                    const float2 w = scf[q * ASM_MAX_NL + j];   // zero for multipoles the pair lacks
+                    Mb = fmaf(w.x, eA[j], fmaf(w.y, eB[j], Mb));
+                }
+                const float B = 2.f * Mb * uw[i];   // 0 on rows outside the grid
+                sig[((int64_t)sp[q] * ntile + tile) * SIG_BYTES + slot] = (unsigned char)df_offset_byte(B);
+            }
+        }
+    }
 }
 
 // Warp roles: two groups of four consumer warps alternate the direct products (row r0 + lt) and the
@@ -382,15 +501,55 @@ constexpr int PS_OFF = 2 * TR * ROWF + NOUT * 8;      // psi_b window offset in 
 // at a block barrier for every pair.
 constexpr int NTHR_OWN = 2 * NT + 32;
 
+// one double-float multiply-add: fixed-binade form (df_fma_off) or the Dot2 form (df_fma)
+template <bool OFF>
+__device__ __forceinline__ void acc_fma(DfAcc& a, float wh, float wl, float xh, float xl)
+{
+    if constexpr (OFF) df_fma_off(a, wh, wl, xh, xl);
+    else df_fma(a, wh, wl, xh, xl);
+}
+
+// direct products of one owned pair for row r0 + lt: acc += W(r, .) u_b over the band (and, NB, the
+// FP32 products of b = A_- psi), from the stage's coupling rows and row windows
+template <bool OFF, bool NB>
+__device__ __forceinline__ void own_direct(DfAcc (&acc)[4], float (&db)[4], const float* Hs, const float* Ls,
+                                           const float4* Us0, const float4* Us1, const float4* Ps, int lt)
+{
+#pragma unroll
+    for (int d = 0; d < BDO; d++) {
+        // window index of row rr = r + d - h: rr - (r0 - h) = lt + d; rows outside the grid are zero
+        // in the window and in W
+        const float4 x0 = Us0[lt + d], x1 = Us1[lt + d];
+        const float4 wh = *reinterpret_cast<const float4*>(Hs + lt * ROWF + d * 4);
+        const float4 wl = *reinterpret_cast<const float4*>(Ls + lt * ROWF + d * 4);
+        // W[t][u] = (w.x, w.y ; w.z, w.w)
+        acc_fma<OFF>(acc[0], wh.x, wl.x, x0.x, x0.y); acc_fma<OFF>(acc[0], wh.y, wl.y, x1.x, x1.y);
+        acc_fma<OFF>(acc[1], wh.x, wl.x, x0.z, x0.w); acc_fma<OFF>(acc[1], wh.y, wl.y, x1.z, x1.w);
+        acc_fma<OFF>(acc[2], wh.z, wl.z, x0.x, x0.y); acc_fma<OFF>(acc[2], wh.w, wl.w, x1.x, x1.y);
+        acc_fma<OFF>(acc[3], wh.z, wl.z, x0.z, x0.w); acc_fma<OFF>(acc[3], wh.w, wl.w, x1.z, x1.w);
+        if (NB) {   // psi_b window rows outside the grid are zero, as u_b's
+            const float4 q = Ps[lt + d];
+            db[0] += wh.x * q.x + wh.y * q.z;
+            db[1] += wh.x * q.y + wh.y * q.w;
+            db[2] += wh.z * q.x + wh.w * q.z;
+            db[3] += wh.z * q.y + wh.w * q.w;
+        }
+    }
+}
+
 // NEED_B: the pass also forms the FP32 products of b = A_- psi (a step's first pass).  The flag is
 // read on the device (a captured graph replays one launch for every pass), so both instantiations
-// are launched and the one that does not match the flag returns at once.
-template <bool NEED_B>
+// are launched and the one that does not match the flag returns at once.  OFF: the accumulators
+// take the fixed-binade form with the offsets of k_own_sigma (six FP32 operations per multiply-add,
+// error of order 2^-48 times the offset), else the Dot2 form (ten operations, error of order 2^-48
+// times the running sum); the host picks OFF from the solve's tolerance.
+template <bool NEED_B, bool OFF>
 __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const float4* __restrict__ u,
                                                              const float2* __restrict__ psi32,
                                                              const float* __restrict__ Wh, const float* __restrict__ Wl,
                                                              double2* __restrict__ r_out, float2* __restrict__ b_out,
                                                              float4* __restrict__ part_r, float4* __restrict__ part_b,
+                                                             const unsigned char* __restrict__ sig,
                                                              const int* need_b_flag, int* err)
 {
     if ((*need_b_flag != 0) != NEED_B) return;   // uniform over the grid
@@ -408,7 +567,7 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
     const uint32_t bytes = (uint32_t)rows * ROWF * 4;
     const int own0 = A.own_start[ch], nown = A.own_start[ch + 1] - own0;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int stage_f = STAGE_DF;
+    const int stage_f = STAGE_DFS;
     // u_b window: rows [lo, hi) land at window index lo - (r0 - h)
     const int lo = max(0, r0 - HO), hi = min(n1, r0 + TR + HO);
     // u is type-major ([channel][type][slot]): a type's window is one contiguous copy of 16 B rows
@@ -473,13 +632,15 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 const int64_t pw = DG_INB(A, (p * n1 + r0 + rows) * ROWF <= A.nb_coup, 0) ? p : 0;
                 const int nbw = DG_INB(A, ((int64_t)nb * 2 + 1) * n1 + hi <= (int64_t)A.nch * n1 * 2, 1) ? nb : 0;
                 fence_proxy_async();
-                mbar_expect_tx(&full[s], 2 * bytes + (need_b ? 3 : 2) * ubytes);
+                mbar_expect_tx(&full[s], 2 * bytes + (need_b ? 3 : 2) * ubytes + (OFF ? SIG_BYTES : 0));
                 bulk_load(st, Wh + (pw * n1 + r0) * ROWF, bytes, &full[s]);
                 bulk_load(st + TR * ROWF, Wl + (pw * n1 + r0) * ROWF, bytes, &full[s]);
                 bulk_load(st + 2 * TR * ROWF + uoff, u + ((int64_t)nbw * 2) * n1 + lo, ubytes, &full[s]);
                 bulk_load(st + 2 * TR * ROWF + NOUT * 4 + uoff, u + ((int64_t)nbw * 2 + 1) * n1 + lo, ubytes, &full[s]);
                 if (need_b)   // psi_b rows [lo, hi): 16 B each (both types), the state's own order
                     bulk_load(st + PS_OFF + uoff, psi32 + ((int64_t)nbw * n1 + lo) * 2, ubytes, &full[s]);
+                if (OFF)   // this pair-tile's accumulator offsets
+                    bulk_load(st + STAGE_DF, sig + ((int64_t)pw * ntile + tile) * SIG_BYTES, SIG_BYTES, &full[s]);
                 issued = k + 1;
             }
         }
@@ -491,28 +652,24 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
             const float* Ls = Hs + TR * ROWF;
             const float4* Us0 = reinterpret_cast<const float4*>(Hs + 2 * TR * ROWF);   // [row window], type 0
             const float4* Us1 = Us0 + NOUT;                                             // type 1
+            const unsigned char* Sg = reinterpret_cast<const unsigned char*>(Hs + STAGE_DF);   // offsets
             if (((k + grp) & 1) == 0) {
                 if (direct_row) {
                     const float4* Ps = reinterpret_cast<const float4*>(Hs + PS_OFF);   // psi_b window
-#pragma unroll
-                    for (int d = 0; d < BDO; d++) {
-                        // window index of row rr = r + d - h: rr - (r0 - h) = lt + d; rows outside the
-                        // grid are zero in the window and in W
-                        float4 x0 = Us0[lt + d], x1 = Us1[lt + d];
-                        float4 wh = *reinterpret_cast<const float4*>(Hs + lt * ROWF + d * 4);
-                        float4 wl = *reinterpret_cast<const float4*>(Ls + lt * ROWF + d * 4);
-                        // W[t][u] = (w.x, w.y ; w.z, w.w)
-                        df_fma(dd[0], wh.x, wl.x, x0.x, x0.y); df_fma(dd[0], wh.y, wl.y, x1.x, x1.y);
-                        df_fma(dd[1], wh.x, wl.x, x0.z, x0.w); df_fma(dd[1], wh.y, wl.y, x1.z, x1.w);
-                        df_fma(dd[2], wh.z, wl.z, x0.x, x0.y); df_fma(dd[2], wh.w, wl.w, x1.x, x1.y);
-                        df_fma(dd[3], wh.z, wl.z, x0.z, x0.w); df_fma(dd[3], wh.w, wl.w, x1.z, x1.w);
-                        if (need_b) {   // psi_b window rows outside the grid are zero, as u_b's
-                            float4 q = Ps[lt + d];
-                            db[0] += wh.x * q.x + wh.y * q.z;
-                            db[1] += wh.x * q.y + wh.y * q.w;
-                            db[2] += wh.z * q.x + wh.w * q.z;
-                            db[3] += wh.z * q.y + wh.w * q.w;
+                    if constexpr (OFF) {
+                        // this pair's sums in fixed-binade accumulators (df_fma_off), then added to dd
+                        const float sg = df_offset(Sg[lt]);
+                        DfAcc aa[4];
+                        for (int q = 0; q < 4; q++) { aa[q].s = sg; aa[q].c = 0.f; }
+                        own_direct<true, NEED_B>(aa, db, Hs, Ls, Us0, Us1, Ps, lt);
+                        for (int q = 0; q < 4; q++) {
+                            // the bound held: the sum stayed within 2^(k-2) = sg / 6 of the offset
+                            (void)DG_INB(A, fabsf(aa[q].s - sg) <= 0.1667f * sg, 6);
+                            DfAcc v = {aa[q].s - sg, aa[q].c};
+                            df_add(dd[q], v, 1.f);
                         }
+                    } else {
+                        own_direct<false, NEED_B>(dd, db, Hs, Ls, Us0, Us1, Ps, lt);
                     }
                 }
             } else {
@@ -522,7 +679,8 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                 const int j = lt;   // one output row per thread (NOUT == NT)
                 const bool slot_ok = DG_INB(A, ((int64_t)p * ntile + tile) * NOUT + j < A.nb_part, 2);
                 DfAcc tt[4];
-                for (int q = 0; q < 4; q++) df_zero(tt[q]);
+                const float sg = OFF ? df_offset(Sg[NOUT + j]) : 0.f;   // Dot2 form: from zero
+                for (int q = 0; q < 4; q++) { tt[q].s = sg; tt[q].c = 0.f; }
                 float tb[4] = {0.f, 0.f, 0.f, 0.f};
                 // diagonals whose W row r0 + j - d lies in the tile (a rolled loop: with the direct
                 // products unrolled, unrolling this one too overflows the instruction cache)
@@ -534,10 +692,10 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                     float4 wl = *reinterpret_cast<const float4*>(Ls + lr * ROWF + d * 4);
                     float4 x0 = us0[lr], x1 = us1[lr];
                     // (W^T)[t][u] = W[u][t]
-                    df_fma(tt[0], wh.x, wl.x, x0.x, x0.y); df_fma(tt[0], wh.z, wl.z, x1.x, x1.y);
-                    df_fma(tt[1], wh.x, wl.x, x0.z, x0.w); df_fma(tt[1], wh.z, wl.z, x1.z, x1.w);
-                    df_fma(tt[2], wh.y, wl.y, x0.x, x0.y); df_fma(tt[2], wh.w, wl.w, x1.x, x1.y);
-                    df_fma(tt[3], wh.y, wl.y, x0.z, x0.w); df_fma(tt[3], wh.w, wl.w, x1.z, x1.w);
+                    acc_fma<OFF>(tt[0], wh.x, wl.x, x0.x, x0.y); acc_fma<OFF>(tt[0], wh.z, wl.z, x1.x, x1.y);
+                    acc_fma<OFF>(tt[1], wh.x, wl.x, x0.z, x0.w); acc_fma<OFF>(tt[1], wh.z, wl.z, x1.z, x1.w);
+                    acc_fma<OFF>(tt[2], wh.y, wl.y, x0.x, x0.y); acc_fma<OFF>(tt[2], wh.w, wl.w, x1.x, x1.y);
+                    acc_fma<OFF>(tt[3], wh.y, wl.y, x0.z, x0.w); acc_fma<OFF>(tt[3], wh.w, wl.w, x1.z, x1.w);
                     if (need_b) {
                         float4 q = ps[lr];
                         tb[0] += wh.x * q.x + wh.z * q.z;
@@ -547,8 +705,12 @@ __global__ void __launch_bounds__(NTHR_OWN) k_residual_own_df(OpView A, const fl
                     }
                 }
                 if (slot_ok) {
-                    pr[2 * j] = make_float4(tt[0].s, tt[0].c, tt[1].s, tt[1].c);
-                    pr[2 * j + 1] = make_float4(tt[2].s, tt[2].c, tt[3].s, tt[3].c);
+                    if (OFF)
+                        for (int q = 0; q < 4; q++) (void)DG_INB(A, fabsf(tt[q].s - sg) <= 0.1667f * sg, 6);
+                    // (s - offset, c): exact (the Dot2 form has offset 0), the unnormalised pair the
+                    // gather pass adds
+                    pr[2 * j] = make_float4(tt[0].s - sg, tt[0].c, tt[1].s - sg, tt[1].c);
+                    pr[2 * j + 1] = make_float4(tt[2].s - sg, tt[2].c, tt[3].s - sg, tt[3].c);
                     if (need_b) pbp[j] = make_float4(tb[0], tb[1], tb[2], tb[3]);
                 }
             }
@@ -691,18 +853,38 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
     if (need_b) block_reduce_store(make_double2(0, 0), nb, nullptr, pn_b, slot);
 }
 
-size_t residual_own_df_smem() { return (size_t)NSTD * STAGE_DF * sizeof(float); }
+size_t residual_own_df_smem() { return (size_t)NSTD * STAGE_DFS * sizeof(float); }
 
-void launch_residual_owner_df(cudaStream_t st, const OpView& A, const float4* u, const float2* psi32, const float* Wh,
-                              const float* Wl, double2* r, float2* b, float4* part_r, float4* part_b,
-                              const int* need_b, int* err)
+void launch_residual_offsets(cudaStream_t st, const OpView& A, const AsmChunk* chunks, int nchunks, const int* gpair,
+                             const float4* gcoef, const double* s, const float* E, const float* Ew, float* US,
+                             unsigned char* sig, const float4* u)
+{
+    const int ntile = (A.n1 + TR - 1) / TR;
+    k_usum<<<dim3((A.n1 + 127) / 128, A.nch), 128, 0, st>>>(A, u, US);
+    k_own_sigma<<<dim3(ntile, (unsigned)(nchunks < 65535 ? nchunks : 65535)), SIG_BYTES, 0, st>>>(A, chunks, nchunks, gpair,
+                                                                                    gcoef, s, E, Ew, US, sig);
+}
+
+void launch_residual_owner_df(cudaStream_t st, const OpView& A, bool offsets, const unsigned char* sig,
+                              const float4* u, const float2* psi32, const float* Wh, const float* Wl, double2* r,
+                              float2* b, float4* part_r, float4* part_b, const int* need_b, int* err)
 {
     dim3 grid(A.nch, (A.n1 + TR - 1) / TR);
-    k_residual_own_df<true><<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r,
-                                                                          part_b, need_b, err);
-    k_residual_own_df<false><<<grid, NTHR_OWN, residual_own_df_smem(), st>>>(A, u, psi32, Wh, Wl, r, b, part_r,
-                                                                           part_b, need_b, err);
+    const size_t sm = residual_own_df_smem();
+    if (offsets) {
+        k_residual_own_df<true, true><<<grid, NTHR_OWN, sm, st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b, sig,
+                                                                need_b, err);
+        k_residual_own_df<false, true><<<grid, NTHR_OWN, sm, st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b, sig,
+                                                                 need_b, err);
+    } else {
+        k_residual_own_df<true, false><<<grid, NTHR_OWN, sm, st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b, sig,
+                                                                 need_b, err);
+        k_residual_own_df<false, false><<<grid, NTHR_OWN, sm, st>>>(A, u, psi32, Wh, Wl, r, b, part_r, part_b, sig,
+                                                                  need_b, err);
+    }
 }
+
+int residual_sig_bytes() { return SIG_BYTES; }
 
 void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                                const float4* v, const float2* psi32, double2* r, const float2* b,
@@ -724,11 +906,15 @@ cudaError_t apply_own32_prepare()
     cudaError_t e =
         cudaFuncSetAttribute(k_apply_own32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)apply_own32_smem());
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_residual_own_df<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)residual_own_df_smem());
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_residual_own_df<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)residual_own_df_smem());
+    const int sm = (int)residual_own_df_smem();
+    if ((e = cudaFuncSetAttribute(k_residual_own_df<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_residual_own_df<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_residual_own_df<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm)) !=
+            cudaSuccess)
+        return e;
+    return cudaFuncSetAttribute(k_residual_own_df<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
 }
 
 void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const float* H, int sign, const void* x,

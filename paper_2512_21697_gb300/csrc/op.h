@@ -94,6 +94,12 @@ struct dirac_op {
     float4* part_bdf = nullptr;  // ... of b = A_- psi on a step's first refinement pass
     float2* psi32 = nullptr;     // psi in FP32 and b = A_- psi (tolerance scale) of the residual pass
     float2* b32 = nullptr;
+    // offsets of the residual owner pass's accumulators: static envelopes of the pulse matrices
+    // ([L][4][n1], row/column maxima and their 13-row window maxima), u-window sums, offset bytes
+    float* own_E = nullptr;
+    float* own_Ew = nullptr;
+    float* own_US = nullptr;
+    unsigned char* own_sig = nullptr;
     int* need_b = nullptr;       // device flag: the next residual pass also forms ||b||^2
     int* ch_two_mu = nullptr;    // [nch] 2 mu of each channel (learned-guess features)
     dirac_guess* net = nullptr;  // learned initial guess (guess option 2), not owned
@@ -120,6 +126,7 @@ struct dirac_op {
     // overlapped assembly (dirac_op_set_overlap): the next step's coupling values are assembled on
     // st_asm into the other buffer set while the current step solves
     bool overlap = false;
+    int resid_mode = 0;                  // dirac_op_set_residual_mode (0 automatic, 1 Dot2, 2 offsets)
     dg::AsmSet aset[2];
     int acur = 0;                        // the set op->Wh / op->Wl currently point to
     cudaStream_t st_asm = nullptr;

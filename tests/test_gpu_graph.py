@@ -21,14 +21,19 @@ def _masked_random(bas, seed):
     return x / np.linalg.norm(x)
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+# (precision, residual accumulation mode, tolerance): mode 0 picks the Dot2 form at 1e-13; mode 2
+# forces the fixed-binade accumulators (the default at tolerances >= 1e-11) and their offset kernels
+@pytest.mark.parametrize("prec,mode,tol", [(0, 0, 1e-13), (1, 0, 1e-13), (2, 0, 1e-13), (2, 2, 1e-11)])
 @pytest.mark.parametrize("name", ["tiny", "small"])
-def test_graph_driver_matches_host_loop(name, prec):
+def test_graph_driver_matches_host_loop(name, prec, mode, tol):
     import torch
     cfg = W.WORKLOADS[name]
     bas = B.Basis(cfg)
-    kw = dict(tol=1e-13, precision=prec, max_iter=1000, tol_inner=1e-5, max_outer=30)
+    kw = dict(tol=tol, precision=prec, max_iter=1000, tol_inner=1e-5, max_outer=30)
     op1, op2 = B.Operator(bas, cfg, **kw), B.Operator(bas, cfg, **kw)
+    if mode:
+        op1.set_residual_mode(mode)
+        op2.set_residual_mode(mode)
     psi0 = _masked_random(bas, 5)
     T = cfg["n_cycles"] * 2 * np.pi / cfg["omega"]
     t0 = 0.45 * T
@@ -41,7 +46,7 @@ def test_graph_driver_matches_host_loop(name, prec):
     ib, rb, nb = op2.run(pb, 6, t0, hb, n_hist=0)
     assert na == nb == 2
     assert np.array_equal(ia, ib)
-    assert np.all(rb <= 1e-13)
+    assert np.all(rb <= tol)
     assert torch.linalg.norm(pa - pb).item() <= 1e-14 * torch.linalg.norm(pa).item()
     # a second call continues from the history and reuses the captured graph
     ia2, _, _ = op1.step(pa, 3, t0 + 6 * cfg["dt"], hist=ha, n_hist=2)

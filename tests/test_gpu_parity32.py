@@ -214,11 +214,14 @@ def test_precond32_backward_error(oracle_mod, name, sched):
           (name, sched, be, 8 * (2 * kb + 1) * U32, fe))
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", ["tiny", "small", "slice", "tail", "wide_l", "order5"])
-def test_residual_matches_oracle(oracle_mod, name):
+def test_residual_matches_oracle(oracle_mod, name, mode):
     # the refinement residual r = A_- psi - A_+ x as the step forms it (double-float owner/gather
-    # passes for order 7, per-row double-float kernel otherwise), against the oracle's two applies
+    # passes for order 7, per-row double-float kernel otherwise), against the oracle's two applies;
+    # mode 1: Dot2 accumulators, mode 2: fixed-binade accumulators with offsets (order 7 only)
     c = Case32(W.WORKLOADS[name], oracle_mod, precision=2)
+    c.op.set_residual_mode(mode)
     psi = c.random(35)
     x = psi + 0.01 * c.random(36)            # an iterate near psi, so the residual cancels partly
     pd, xd = c.to_dev(psi), c.to_dev(x)
@@ -231,8 +234,42 @@ def test_residual_matches_oracle(oracle_mod, name):
         ref = b - ax
         scale = max(np.abs(b).max(), np.abs(ax).max())
         assert np.abs(r - ref).max() <= 1e-11 * scale, (t, np.abs(r - ref).max() / scale)
+        print("residual %s mode %d t=%.3g: max err / scale %.3g, ||err|| / ||b|| %.3g" %
+              (name, mode, t, np.abs(r - ref).max() / scale, np.linalg.norm(r - ref) / np.linalg.norm(b)))
         # ||b|| from FP32 products: relative 1e-6
         assert abs(bn - np.linalg.norm(b)) <= 1e-6 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("name", ["tiny", "small", "tail", "wide_l"])
+def test_offset_residual_step_meets_tolerance(oracle_mod, name):
+    # a precision-2 step with the fixed-binade accumulators (mode 2, the default at tolerances
+    # >= 1e-11) ends on a state that solves the CN system to the tolerance: the oracle's FP64
+    # operator gives ||A_- psi - A_+ psi'|| <= 2 tol ||A_- psi|| (the residual the refinement tests
+    # carries an error of about 1e-13 ||b|| at most, far below tol), from a random state at
+    # peak-field times; the Dot2 form (mode 1) on the same inputs for comparison
+    tol = 1e-11
+    for mode in (2, 1):
+        c = Case32(W.WORKLOADS[name], oracle_mod, precision=2, tol=tol)
+        c.op.set_residual_mode(mode)
+        psi0 = c.random(51)
+        t0 = 0.5 * c.T()
+        pd = c.to_dev(psi0)
+        its, res, _ = c.op.step(pd, 1, t0)
+        psi1 = c.from_dev(pd)
+        tm = t0 + 0.5 * c.cfg["dt"]   # the step's midpoint time, where the oracle forms A_-+
+        b = c.orc.apply(tm, -1, psi0)
+        rel = np.linalg.norm(b - c.orc.apply(tm, +1, psi1)) / np.linalg.norm(b)
+        print("%s mode %d: reported %.3g, true residual %.3g, inner iterations %s" % (name, mode, res[0], rel,
+                                                                                    list(its)))
+        assert res[0] <= tol
+        assert rel <= 2 * tol, (mode, rel)
+
+
+def test_residual_mode_rejects_bad_values(oracle_mod):
+    c = Case32(W.TINY, oracle_mod, precision=2)
+    for bad in (-1, 3):
+        with pytest.raises(B.DiracError):
+            c.op.set_residual_mode(bad)
 
 
 def test_residual_precision0_matches_oracle(oracle_mod):
