@@ -257,7 +257,7 @@ void residual_accurate(dirac_op* op, const void* psi)
                                          (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b,
                                          op->dev_err);
             }
-            launch_residual_gather_df(op->st, op->ov, op->Sdf, op->Htdf, op->xsplit, op->vsplit, op->psi32,
+            launch_residual_gather_df(op->st, op->ov, op->SdfT, op->HdfT, op->xsplit, op->vsplit, op->psi32,
                                       (double2*)K.r, op->b32, op->part_rdf, op->part_bdf, op->need_b, op->part_n,
                                       op->part_n2);
         }
@@ -866,6 +866,20 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         for (size_t e = 0; e < hS.size(); e++) { sdf[e] = split(hS[e]); hdf[e] = split(tau * hH[e]); }
         TRY(upload(op, &op->Sdf, sdf));
         TRY(upload(op, &op->Htdf, hdf));
+        if (bd == 13) {
+            // the same bands row-contiguous, [kappa slot][d][entry][row], for the residual's gather
+            // pass (its threads hold consecutive rows, so a band load is one coalesced access)
+            std::vector<float2> st(sdf.size()), ht(hdf.size());
+            for (int ks = 0; ks < nk2; ks++)
+                for (int r = 0; r < n1; r++)
+                    for (int q = 0; q < bd * 4; q++) {
+                        size_t a = ((size_t)ks * n1 + r) * bd * 4 + q, t = ((size_t)ks * bd * 4 + q) * n1 + r;
+                        st[t] = sdf[a];
+                        ht[t] = hdf[a];
+                    }
+            TRY(upload(op, &op->SdfT, st));
+            TRY(upload(op, &op->HdfT, ht));
+        }
         std::vector<float4> cdf(B.pterm.size());
         for (size_t e = 0; e < cdf.size(); e++) {
             float2 a = split(tcab[2 * e]), b = split(tcab[2 * e + 1]);

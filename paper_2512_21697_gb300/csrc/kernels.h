@@ -182,6 +182,7 @@ void launch_residual_owner_df(cudaStream_t st, const OpView& A, bool offsets, co
                               const float4* u, const float2* psi32, const float* Wh, const float* Wl, double2* r,
                               float2* b, float4* part_r, float4* part_b, const int* need_b, int* err);
 int residual_sig_bytes();
+// S, Ht: the diagonal bands row-contiguous ([kappa slot][d][entry][row] float2)
 void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                                const float4* v, const float2* psi32, double2* r, const float2* b,
                                const float4* part_r, const float4* part_b, const int* need_b, double* pn_r,

@@ -778,8 +778,9 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
         const float4* va = v + (int64_t)ch * 2 * n1;
         const float2* pa = psi32 + (int64_t)ch * 2 * n1;
         int ks = A.ch_kslot[ch];
-        const float2* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
-        const float2* Hk = Ht + ((int64_t)ks * n1 + r) * ROWF;
+        // bands row-contiguous: entry q = 4 d + 2 t + u of row r at q * n1 + r (coalesced over rows)
+        const float2* Sk = S + (int64_t)ks * ROWF * n1 + r;
+        const float2* Hk = Ht + (int64_t)ks * ROWF * n1 + r;
         DfAcc acc[4];   // (type 0 re, im, type 1 re, im)
         for (int k = 0; k < 4; k++) df_zero(acc[k]);
         float bb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -790,8 +791,8 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
             float4 u0 = ua[rr], u1 = ua[n1 + rr], v0 = va[rr], v1 = va[n1 + rr];
             float4 pv = need_b ? *reinterpret_cast<const float4*>(pa + 2 * rr) : make_float4(0.f, 0.f, 0.f, 0.f);
             for (int t = 0; t < 2; t++) {
-                float2 s0 = Sk[d * 4 + 2 * t], s1 = Sk[d * 4 + 2 * t + 1];
-                float2 h0 = Hk[d * 4 + 2 * t], h1 = Hk[d * 4 + 2 * t + 1];
+                float2 s0 = Sk[(int64_t)(d * 4 + 2 * t) * n1], s1 = Sk[(int64_t)(d * 4 + 2 * t + 1) * n1];
+                float2 h0 = Hk[(int64_t)(d * 4 + 2 * t) * n1], h1 = Hk[(int64_t)(d * 4 + 2 * t + 1) * n1];
                 // re: S v_re + tau H u_im ;  im: S v_im - tau H u_re
                 df_fma(acc[2 * t], s0.x, s0.y, v0.x, v0.y);
                 df_fma(acc[2 * t], s1.x, s1.y, v1.x, v1.y);
