@@ -18,6 +18,32 @@ __device__ __forceinline__ float2 df_split(double v)
     return make_float2(h, l);
 }
 
+// split a double into hi + lo floats with integer operations on its bit pattern, no FP64 instruction:
+// hi is v truncated to 24 significant bits (sign, exponent rebiased, the top 23 mantissa bits), lo
+// the remaining 29 mantissa bits converted once to float (one rounding to 24 bits), so
+// |v - (hi + lo)| <= 2^-48 |v| and |lo| < ulp(hi).  |v| < 2^-126 gives (+-0, 0) (the float range's
+// underflow); lo is 0 when hi is within 2^52 of the smallest normal float (v below 2^-74);
+// infinities and NaN keep their kind in hi.  The FP64 pipe of this part issues a 64th of the FP32
+// rate, and a conversion split (df_split) costs it three conversions and a subtraction.
+__device__ __forceinline__ float2 df_split_bits(double v)
+{
+    const unsigned int h = (unsigned int)__double2hiint(v), l = (unsigned int)__double2loint(v);
+    const unsigned int sgn = h & 0x80000000u;
+    const int E = (int)((h >> 20) & 0x7ffu);
+    const int ef = E - 896;   // the float's biased exponent
+    if (E == 0x7ff)
+        return make_float2(__int_as_float((int)(sgn | 0x7f800000u | (((h & 0xfffffu) | l) ? 0x400000u : 0u))), 0.f);
+    if (ef <= 0) return make_float2(__int_as_float((int)sgn), 0.f);
+    if (ef >= 255) return make_float2(__int_as_float((int)(sgn | 0x7f800000u)), 0.f);
+    const unsigned int hb = sgn | ((unsigned int)ef << 23) | ((h & 0xfffffu) << 3) | (l >> 29);
+    float lo = 0.f;
+    if (ef > 52) {   // the low 29 bits weigh 2^(ef - 179) each: a normal float scale
+        lo = __int2float_rn((int)(l & 0x1fffffffu)) * __int_as_float((ef - 52) << 23);
+        if (sgn) lo = -lo;
+    }
+    return make_float2(__int_as_float((int)hb), lo);
+}
+
 // running compensated sum: s (the float sum of the rounded products) and c (all rounding errors)
 struct DfAcc {
     float s, c;

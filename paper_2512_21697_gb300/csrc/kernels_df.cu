@@ -277,13 +277,15 @@ __global__ void k_split_uv3(int64_t n, int n1, const double2* __restrict__ psi, 
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double2 p = psi[i], q = x[i];
-    float2 a = df_split(p.x + q.x), b = df_split(p.y + q.y), c = df_split(p.x - q.x), d = df_split(p.y - q.y);
+    // the sums exact in FP64 (4 additions), their splits and psi's hi words by integer operations
+    float2 a = df_split_bits(p.x + q.x), b = df_split_bits(p.y + q.y), c = df_split_bits(p.x - q.x),
+           d = df_split_bits(p.y - q.y);
     const int64_t ch = i / (2 * n1);
     const int rem = (int)(i - ch * 2 * n1), r = rem >> 1, t = rem & 1;
     const int64_t o = (ch * 2 + t) * n1 + r;
     u[o] = make_float4(a.x, a.y, b.x, b.y);
     v[o] = make_float4(c.x, c.y, d.x, d.y);
-    psi32[i] = make_float2((float)p.x, (float)p.y);
+    psi32[i] = make_float2(df_split_bits(p.x).x, df_split_bits(p.y).x);
 }
 
 // Refinement residual r = A_- psi - A_+ x in double-float through one coupling product:

@@ -810,7 +810,7 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
         double2 y0 = r_out[o], y1 = r_out[o + 1];
         const double yv[4] = {y0.x, y0.y, y1.x, y1.y};
         for (int k = 0; k < 4; k++) {
-            float2 h = df_split(yv[k]);
+            float2 h = df_split_bits(yv[k]);
             DfAcc t = {h.x, h.y};
             df_add(acc[k], t, 1.f);
         }
