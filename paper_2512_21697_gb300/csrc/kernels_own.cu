@@ -422,31 +422,42 @@ __global__ void __launch_bounds__(128) k_usum(OpView A, const float4* __restrict
 //    13-row window maxima of E.
 // All factors are rounded up or carry the 1.0625 of df_offset_byte.  Grid: (tiles, chunks of the
 // grouped assembly); a block forms its rows' eA, eB once and then spends a few FMAs per pair.
-__global__ void __launch_bounds__(SIG_BYTES) k_own_sigma(OpView A, const AsmChunk* __restrict__ chunks, int nchunks,
-                                                          const int* __restrict__ gpair,
-                                                          const float4* __restrict__ gcoef,
-                                                          const double* __restrict__ s, const float* __restrict__ E,
-                                                          const float* __restrict__ Ew, const float* __restrict__ US,
-                                                          unsigned char* __restrict__ sig)
+__global__ void __launch_bounds__(SIG_BYTES / 4) k_own_sigma(OpView A, const AsmChunk* __restrict__ chunks,
+                                                              int nchunks, const int* __restrict__ gpair,
+                                                              const float4* __restrict__ gcoef,
+                                                              const double* __restrict__ s, const float* __restrict__ E,
+                                                              const float* __restrict__ Ew,
+                                                              const float* __restrict__ US,
+                                                              unsigned char* __restrict__ sig)
 {
     __shared__ int sp[ASM_CHUNK], sa[ASM_CHUNK], sb[ASM_CHUNK];
     __shared__ float2 scf[ASM_CHUNK * ASM_MAX_NL];   // (|cA_l| S_l, |cB_l| S_l)
-    const int n1 = A.n1, tile = blockIdx.x, ntile = gridDim.x, slot = threadIdx.x;
-    const bool direct = slot < TR;
-    const int row = direct ? tile * TR + slot : tile * TR - HO + (slot - NOUT);
-    const bool valid = (direct || slot >= NOUT) && row >= 0 && row < n1;
-    const float* Et = (direct ? E : Ew) + (valid ? row : 0);
+    const int n1 = A.n1, tile = blockIdx.x, ntile = gridDim.x;
+    // each thread owns four consecutive slots of the record: slot0 .. slot0 + 3 (a group never
+    // straddles the direct / transposed boundary: TR and NOUT are multiples of 4)
+    static_assert(TR % 4 == 0 && NOUT % 4 == 0, "slot groups of four");
+    const int slot0 = 4 * threadIdx.x;
+    const bool direct = slot0 < TR;
+    int row[4];
+    bool valid[4];
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int sl = slot0 + i;
+        row[i] = direct ? tile * TR + sl : tile * TR - HO + (sl - NOUT);
+        valid[i] = (direct || sl >= NOUT) && row[i] >= 0 && row[i] < n1;
+    }
+    const float* Et = direct ? E : Ew;
     for (int c = blockIdx.y; c < nchunks; c += gridDim.y) {
         const AsmChunk ch = chunks[c];
         __syncthreads();   // the previous chunk's staged values are no longer read
-        for (int i = slot; i < ch.count; i += blockDim.x) {
+        for (int i = threadIdx.x; i < ch.count; i += blockDim.x) {
             const int p = gpair[ch.first + i];
             sp[i] = p;
             sa[i] = A.pair_a[p];
             sb[i] = A.pair_b[p];
         }
-        for (int i = slot; i < ch.count * ASM_MAX_NL; i += blockDim.x) {
-            const int l = ch.l[i % ASM_MAX_NL];
+        for (int i = threadIdx.x; i < ch.count * ASM_MAX_NL; i += blockDim.x) {
+            const int l = chunks[c].l[i % ASM_MAX_NL];   // from memory: no local copy of the record
             const float S = (float)((fabs(s[3 * l]) + fabs(s[3 * l + 1]) + fabs(s[3 * l + 2])) * (1.0 + 1e-6));
             const float4 cf = gcoef[(int64_t)ch.first * ASM_MAX_NL + i];   // (cA hi, lo, cB hi, lo)
             scf[i] = make_float2(fabsf(cf.x) * S, fabsf(cf.z) * S);
@@ -454,42 +465,40 @@ __global__ void __launch_bounds__(SIG_BYTES) k_own_sigma(OpView A, const AsmChun
         __syncthreads();
         const float fa = fabsf((float)ch.ka), fb = fabsf((float)ch.kb);
         const float mk[4] = {1.f, fa, fb, fa * fb}, mt[4] = {1.f, fb, fa, fa * fb};
-        float eA[ASM_MAX_NL], eB[ASM_MAX_NL];
+        float eA[4][ASM_MAX_NL], eB[4][ASM_MAX_NL];   // [slot][multipole]
 #pragma unroll
-        for (int j = 0; j < ASM_MAX_NL; j++) {
-            eA[j] = 0.f;
-            eB[j] = 0.f;
-            if (valid && j < ch.nl) {
-                const float* El = Et + (int64_t)ch.l[j] * 4 * n1;
+        for (int i = 0; i < 4; i++)
 #pragma unroll
-                for (int n = 0; n < 4; n++) {
-                    const float v = El[(int64_t)n * n1];
-                    eA[j] = fmaf(mk[n], v, eA[j]);
-                    eB[j] = fmaf(mt[n], v, eB[j]);
+            for (int j = 0; j < ASM_MAX_NL; j++) {
+                eA[i][j] = 0.f;
+                eB[i][j] = 0.f;
+                if (valid[i] && j < ch.nl) {
+                    const float* El = Et + (int64_t)ch.l[j] * 4 * n1 + row[i];
+#pragma unroll
+                    for (int n = 0; n < 4; n++) {
+                        const float v = El[(int64_t)n * n1];
+                        eA[i][j] = fmaf(mk[n], v, eA[i][j]);
+                        eB[i][j] = fmaf(mt[n], v, eB[i][j]);
+                    }
                 }
             }
-        }
-        // eight pairs at a time, their u-window sums loaded together (L2 latency once per eight)
-        for (int q0 = 0; q0 < ch.count; q0 += 8) {
-            float uw[8];
+        for (int q = 0; q < ch.count; q++) {
+            const int64_t ub = (int64_t)(direct ? sb[q] : sa[q]) * n1;
+            float uw[4];
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int q = q0 + i;
-                uw[i] = (valid && q < ch.count) ? US[(int64_t)(direct ? sb[q] : sa[q]) * n1 + row] : 0.f;
-            }
+            for (int i = 0; i < 4; i++) uw[i] = valid[i] ? US[ub + row[i]] : 0.f;
+            float2 w[ASM_MAX_NL];   // zero for multipoles the pair lacks
 #pragma unroll
-            for (int i = 0; i < 8; i++) {
-                const int q = q0 + i;
-                if (q >= ch.count) break;
+            for (int j = 0; j < ASM_MAX_NL; j++) w[j] = scf[q * ASM_MAX_NL + j];
+            unsigned int packed = 0;
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
                 float Mb = 0.f;
 #pragma unroll
-                for (int j = 0; j < ASM_MAX_NL; j++) {
-                    const float2 w = scf[q * ASM_MAX_NL + j];   // zero for multipoles the pair lacks
-                    Mb = fmaf(w.x, eA[j], fmaf(w.y, eB[j], Mb));
-                }
-                const float B = 2.f * Mb * uw[i];   // 0 on rows outside the grid
-                sig[((int64_t)sp[q] * ntile + tile) * SIG_BYTES + slot] = (unsigned char)df_offset_byte(B);
+                for (int j = 0; j < ASM_MAX_NL; j++) Mb = fmaf(w[j].x, eA[i][j], fmaf(w[j].y, eB[i][j], Mb));
+                packed |= df_offset_byte(2.f * Mb * uw[i]) << (8 * i);   // 0 on rows outside the grid
             }
+            *reinterpret_cast<unsigned int*>(sig + ((int64_t)sp[q] * ntile + tile) * SIG_BYTES + slot0) = packed;
         }
     }
 }
@@ -862,7 +871,7 @@ void launch_residual_offsets(cudaStream_t st, const OpView& A, const AsmChunk* c
 {
     const int ntile = (A.n1 + TR - 1) / TR;
     k_usum<<<dim3((A.n1 + 127) / 128, A.nch), 128, 0, st>>>(A, u, US);
-    k_own_sigma<<<dim3(ntile, (unsigned)(nchunks < 65535 ? nchunks : 65535)), SIG_BYTES, 0, st>>>(A, chunks, nchunks, gpair,
+    k_own_sigma<<<dim3(ntile, (unsigned)(nchunks < 65535 ? nchunks : 65535)), SIG_BYTES / 4, 0, st>>>(A, chunks, nchunks, gpair,
                                                                                     gcoef, s, E, Ew, US, sig);
 }
 
