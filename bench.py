@@ -56,6 +56,13 @@ def parse():
                     help="skip the comparison legs (peak-field window, precision 1, learned guess, batch)")
     ap.add_argument("--no-batch-leg", action="store_true", help="skip the batch leg of the comparison")
     ap.add_argument("--train-n", type=int, default=12, help="training trajectories of the learned guess")
+    ap.add_argument("--learned-eval", action="store_true",
+                    help="wider training (--train-pulses x --train-windows windows of --train-steps steps), then "
+                         "per-seed timing on --eval-seeds held-out pulses from seed --eval-seed0")
+    ap.add_argument("--train-pulses", type=int, default=25)
+    ap.add_argument("--train-windows", type=int, default=8)
+    ap.add_argument("--eval-seeds", type=int, default=16)
+    ap.add_argument("--eval-seed0", type=int, default=2000)
     ap.add_argument("--train-steps", type=int, default=10, help="steps per training trajectory")
     ap.add_argument("--guess-forward", type=int, default=0, metavar="M",
                     help="time only the learned-guess network forward on M seeded random positions (tcgen05 "
@@ -321,6 +328,97 @@ def train_guess(B, torch, bas, cfg, precision, n_train, train_steps, per_step=65
             "proportional to s^2, %d Adam steps of 8192; data %.1f s, training %.1f s; loss %.3g -> %.3g" %
             (n_train, 999 + n_train, train_steps, n_samples, iters, t_data, t_train, losses[0], losses[-1]))
     return net, note
+
+
+def train_guess_windows(B, torch, bas, cfg, precision, pulses, windows, steps, per_step=65536, iters=3000,
+                        seed0=1000):
+    """Wider training set: `pulses` seeded pulses (seeds seed0..), each stepping `windows` windows of
+    `steps` steps from the ground state at seeded start times, one operator per pulse; every window's
+    samples are drawn at once (probability proportional to s^2) so the set streams into device
+    memory.  Returns (net, note)."""
+    import numpy as np
+    from paper_2512_21697_gb300 import learned as L, workloads as W
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    X, Tg = [], []
+    t_data = time.time()
+    for pc in L.pulse_variants(cfg, range(seed0, seed0 + pulses)):
+        op = B.Operator(bas, pc, tol=cfg["tol"], precision=precision, max_iter=1000, tol_inner=1e-5, max_outer=30,
+                        guess=1)
+        T = pc["n_cycles"] * 2 * math.pi / pc["omega"]
+        rng = np.random.default_rng(int(round(pc["E0"] * 1e9)) % (2 ** 31))
+        for t_s in rng.uniform(0.05, 0.95, windows) * T:
+            tr = L.Trajectory(bas, pc, steps, precision=precision, tol=cfg["tol"], op=op, t_start=t_s)
+            x, t, sc = L.samples(tr)
+            xs, ts = L.importance_subsample(x, t, sc, per_step * (steps - 4), g)
+            X.append(xs)
+            Tg.append(ts)
+            del tr, x, t, sc
+        del op
+        torch.cuda.empty_cache()
+    X, Tg = torch.cat(X), torch.cat(Tg)
+    n_samples = int(X.shape[0])
+    t_data = time.time() - t_data
+    net = B.GuessNet(8192, W.guess_net_init(7))
+    t_train = time.time()
+    losses = L.train(net, X, Tg, iters, batch=8192, lr=1e-3, seed=1)
+    torch.cuda.synchronize()
+    t_train = time.time() - t_train
+    del X, Tg
+    note = ("%d seeded pulses (seeds %d..%d) x %d windows of %d steps from seeded start times (%d windows, "
+            "extrapolated guess), %d samples drawn with probability proportional to s^2, %d Adam steps of 8192; "
+            "data %.1f s, training %.1f s; loss %.3g -> %.3g" %
+            (pulses, seed0, seed0 + pulses - 1, windows, steps, pulses * windows, n_samples, iters, t_data, t_train,
+             losses[0], losses[-1]))
+    return net, note
+
+
+def learned_eval(args, world, rank, local, dist):
+    """--learned-eval: the wider training set (train_guess_windows), then every held-out seeded pulse
+    (seeds --eval-seed0.., never trained on) from its own seeded start time: W warm-up steps and K
+    timed steps on the graph driver with the extrapolated guess and with the learned one, to the
+    workload's tolerance; per-seed iterations/step and steps/s."""
+    import numpy as np
+    import torch
+    from paper_2512_21697_gb300 import binding as B, learned as L, workloads as W
+    dev = torch.device("cuda", local)
+    cfg = dict(W.WORKLOADS[args.workload])
+    bas = B.Basis(cfg)
+    net, note = train_guess_windows(B, torch, bas, cfg, args.precision, args.train_pulses, args.train_windows,
+                                    args.train_steps)
+    psi0, _ = bas.initial_state()
+    rows = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for seed, pc in zip(range(args.eval_seed0, args.eval_seed0 + args.eval_seeds),
+                        L.pulse_variants(cfg, range(args.eval_seed0, args.eval_seed0 + args.eval_seeds))):
+        row = {"seed": seed, "E0": pc["E0"], "wavelength_nm": W.NM_HARTREE / pc["omega"], "cycles": pc["n_cycles"],
+               "t_start_over_T": pc["t_start"] / (pc["n_cycles"] * 2 * math.pi / pc["omega"])}
+        for guess, key in ((1, "extrapolated"), (2, "learned")):
+            stream = torch.cuda.Stream()
+            r, _, op = window_run(B, torch, bas, pc, psi0, pc["t_start"], args.warmup, args.steps, stream, dev,
+                                  args.precision, guess=guess, net=net if guess == 2 else None)
+            row[key] = {k: r[k] for k in ("value", "ms_per_step", "iters_per_step", "max_resid")}
+            del op
+            torch.cuda.empty_cache()
+        row["speedup"] = row["learned"]["value"] / row["extrapolated"]["value"]
+        rows.append(row)
+    ck = clocks.stop()
+    agg = {k: float(np.mean([r[g][k] for r in rows])) for g in ("learned",) for k in ("value", "iters_per_step")}
+    ext = {k: float(np.mean([r["extrapolated"][k] for r in rows])) for k in ("value", "iters_per_step")}
+    line = {"metric": METRIC, "value": agg["value"] * world, "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 / agg["value"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ["f64", "c64+f64", "c64+df64"][args.precision], "data": "synthetic",
+            "config": {"workload": workload_desc(args.workload, cfg) + "; learned initial guess on %d held-out "
+                                   "seeded pulses (seeds %d..%d), each from its own seeded start time" %
+                                   (args.eval_seeds, args.eval_seed0, args.eval_seed0 + args.eval_seeds - 1),
+                       "training": note},
+            "mean_learned": agg, "mean_extrapolated": ext,
+            "mean_speedup_vs_extrapolated": float(np.mean([r["speedup"] for r in rows])),
+            "per_seed": rows, "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def hbm_peak():
@@ -659,6 +757,9 @@ def main():
         return
     if args.workload == "batch":
         batch_bench(args, world, rank, local, dist)
+        return
+    if args.learned_eval:
+        learned_eval(args, world, rank, local, dist)
         return
     if args.learned:
         learned_bench(args, world, rank, local, dist)

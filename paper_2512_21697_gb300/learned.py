@@ -32,13 +32,20 @@ def pulse_variants(base, seeds, E0=(0.02, 0.2), wavelength=(400.0, 1600.0), cycl
 
 
 class Trajectory:
-    """States of one run: psi at t_start + k dt for k = 0..n_steps (device complex128 tensors)."""
+    """States of one run: psi at t_start + k dt for k = 0..n_steps (device complex128 tensors), from
+    the ground state.  op: an operator of this pulse to reuse (one is made otherwise); t_start:
+    the start time (default cfg["t_start"]), so one operator serves several windows of a pulse."""
 
-    def __init__(self, bas, cfg, n_steps, precision=0, tol=1e-12):
+    def __init__(self, bas, cfg, n_steps, precision=0, tol=1e-12, op=None, t_start=None):
         import torch
-        self.cfg = cfg
+        self.cfg = dict(cfg)
+        if t_start is not None:
+            self.cfg["t_start"] = float(t_start)
+        cfg = self.cfg
         self.bas = bas
-        op = B.Operator(bas, cfg, tol=tol, precision=precision, max_iter=1000, tol_inner=1e-5, max_outer=30, guess=1)
+        if op is None:
+            op = B.Operator(bas, cfg, tol=tol, precision=precision, max_iter=1000, tol_inner=1e-5, max_outer=30,
+                            guess=1)
         psi0, _ = bas.initial_state()
         psi = torch.from_numpy(psi0).cuda()
         hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device="cuda")
