@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("order", C.c_int), ("grid", C.c_int), ("r_lin", C.c_double), ("n_lin", C.c_int),
                 ("kappa_max", C.c_int), ("two_mu_max", C.c_int), ("l_max", C.c_int),
                 ("quad", C.c_int), ("E0", C.c_double), ("omega", C.c_double),
-                ("n_cycles", C.c_double), ("dt", C.c_double), ("time_eval", C.c_int)]
+                ("n_cycles", C.c_double), ("dt", C.c_double), ("time_eval", C.c_int), ("b1_drop", C.c_int)]
 
 
 def _load():

@@ -28,8 +28,9 @@ typedef struct {
     double Z, c, R;      /* nuclear charge, speed of light (a.u.), box radius                    */
     int N;               /* retained B-splines per radial block                                  */
     int order;           /* B-spline order k (polynomial degree k-1)                             */
-    int grid;            /* 0 linear breakpoints, 1 linear up to r_lin then geometric            */
-    double r_lin;        /* grid 1: end of the linear part                                       */
+    int grid;            /* 0 linear breakpoints, 1 linear up to r_lin then geometric,           */
+                         /* 2 exponential: first interval r_lin, ratio fixed by the last = R     */
+    double r_lin;        /* grid 1: end of the linear part; grid 2: the first interval           */
     int n_lin;           /* grid 1: number of linear intervals                                   */
     int kappa_max;       /* |kappa| <= kappa_max                                                 */
     int two_mu_max;      /* |2mu| <= two_mu_max; <= 0 keeps every mu                             */
@@ -38,6 +39,7 @@ typedef struct {
     double E0, omega, n_cycles; /* sin^2 pulse, Eq. (ndpPot)                                     */
     double dt;           /* time step                                                            */
     int time_eval;       /* 0: H at t+dt/2 (midpoint rule), 1: H at t+dt (Eq. solPsi as printed) */
+    int b1_drop;         /* 1: the literal boundary reading, B_1 removed for every kappa too      */
 } or_params;
 
 typedef struct or_ctx or_ctx;

@@ -162,3 +162,24 @@ def test_1s_mean_radius(small):
     assert abs(v @ R @ v - (2 * g + 1) / 2) < 1e-7   # first order in the basis error
     S, _ = small.radial(-1)
     assert abs(v @ S @ v - 1) < 1e-13
+
+
+def test_literal_b1_reading_under_refinement(oracle_mod):
+    # Sec. 2.2 read literally removes B_1 (nonzero slope at r = 0) for every kappa, forcing P'(0) = 0
+    # for the 1s state, whose large component grows as r^gamma (gamma ~ 1).  On knots refined
+    # towards r = 0 (exponential grid, first interval h) its miss of the closed-form level falls,
+    # but slowly: measured 2.7e-2, 1.0e-2, 3.4e-3, 2.2e-3 for h = 0.3 .. 0.01 and still 1.0e-3 at
+    # h = 1e-5, while the adopted reading (B_1 kept where P(0) = Q(0) = 0) sits at ~1e-11 on the same
+    # knots.  The literal reading does not reach the same level on any practical grid.
+    e_ex = dirac_level(1, -1)
+    lit, kept = [], []
+    for h in (0.3, 0.1, 0.03, 0.01):
+        for drop, out in ((1, lit), (0, kept)):
+            o = small_oracle(oracle_mod, R=40.0, N=40, grid=2, r_lin=h, n_lin=0, b1_drop=drop, kappa_max=1,
+                             l_max=1)
+            E, _ = o.eigen(-1)
+            out.append(E[E > -C * C][0] - e_ex)
+    assert all(e > 0 for e in lit)                               # above the level (variational side)
+    assert all(a > 1.4 * b for a, b in zip(lit, lit[1:]))        # falls with every refinement
+    assert lit[-1] > 1e-3                                        # and stays far from the closed form
+    assert max(abs(e) for e in kept) < 1e-9                      # where the adopted reading sits
