@@ -143,7 +143,7 @@ void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void
         launch_fact32(op->st, op->ov, op->rad_chunks, op->nrad, op->Gdf, op->pv.L, (const float*)K.S,
                       (const float*)K.H, sign, x, op->Zf, op->cab_df, y, bsub, dv, pdot, pnrm, skip);
     else if (op->part_own)
-        launch_apply_own32(op->st, op->ov, (const float*)K.S, (const float*)K.H, sign, x, (const float*)K.W, y,
+        launch_apply_own32(op->st, op->ov, op->S32T, op->H32T, sign, x, (const float*)K.W, y,
                            op->part_own, bsub, dv, pdot, pnrm, skip, op->dev_err);
     else
         launch_apply_t<float>(grid, op->st, op->ov, (const float*)K.S, (const float*)K.H, sign, x,
@@ -867,16 +867,19 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         TRY(upload(op, &op->Sdf, sdf));
         TRY(upload(op, &op->Htdf, hdf));
         if (bd == 13) {
-            // the same bands row-contiguous, [kappa slot][d][entry][row], for the residual's gather
-            // pass (its threads hold consecutive rows, so a band load is one coalesced access)
+            // the same bands with the rows innermost, [kappa slot][d][row][entry], for the residual's
+            // gather pass (its threads hold consecutive rows: a diagonal's 2 x 2 block of a row is one
+            // 32-byte record next to the neighbouring rows' records)
             std::vector<float2> st(sdf.size()), ht(hdf.size());
             for (int ks = 0; ks < nk2; ks++)
                 for (int r = 0; r < n1; r++)
-                    for (int q = 0; q < bd * 4; q++) {
-                        size_t a = ((size_t)ks * n1 + r) * bd * 4 + q, t = ((size_t)ks * bd * 4 + q) * n1 + r;
-                        st[t] = sdf[a];
-                        ht[t] = hdf[a];
-                    }
+                    for (int d = 0; d < bd; d++)
+                        for (int e = 0; e < 4; e++) {
+                            size_t a = (((size_t)ks * n1 + r) * bd + d) * 4 + e;
+                            size_t t = (((size_t)ks * bd + d) * n1 + r) * 4 + e;
+                            st[t] = sdf[a];
+                            ht[t] = hdf[a];
+                        }
             TRY(upload(op, &op->SdfT, st));
             TRY(upload(op, &op->HdfT, ht));
         }
@@ -965,6 +968,21 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
         float2 *fdU, *fdL, *fdUr, *fdDi;
         TRY(upload(op, &fdS, fS));
         TRY(upload(op, &fdH, fH));
+        if (bd == 13) {
+            // rows innermost, [kappa slot][d][row][entry], for the complex64 owner pass's diagonal block
+            std::vector<float> st(fS.size()), ht(fH.size());
+            for (int ks = 0; ks < nk2; ks++)
+                for (int r = 0; r < n1; r++)
+                    for (int d = 0; d < bd; d++)
+                        for (int e = 0; e < 4; e++) {
+                            size_t a = (((size_t)ks * n1 + r) * bd + d) * 4 + e;
+                            size_t t = (((size_t)ks * bd + d) * n1 + r) * 4 + e;
+                            st[t] = fS[a];
+                            ht[t] = fH[a];
+                        }
+            TRY(upload(op, &op->S32T, st));
+            TRY(upload(op, &op->H32T, ht));
+        }
         TRY(upload(op, &fdU, fU));
         TRY(upload(op, &fdL, fL));
         TRY(upload(op, &fdUr, fUr));

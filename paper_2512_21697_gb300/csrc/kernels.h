@@ -182,11 +182,12 @@ void launch_residual_owner_df(cudaStream_t st, const OpView& A, bool offsets, co
                               const float4* u, const float2* psi32, const float* Wh, const float* Wl, double2* r,
                               float2* b, float4* part_r, float4* part_b, const int* need_b, int* err);
 int residual_sig_bytes();
-// S, Ht: the diagonal bands row-contiguous ([kappa slot][d][entry][row] float2)
+// S, Ht: the diagonal bands with the rows innermost ([kappa slot][d][row][entry] float2)
 void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                                const float4* v, const float2* psi32, double2* r, const float2* b,
                                const float4* part_r, const float4* part_b, const int* need_b, double* pn_r,
                                double* pn_b);
+// S, H: the FP32 diagonal bands with the rows innermost ([kappa slot][d][row][entry])
 void launch_apply_own32(cudaStream_t st, const OpView& A, const float* S, const float* H, int sign, const void* x,
                         const float* W, void* y, float4* part, const void* bsub, const void* dv, double2* pdot,
                         double* pnrm, const KState* skip, int* err);

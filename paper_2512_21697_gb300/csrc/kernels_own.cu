@@ -209,8 +209,9 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
         // group 0's diagonal block (S + sign i tau H0) x_a, while the first copies are in flight
         if (grp == 0 && direct_row) {
             int ks = A.ch_kslot[ch];
-            const float* Sk = S + ((int64_t)ks * n1 + r) * ROWF;
-            const float* Hk = H + ((int64_t)ks * n1 + r) * ROWF;
+            // bands with the rows innermost: diagonal d of row r is the float4 at (ks BDO + d) n1 + r
+            const float4* Sk = reinterpret_cast<const float4*>(S) + (int64_t)ks * BDO * n1 + r;
+            const float4* Hk = reinterpret_cast<const float4*>(H) + (int64_t)ks * BDO * n1 + r;
             const float* xaf = reinterpret_cast<const float*>(xa);
             float st = (float)(sign * A.tau);
 #pragma unroll
@@ -218,8 +219,8 @@ __global__ void __launch_bounds__(2 * NT + 32) k_apply_own32(OpView A, const flo
                 int rr = r + d - HO;
                 if (rr < 0 || rr >= n1) continue;
                 float4 xv = *reinterpret_cast<const float4*>(xaf + 4 * rr);
-                float4 sv = *reinterpret_cast<const float4*>(Sk + d * 4);
-                float4 hv = *reinterpret_cast<const float4*>(Hk + d * 4);
+                float4 sv = Sk[(int64_t)d * n1];
+                float4 hv = Hk[(int64_t)d * n1];
                 float h00 = st * hv.x, h01 = st * hv.y, h10 = st * hv.z, h11 = st * hv.w;
                 d0.x += sv.x * xv.x + sv.y * xv.z - (h00 * xv.y + h01 * xv.w);
                 d0.y += sv.x * xv.y + sv.y * xv.w + (h00 * xv.x + h01 * xv.z);
@@ -787,9 +788,9 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
         const float4* va = v + (int64_t)ch * 2 * n1;
         const float2* pa = psi32 + (int64_t)ch * 2 * n1;
         int ks = A.ch_kslot[ch];
-        // bands row-contiguous: entry q = 4 d + 2 t + u of row r at q * n1 + r (coalesced over rows)
-        const float2* Sk = S + (int64_t)ks * ROWF * n1 + r;
-        const float2* Hk = Ht + (int64_t)ks * ROWF * n1 + r;
+        // bands with the rows innermost: diagonal d of row r is the 32-byte record (ks BDO + d) n1 + r
+        const float4* Sk = reinterpret_cast<const float4*>(S) + ((int64_t)ks * BDO * n1 + r) * 2;
+        const float4* Hk = reinterpret_cast<const float4*>(Ht) + ((int64_t)ks * BDO * n1 + r) * 2;
         DfAcc acc[4];   // (type 0 re, im, type 1 re, im)
         for (int k = 0; k < 4; k++) df_zero(acc[k]);
         float bb[4] = {0.f, 0.f, 0.f, 0.f};
@@ -799,9 +800,11 @@ __global__ void __launch_bounds__(NT) k_residual_gather_df(OpView A, const float
             if (rr < 0 || rr >= n1) continue;
             float4 u0 = ua[rr], u1 = ua[n1 + rr], v0 = va[rr], v1 = va[n1 + rr];
             float4 pv = need_b ? *reinterpret_cast<const float4*>(pa + 2 * rr) : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 sq[2] = {Sk[(int64_t)d * n1 * 2], Sk[(int64_t)d * n1 * 2 + 1]};   // entries (0 1 | 2 3)
+            const float4 hq[2] = {Hk[(int64_t)d * n1 * 2], Hk[(int64_t)d * n1 * 2 + 1]};
             for (int t = 0; t < 2; t++) {
-                float2 s0 = Sk[(int64_t)(d * 4 + 2 * t) * n1], s1 = Sk[(int64_t)(d * 4 + 2 * t + 1) * n1];
-                float2 h0 = Hk[(int64_t)(d * 4 + 2 * t) * n1], h1 = Hk[(int64_t)(d * 4 + 2 * t + 1) * n1];
+                const float2 s0 = make_float2(sq[t].x, sq[t].y), s1 = make_float2(sq[t].z, sq[t].w);
+                const float2 h0 = make_float2(hq[t].x, hq[t].y), h1 = make_float2(hq[t].z, hq[t].w);
                 // re: S v_re + tau H u_im ;  im: S v_im - tau H u_re
                 df_fma(acc[2 * t], s0.x, s0.y, v0.x, v0.y);
                 df_fma(acc[2 * t], s1.x, s1.y, v1.x, v1.y);

@@ -70,7 +70,8 @@ struct dirac_op {
     double* W = nullptr;         // coupling values, FP64 (precision 0 and 1)
     // precision 2: double-float operator data (hi/lo float pairs)
     float2 *Gdf = nullptr, *Kdf = nullptr, *KTdf = nullptr, *Sdf = nullptr, *Htdf = nullptr;
-    float2 *SdfT = nullptr, *HdfT = nullptr;   // S, tau H0 row-contiguous (order 7), for the gather pass
+    float2 *SdfT = nullptr, *HdfT = nullptr;   // S, tau H0 rows innermost (order 7), for the gather pass
+    float *S32T = nullptr, *H32T = nullptr;     // S, H0 in FP32 rows innermost, for the complex64 owner pass
     float *Wh = nullptr, *Wl = nullptr;   // coupling hi words (also the FP32 values) and lo words
     float4* cab_df = nullptr;
     // factorised complex64 apply of the inner solve (dirac_op_set_factorised)
