@@ -152,7 +152,7 @@ FP32_LANE_OPS = 152 * 128 * 2.070   # 10^9 lane operations/s: SMs x FP32 lanes x
 # raw counters.  Valid for the kernels as captured (a changed kernel needs a new capture).
 TRAFFIC_MEDIUM = {"df": (1.768965e9 + 0.155458e9, "profiles/k_residual_own_df_medium.md"),
                   "df_owner": (1.768965e9 + 0.155458e9, "profiles/k_residual_own_df_medium.md"),
-                  "f32": (0.886455e9 + 0.075098e9, "profiles/k_apply_own32_medium.md")}
+                  "f32": (0.887222e9 + 0.074195e9, "profiles/k_apply_own32_medium.md")}
 MEDIUM_UNITS = 6944 * 601
 DF_OPS_PER_FMA = 10                 # FP32 operations of one double-float multiply-add (df64.cuh df_fma)
 DF_OPS_PER_FMA_OFF = 6              # ... in the fixed-binade form (df_fma_off), tolerances >= 1e-11
