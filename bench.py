@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=8.0)
     ap.add_argument("--batch-n", type=int, default=64, help="instances of --workload batch")
+    ap.add_argument("--batch-lmax", type=int, default=2, help="multipole limit of the batch instances")
+    ap.add_argument("--batch-kmax", type=int, default=20, help="|kappa| limit of the batch instances")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned initial guess on production trajectories, then time guess=2 vs guess=1")
     ap.add_argument("--factorised", action="store_true",
@@ -601,7 +603,7 @@ def batch_measure(args, world, local, n_req, learned, peak, fp64=True):
     import torch
     from paper_2512_21697_gb300 import binding as B, learned as L, workloads as W
     dev = torch.device("cuda", local)
-    cfgs = W.batch_instances(n_req, seed0=0)
+    cfgs = W.batch_instances(n_req, seed0=0, kappa_max=args.batch_kmax, l_max=args.batch_lmax)
     t_setup = time.time()
     with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         bases = list(ex.map(B.Basis, cfgs))
@@ -668,9 +670,9 @@ def batch_measure(args, world, local, n_req, learned, peak, fp64=True):
     if "fp64" in out:
         out["speedup_vs_fp64"] = head["value"] / out["fp64"]["value"]   # instance-steps/s against instance-steps/s
     config = {"workload": "batch: %d instances (of %d requested), E0 log-uniform [0.02, 0.2], wavelength "
-                          "[400, 1600] nm, 2-6 cycles, N 400-1000, |kappa|<=20, l<=2, R=300, dt=0.005, "
-                          "tol=1e-10, start %s" % (n_inst, n_req, "at each instance's peak field"
-                                                   if peak else "at the pulse start"),
+                          "[400, 1600] nm, 2-6 cycles, N 400-1000, |kappa|<=%d, l<=%d, R=300, dt=0.005, "
+                          "tol=1e-10, start %s" % (n_inst, n_req, args.batch_kmax, args.batch_lmax,
+                                                   "at each instance's peak field" if peak else "at the pulse start"),
               "instances": n_inst, "unknowns": int(sum(b.n for _, b in used)), "window": best,
               "precond_schedule": "tuned (one lane per channel, or one warp per channel with rows fixed to lanes)",
               "tune_ms": {"windows": cand, "lanes": tune_ms[0].tolist(), "warps": tune_ms[1].tolist()},
