@@ -1031,7 +1031,14 @@ extern "C" dirac_status dirac_operator_setup(const dirac_basis* basis, const dir
                         }
                     TRY(upload(op, &op->own_E, hE));
                     TRY(upload(op, &op->own_Ew, hEw));
-                    TRY(dev_alloc(op, &op->own_US, (size_t)B.nch * n1));
+                    // u-window sums with zero margins (residual_us_floats); the margins stay zero
+                    const size_t nus = residual_us_floats(B.nch, n1);
+                    TRY(dev_alloc(op, &op->own_US, nus));
+                    if (cudaMemsetAsync(op->own_US, 0, nus * sizeof(float), op->st) != cudaSuccess) {
+                        set_error("dirac_operator_setup: cudaMemsetAsync failed");
+                        dirac_op_free(op);
+                        return DIRAC_E_CUDA;
+                    }
                     TRY(dev_alloc(op, &op->own_sig, (size_t)op->npairs * ntile * residual_sig_bytes()));
                 }
                 TRY(dev_alloc(op, &op->psi32, (size_t)op->n));

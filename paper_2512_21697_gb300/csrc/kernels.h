@@ -171,7 +171,7 @@ bool apply_own_supported(const OpView& A);
 cudaError_t apply_own32_prepare();
 size_t residual_own_df_smem();
 // the double-float residual's owner pass reads one offset byte per accumulator (df_fma_off):
-// launch_residual_offsets forms them from the u-window sums US (nch x n1 floats, written here), the
+// launch_residual_offsets forms them from the u-window sums US (residual_us_floats, written here), the
 // static envelopes E, Ew ([L][4][n1] floats), the grouped assembly's chunks and coefficients and
 // the time factors s, into sig (npairs x tiles x residual_sig_bytes() bytes)
 void launch_residual_offsets(cudaStream_t st, const OpView& A, const AsmChunk* chunks, int nchunks, const int* gpair,
@@ -182,6 +182,7 @@ void launch_residual_owner_df(cudaStream_t st, const OpView& A, bool offsets, co
                               const float4* u, const float2* psi32, const float* Wh, const float* Wl, double2* r,
                               float2* b, float4* part_r, float4* part_b, const int* need_b, int* err);
 int residual_sig_bytes();
+size_t residual_us_floats(int nch, int n1);   // size of the u-window-sum buffer US (zeroed once)
 // S, Ht: the diagonal bands with the rows innermost ([kappa slot][d][row][entry] float2)
 void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                                const float4* v, const float2* psi32, double2* r, const float2* b,

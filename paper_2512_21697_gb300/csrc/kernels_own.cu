@@ -377,6 +377,11 @@ constexpr int PS_OFF = 2 * TR * ROWF + NOUT * 8;      // psi_b window offset in 
 // offset bytes of one (pair, tile): direct rows r0 + [0, TR) at [0, TR), transposed output rows
 // r0 - h + [0, NOUT) at [NOUT, 2 NOUT); the stage keeps them after its floats
 constexpr int SIG_BYTES = 2 * NOUT;
+// u-window sums: row r of channel ch at ch * us_stride(n1) + US_PAD + r; US_PAD zero rows on both
+// sides (the offset kernel reads four consecutive rows from r0 - h on) and a stride that keeps the
+// four-row groups of the offset kernel 8- or 16-byte aligned
+constexpr int US_PAD = 8;
+__host__ __device__ constexpr int us_stride(int n1) { return ((n1 + 2 * US_PAD) + 3) & ~3; }
 constexpr int STAGE_DFS = STAGE_DF + SIG_BYTES / 4;   // floats per stage with the offset bytes
 }
 
@@ -404,7 +409,7 @@ __global__ void __launch_bounds__(128) k_usum(OpView A, const float4* __restrict
     if (r < n1) {
         float sum = 0.f;
         for (int d = 0; d < BDO; d++) sum += m[threadIdx.x + d];
-        US[(int64_t)ch * n1 + r] = sum;
+        US[(int64_t)ch * us_stride(n1) + US_PAD + r] = sum;
     }
 }
 
@@ -423,6 +428,69 @@ __global__ void __launch_bounds__(128) k_usum(OpView A, const float4* __restrict
 //    13-row window maxima of E.
 // All factors are rounded up or carry the 1.0625 of df_offset_byte.  Grid: (tiles, chunks of the
 // grouped assembly); a block forms its rows' eA, eB once and then spends a few FMAs per pair.
+// the pairs of one chunk for one thread's four row slots (NL = the chunk's multipoles): the chunk's
+// kappa-weighted envelopes eA, eB at the four rows, then per pair the bound of each slot and its
+// offset byte, the four packed into one store
+template <int NL>
+__device__ __forceinline__ void sigma_pairs(const AsmChunk& ch, const int* __restrict__ lsel,
+                                            const float* __restrict__ Et, int n1, int usn, const int (&row)[4],
+                                            const bool (&valid)[4], bool direct, int slot0, int tile, int ntile,
+                                            const int* sp, const int* sa, const int* sb, const float2* scf,
+                                            const float* __restrict__ US, unsigned char* __restrict__ sig)
+{
+    const float fa = fabsf((float)ch.ka), fb = fabsf((float)ch.kb);
+    const float mk[4] = {1.f, fa, fb, fa * fb}, mt[4] = {1.f, fb, fa, fa * fb};
+    float eA[4][NL], eB[4][NL];   // [slot][multipole]
+#pragma unroll
+    for (int j = 0; j < NL; j++) {
+        const float* El = Et + (int64_t)lsel[j] * 4 * n1;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            eA[i][j] = 0.f;
+            eB[i][j] = 0.f;
+            if (valid[i]) {
+#pragma unroll
+                for (int n = 0; n < 4; n++) {
+                    const float v = El[(int64_t)n * n1 + row[i]];
+                    eA[i][j] = fmaf(mk[n], v, eA[i][j]);
+                    eB[i][j] = fmaf(mt[n], v, eB[i][j]);
+                }
+            }
+        }
+    }
+    // the four rows' u-window sums are one aligned group (zero margins outside the grid): one
+    // 16-byte load for the direct slots (rows r0 + 4 t), two 8-byte ones for the transposed slots
+    // (rows r0 - h + 4 t, two rows off the 16-byte grid)
+    // a group with a valid slot has rows within [-h, n1 + 2], inside the margins; the unused slots
+    // TR .. NOUT - 1 and groups past the grid load nothing
+    const bool any = valid[0] || valid[1] || valid[2] || valid[3];
+    const int64_t uo = US_PAD + row[0];
+    for (int q = 0; q < ch.count; q++) {
+        const float* ub = US + (int64_t)(direct ? sb[q] : sa[q]) * usn + uo;
+        float uw[4] = {0.f, 0.f, 0.f, 0.f};
+        if (!any) {
+        } else if (direct) {
+            const float4 t = *reinterpret_cast<const float4*>(ub);
+            uw[0] = t.x; uw[1] = t.y; uw[2] = t.z; uw[3] = t.w;
+        } else {
+            const float2 t0 = *reinterpret_cast<const float2*>(ub), t1 = *reinterpret_cast<const float2*>(ub + 2);
+            uw[0] = t0.x; uw[1] = t0.y; uw[2] = t1.x; uw[3] = t1.y;
+        }
+        float2 w[NL];   // zero for multipoles the pair lacks
+#pragma unroll
+        for (int j = 0; j < NL; j++) w[j] = scf[q * ASM_MAX_NL + j];
+        unsigned int packed = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            float Mb = 0.f;
+#pragma unroll
+            for (int j = 0; j < NL; j++) Mb = fmaf(w[j].x, eA[i][j], fmaf(w[j].y, eB[i][j], Mb));
+            packed |= df_offset_byte(valid[i] ? 2.f * Mb * uw[i] : 0.f) << (8 * i);
+        }
+        *reinterpret_cast<unsigned int*>(sig + ((int64_t)sp[q] * ntile + tile) * SIG_BYTES + slot0) = packed;
+    }
+}
+
 __global__ void __launch_bounds__(SIG_BYTES / 4) k_own_sigma(OpView A, const AsmChunk* __restrict__ chunks,
                                                               int nchunks, const int* __restrict__ gpair,
                                                               const float4* __restrict__ gcoef,
@@ -448,6 +516,7 @@ __global__ void __launch_bounds__(SIG_BYTES / 4) k_own_sigma(OpView A, const Asm
         valid[i] = (direct || sl >= NOUT) && row[i] >= 0 && row[i] < n1;
     }
     const float* Et = direct ? E : Ew;
+    const int usn = us_stride(n1);
     for (int c = blockIdx.y; c < nchunks; c += gridDim.y) {
         const AsmChunk ch = chunks[c];
         __syncthreads();   // the previous chunk's staged values are no longer read
@@ -464,42 +533,15 @@ __global__ void __launch_bounds__(SIG_BYTES / 4) k_own_sigma(OpView A, const Asm
             scf[i] = make_float2(fabsf(cf.x) * S, fabsf(cf.z) * S);
         }
         __syncthreads();
-        const float fa = fabsf((float)ch.ka), fb = fabsf((float)ch.kb);
-        const float mk[4] = {1.f, fa, fb, fa * fb}, mt[4] = {1.f, fb, fa, fa * fb};
-        float eA[4][ASM_MAX_NL], eB[4][ASM_MAX_NL];   // [slot][multipole]
-#pragma unroll
-        for (int i = 0; i < 4; i++)
-#pragma unroll
-            for (int j = 0; j < ASM_MAX_NL; j++) {
-                eA[i][j] = 0.f;
-                eB[i][j] = 0.f;
-                if (valid[i] && j < ch.nl) {
-                    const float* El = Et + (int64_t)ch.l[j] * 4 * n1 + row[i];
-#pragma unroll
-                    for (int n = 0; n < 4; n++) {
-                        const float v = El[(int64_t)n * n1];
-                        eA[i][j] = fmaf(mk[n], v, eA[i][j]);
-                        eB[i][j] = fmaf(mt[n], v, eB[i][j]);
-                    }
-                }
-            }
-        for (int q = 0; q < ch.count; q++) {
-            const int64_t ub = (int64_t)(direct ? sb[q] : sa[q]) * n1;
-            float uw[4];
-#pragma unroll
-            for (int i = 0; i < 4; i++) uw[i] = valid[i] ? US[ub + row[i]] : 0.f;
-            float2 w[ASM_MAX_NL];   // zero for multipoles the pair lacks
-#pragma unroll
-            for (int j = 0; j < ASM_MAX_NL; j++) w[j] = scf[q * ASM_MAX_NL + j];
-            unsigned int packed = 0;
-#pragma unroll
-            for (int i = 0; i < 4; i++) {
-                float Mb = 0.f;
-#pragma unroll
-                for (int j = 0; j < ASM_MAX_NL; j++) Mb = fmaf(w[j].x, eA[i][j], fmaf(w[j].y, eB[i][j], Mb));
-                packed |= df_offset_byte(2.f * Mb * uw[i]) << (8 * i);   // 0 on rows outside the grid
-            }
-            *reinterpret_cast<unsigned int*>(sig + ((int64_t)sp[q] * ntile + tile) * SIG_BYTES + slot0) = packed;
+        switch (ch.nl) {
+        case 1: sigma_pairs<1>(ch, chunks[c].l, Et, n1, usn, row, valid, direct, slot0, tile, ntile, sp, sa, sb, scf,
+                               US, sig); break;
+        case 2: sigma_pairs<2>(ch, chunks[c].l, Et, n1, usn, row, valid, direct, slot0, tile, ntile, sp, sa, sb, scf,
+                               US, sig); break;
+        case 3: sigma_pairs<3>(ch, chunks[c].l, Et, n1, usn, row, valid, direct, slot0, tile, ntile, sp, sa, sb, scf,
+                               US, sig); break;
+        default: sigma_pairs<4>(ch, chunks[c].l, Et, n1, usn, row, valid, direct, slot0, tile, ntile, sp, sa, sb, scf,
+                                US, sig); break;
         }
     }
 }
@@ -898,6 +940,7 @@ void launch_residual_owner_df(cudaStream_t st, const OpView& A, bool offsets, co
 }
 
 int residual_sig_bytes() { return SIG_BYTES; }
+size_t residual_us_floats(int nch, int n1) { return (size_t)nch * us_stride(n1); }
 
 void launch_residual_gather_df(cudaStream_t st, const OpView& A, const float2* S, const float2* Ht, const float4* u,
                                const float4* v, const float2* psi32, double2* r, const float2* b,
