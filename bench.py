@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--batch-kmax", type=int, default=20, help="|kappa| limit of the batch instances")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned initial guess on production trajectories, then time guess=2 vs guess=1")
-    ap.add_argument("--factorised", action="store_true",
-                    help="factorised complex64 apply in the inner solve (coupling never stored)")
+    ap.add_argument("--factorised", type=int, nargs="?", const=1, default=0,
+                    help="factorised complex64 apply in the inner solve (coupling never stored): "
+                         "1 subgroup form (default when given), 2 per-channel form")
     ap.add_argument("--spectrum", action="store_true",
                     help="also time the photoelectron spectrum dP/dE of the final state (window (0, 2] a.u.)")
     ap.add_argument("--overlap", action="store_true",
@@ -781,7 +782,7 @@ def main():
     if args.precision == 2 and args.overlap:
         op.set_overlap(True)   # next step's assembly overlaps the current solve (same arithmetic)
     if args.precision == 2 and args.factorised:
-        op.set_factorised(True)
+        op.set_factorised(args.factorised)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)
         hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev)
@@ -884,6 +885,10 @@ def main():
                    "driver": ("dirac_run: the time loop as one CUDA graph with conditional WHILE/IF nodes, one "
                               "graph launch and one status read-back per call" if graph else
                               "dirac_step: host-driven loop"),
+                   "inner_apply": (["stored coupling values (owner/gather passes)",
+                                    "factorised: radial band products x angular coefficients, subgroup form",
+                                    "factorised: radial band products x angular coefficients, per-channel form"]
+                                   [args.factorised] if args.precision == 2 else None),
                    "assembly": "overlapped with the previous step's solve" if (args.precision == 2 and
                                                                                args.overlap) else "in step",
                    "l2": "inputs larger than L2: %.1f GB of coupling values streamed per operator apply" %

@@ -251,8 +251,10 @@ class Operator:
         return self.opts.precision
 
     def set_factorised(self, enable=True):
-        """dirac_op_set_factorised: factorised complex64 apply in the inner solve."""
-        _check(lib().dirac_op_set_factorised(self._h, int(bool(enable))), "dirac_op_set_factorised")
+        """dirac_op_set_factorised: factorised complex64 apply in the inner solve (True or 1: subgroup
+        form, 2: per-channel form, False or 0: stored coupling)."""
+        mode = int(enable) if not isinstance(enable, bool) else int(enable)
+        _check(lib().dirac_op_set_factorised(self._h, mode), "dirac_op_set_factorised")
 
     def spectrum(self, psi, e_lo, e_hi, grid, counts=False):
         """dirac_spectrum: (dP/dE on the host grid, levels in the window) or, with counts=True,

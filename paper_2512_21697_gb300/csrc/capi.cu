@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <map>
 #include <tuple>
 #include <cmath>
@@ -127,7 +128,8 @@ void collect_phases(dirac_op* op)
 // ---- launch helpers ------------------------------------------------------------------------
 int apply_parts(const dirac_op* op, const Krylov& K)
 {
-    if (K.prec == 1 && op->fact32) return grid_for(op->ov.n1, FTR) * op->ov.nch;
+    if (K.prec == 1 && op->fact32 == 1) return grid_for(op->ov.n1, FTR) * op->nfsub;
+    if (K.prec == 1 && op->fact32 == 2) return grid_for(op->ov.n1, FTR) * op->ov.nch;
     return (K.prec == 1 && op->part_own) ? op->nparts_own : op->nparts_apply;
 }
 
@@ -139,9 +141,13 @@ void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void
     if (K.prec == 0)
         launch_apply_t<double>(grid, op->st, op->ov, (const double*)K.S, (const double*)K.H, sign, x,
                                (const double*)K.W, y, bsub, dv, pdot, pnrm, skip);
-    else if (op->fact32)
-        launch_fact32(op->st, op->ov, op->rad_chunks, op->nrad, op->Gdf, op->pv.L, (const float*)K.S,
-                      (const float*)K.H, sign, x, op->Zf, op->cab_df, y, bsub, dv, pdot, pnrm, skip);
+    else if (op->fact32 == 1)
+        launch_fact32_sub(op->st, op->ov, op->rad_lanes, op->nrad_lanes, op->fsub, op->nfsub, op->fsub_max,
+                          op->fitem_off, op->fitem_coef, op->Ghi, op->pv.L, op->S32T, op->H32T, sign, x, op->Zf, y, bsub, dv,
+                          pdot, pnrm, skip, op->dev_err);
+    else if (op->fact32 == 2)
+        launch_fact32_chan(op->st, op->ov, op->rad_chunks, op->nrad, op->Gdf, op->pv.L, (const float*)K.S,
+                           (const float*)K.H, sign, x, op->Zf, op->cab_df, y, bsub, dv, pdot, pnrm, skip);
     else if (op->part_own)
         launch_apply_own32(op->st, op->ov, op->S32T, op->H32T, sign, x, (const float*)K.W, y,
                            op->part_own, bsub, dv, pdot, pnrm, skip, op->dev_err);
@@ -157,7 +163,7 @@ void launch_assemble_set(dirac_op* op, cudaStream_t st, const AsmSet& a)
     PhaseScope ps(op, DIRAC_PHASE_ASSEMBLE, op->npairs ? 4 : 2, st);
     k_time_factors<<<1, 128, 0, st>>>(op->pv, a.t_eval, a.s);
     int be = op->ov.n1 * op->ov.bd * 4;
-    k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, st>>>(op->pv, be, a.s, a.Gdf);
+    k_field_combine_df<<<dim3(grid_for(be, 256), op->pv.L * 4), 256, 0, st>>>(op->pv, be, a.s, a.Gdf, a.Ghi);
     if (op->npairs) {
         if (op->asm_chunks) {
             launch_assemble_grp_df(st, op->ov, op->asm_chunks, op->asm_nchunks, op->asm_gpair, op->asm_gcoef,
@@ -1230,13 +1236,129 @@ extern "C" dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int s
     return DIRAC_OK;
 }
 
+// Subgroup form of the factorised apply (mode 1): kappa chunks of up to FLANE channels for the radial
+// pass; for the angular pass, the channels of each mu in FSG-sized subgroups (ordered by the parity
+// of their orbital l, then |kappa|, so that a subgroup's outputs share many partners) with the union
+// of their (partner, multipole) items and per item and output the coefficients of U, V, U', V'
+// (own pairs a < b: -(cA, cA ka, cB, cB ka); pairs b < a: (cB, cB ka, cA, cA ka); the apply's sign
+// is applied in the kernel).
+static dirac_status fact_sub_setup(dirac_op* op)
+{
+    using namespace dg;
+    const Basis& B = op->B;
+    const int nch = B.nch, L = op->pv.L;
+    // radial: kappa groups of the kappa-sorted channel order, FLANE channels at a time
+    std::vector<int> ks(nch), ordv(nch);
+    CUDA_TRY(cudaMemcpy(ordv.data(), op->ov.prec_order, sizeof(int) * nch, cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(ks.data(), op->ov.ch_kslot, sizeof(int) * nch, cudaMemcpyDeviceToHost));
+    std::vector<RadChunk> ch1;
+    for (int i = 0; i < nch;) {
+        int j = i;
+        while (j < nch && ks[ordv[j]] == ks[ordv[i]] && j - i < FLANE) j++;
+        ch1.push_back(RadChunk{ks[ordv[i]], B.kap[ordv[i]], i, j - i});
+        i = j;
+    }
+    // two chunks per block where their channels fit the lanes together: largest first, each paired
+    // with the largest unpaired chunk that still fits
+    std::stable_sort(ch1.begin(), ch1.end(), [](const RadChunk& p, const RadChunk& q) { return p.count > q.count; });
+    std::vector<char> used(ch1.size(), 0);
+    std::vector<RadPack> rl;
+    for (size_t i = 0; i < ch1.size(); i++) {
+        if (used[i]) continue;
+        used[i] = 1;
+        RadPack pk{};
+        pk.c[0] = ch1[i];
+        pk.c[1] = RadChunk{ch1[i].ks, ch1[i].kappa, ch1[i].first, 0};
+        for (size_t j = i + 1; j < ch1.size(); j++)
+            if (!used[j] && ch1[i].count + ch1[j].count <= FLANE) {
+                used[j] = 1;
+                pk.c[1] = ch1[j];
+                break;
+            }
+        rl.push_back(pk);
+    }
+    // the pair terms' coefficients (cA, cB) = (-c tau A1, c tau A2), from their double-float words
+    std::vector<float4> cdf(B.pterm.size());
+    if (!cdf.empty())
+        CUDA_TRY(cudaMemcpy(cdf.data(), op->cab_df, sizeof(float4) * cdf.size(), cudaMemcpyDeviceToHost));
+    // per channel: its (partner, multipole, coefficients of U, V, U', V') terms
+    struct Use { int b, l; double c[4]; };
+    std::vector<std::vector<Use>> uses(nch);
+    for (size_t p = 0; p < B.pa.size(); p++) {
+        const int a = B.pa[p], b = B.pb[p];
+        for (int q = B.pterm_start[p]; q < B.pterm_start[p + 1]; q++) {
+            const double cA = (double)cdf[q].x + (double)cdf[q].y, cB = (double)cdf[q].z + (double)cdf[q].w;
+            const double ka = B.kap[a], kb = B.kap[b];
+            uses[a].push_back(Use{b, B.pterm[q].l, {-cA, -cA * ka, -cB, -cB * ka}});
+            uses[b].push_back(Use{a, B.pterm[q].l, {cB, cB * kb, cA, cA * kb}});
+        }
+    }
+    std::vector<int> tms(B.tmu.begin(), B.tmu.end());
+    std::sort(tms.begin(), tms.end());
+    tms.erase(std::unique(tms.begin(), tms.end()), tms.end());
+    auto lparity = [](int k) { return (k > 0 ? k : -k - 1) & 1; };
+    std::vector<FactSub> subs;
+    std::vector<int> ioff;
+    std::vector<float4> icoef;
+    for (int tm : tms) {
+        std::vector<int> chs;
+        for (int a = 0; a < nch; a++)
+            if (B.tmu[a] == tm) chs.push_back(a);
+        std::stable_sort(chs.begin(), chs.end(), [&](int p, int q) {
+            const int kp = B.kap[p], kq = B.kap[q];
+            if (lparity(kp) != lparity(kq)) return lparity(kp) < lparity(kq);
+            if (std::abs(kp) != std::abs(kq)) return std::abs(kp) < std::abs(kq);
+            return kp < kq;
+        });
+        for (size_t s0 = 0; s0 < chs.size(); s0 += FSG) {
+            FactSub g{};
+            g.first = (int)ioff.size();
+            std::map<std::pair<int, int>, std::array<float4, FSG>> items;   // (partner, l), ordered
+            for (int j = 0; j < FSG; j++) {
+                g.out[j] = s0 + j < chs.size() ? chs[s0 + j] : -1;
+                if (g.out[j] < 0) continue;
+                for (const Use& u : uses[g.out[j]]) {
+                    auto key = std::make_pair(u.b, u.l);
+                    auto it = items.find(key);
+                    if (it == items.end()) {
+                        std::array<float4, FSG> z;
+                        z.fill(make_float4(0.f, 0.f, 0.f, 0.f));
+                        it = items.emplace(key, z).first;
+                    }
+                    it->second[j] = make_float4((float)u.c[0], (float)u.c[1], (float)u.c[2], (float)u.c[3]);
+                }
+            }
+            for (auto& kv : items) {
+                ioff.push_back(kv.first.first * L + kv.first.second);
+                for (int j = 0; j < FSG; j++) icoef.push_back(kv.second[j]);
+            }
+            g.count = (int)ioff.size() - g.first;
+            subs.push_back(g);
+        }
+    }
+    // heaviest subgroups first, so the long blocks start in the first wave
+    std::stable_sort(subs.begin(), subs.end(), [](const FactSub& p, const FactSub& q) { return p.count > q.count; });
+    if (ioff.empty()) { ioff.push_back(0); icoef.assign(FSG, make_float4(0.f, 0.f, 0.f, 0.f)); }
+    dirac_status e = upload(op, &op->rad_lanes, rl);
+    if (!e) e = upload(op, &op->fsub, subs);
+    if (!e) e = upload(op, &op->fitem_off, ioff);
+    if (!e) e = upload(op, &op->fitem_coef, icoef);
+    if (e) return e;
+    op->nrad_lanes = (int)rl.size();
+    op->nfsub = (int)subs.size();
+    op->fsub_max = subs.empty() ? 1 : std::max(1, subs[0].count);   // sorted by decreasing count
+    CUDA_TRY(fact_sub_prepare(op->fsub_max));
+    return DIRAC_OK;
+}
+
 extern "C" dirac_status dirac_op_set_factorised(dirac_op* op, int enable)
 {
-    if (!op || (enable && (op->opts.precision != 2 || op->ov.bd != 13 || !op->cab_df))) {
-        set_error("dirac_op_set_factorised: needs precision 2 and order-7 splines");
+    if (!op || enable < 0 || enable > 2 ||
+        (enable && (op->opts.precision != 2 || op->ov.bd != 13 || !op->cab_df || !op->S32T))) {
+        set_error("dirac_op_set_factorised: needs precision 2, order-7 splines and a mode 0, 1 or 2");
         return DIRAC_E_ARG;
     }
-    if (enable && !op->Zf) {
+    if (enable == 2 && !op->rad_chunks) {
         // kappa groups of the kappa-sorted channel order, in chunks of at most FCOL channels
         std::vector<int> ks(op->ov.nch), ordv(op->ov.nch), kap(op->ov.nch);
         CUDA_TRY(cudaMemcpy(ordv.data(), op->ov.prec_order, sizeof(int) * ordv.size(), cudaMemcpyDeviceToHost));
@@ -1252,10 +1374,21 @@ extern "C" dirac_status dirac_op_set_factorised(dirac_op* op, int enable)
         dirac_status e = upload(op, &op->rad_chunks, rc);
         if (e) return e;
         op->nrad = (int)rc.size();
-        e = dev_alloc(op, &op->Zf, (size_t)op->ov.nch * op->pv.L * 4 * FTR * 2);
+    }
+    if (enable == 1 && !op->fsub) {
+        dirac_status e = fact_sub_setup(op);
+        if (e) return e;
+        // the G hi words as plain floats, written by every later assembly of each buffer set
+        const size_t gsz = (size_t)op->pv.L * 4 * op->ov.n1 * op->ov.bd * 4;
+        for (int c = 0; c < 2; c++)
+            if (op->aset[c].Gdf && !op->aset[c].Ghi && (e = dev_alloc(op, &op->aset[c].Ghi, gsz))) return e;
+        op->Ghi = op->aset[op->acur].Ghi;
+    }
+    if (enable && !op->Zf) {
+        dirac_status e = dev_alloc(op, &op->Zf, (size_t)op->ov.nch * op->pv.L * 4 * FTR * 2);
         if (e) return e;
     }
-    op->fact32 = enable != 0;
+    op->fact32 = enable;
     op->config_gen++;   // captured graphs hold the other apply
     return DIRAC_OK;
 }
@@ -1274,6 +1407,7 @@ static void select_set(dirac_op* op, int c)
     op->t_eval = a.t_eval;
     op->s = a.s;
     op->Gdf = a.Gdf;
+    op->Ghi = a.Ghi;
     op->Kdf = a.Kdf;
     op->KTdf = a.KTdf;
     op->Wh = a.Wh;
@@ -1319,6 +1453,7 @@ extern "C" dirac_status dirac_op_set_overlap(dirac_op* op, int enable)
             CUDA_TRY(cudaEventCreateWithFlags(&op->ev_asm[i], cudaEventDisableTiming));
             CUDA_TRY(cudaEventCreateWithFlags(&op->ev_use[i], cudaEventDisableTiming));
         }
+        if (op->aset[0].Ghi && (e = dev_alloc(op, &a.Ghi, (size_t)op->pv.L * 4 * be))) return e;
         op->aset[1] = a;
     }
     op->overlap = enable != 0;

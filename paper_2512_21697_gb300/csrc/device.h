@@ -87,6 +87,21 @@ constexpr int FCOL = 8;
 struct RadChunk {
     int ks, kappa, first, count;
 };
+// The subgroup form of the factorised apply: the radial pass puts up to FLANE channels of one kappa
+// on the lanes of a warp (their band entries are the same); the angular pass gives a block FSG
+// output channels of one mu.  Every partner of a channel has mu +- 1, so the outputs of one mu share
+// their partners' band products: an "item" is one (partner, multipole) product set, loaded once per
+// block and applied to all FSG outputs with one float4 of coefficients per output (zero where the
+// output does not use it).
+constexpr int FLANE = 32;
+constexpr int FSG = 8;
+struct RadPack {          // one radial block: up to two kappa chunks, c[0].count + c[1].count <= FLANE lanes
+    RadChunk c[2];
+};
+struct FactSub {
+    int first, count;     // items first .. first + count - 1 of the item lists
+    int out[FSG];         // output channels (-1: slot unused)
+};
 
 struct PulseView {
     int L;

@@ -68,7 +68,7 @@ __global__ void k_add_float_scaled(int64_t n, const float2* d, const KState* st,
 __global__ void k_copy32(int64_t n, const float2* a, float2* b);
 // double-float path (precision 2)
 __global__ void k_split_vec(int64_t n, const double2* __restrict__ x, float4* __restrict__ xd);
-__global__ void k_field_combine_df(PulseView P, int block_elems, const double* s, float2* G);
+__global__ void k_field_combine_df(PulseView P, int block_elems, const double* s, float2* G, float* Gh);
 __global__ void k_build_K_df(OpView A, int block_elems, const float2* G, float2* K, float2* KT);
 void launch_assemble_df(dim3 grid, cudaStream_t st, const OpView& A, const float2* K, const float2* KT, const float4* cab, float* Wh,
                         float* Wl);
@@ -147,11 +147,18 @@ void launch_precond_rot_t(cudaStream_t st, const OpView& A, const void* U, const
 // bounded-wait self-test: one block waits `limit` cycles on an mbarrier nothing completes
 cudaError_t launch_wait_selftest(cudaStream_t st, long long limit, int* err);
 
-// factorised complex64 apply (coupling values never stored): radial + angular pass per tile
+// factorised complex64 apply (coupling values never stored): radial + angular pass per tile, in the
+// per-channel form (partials: one per tile and channel) or the subgroup form (one per tile and
+// subgroup; ST, HT the FP32 diagonal bands with the rows innermost)
 int fact_tile();
-void launch_fact32(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc, const float2* G, int L,
-                   const float* S, const float* H, int sign, const void* x, float2* Z, const float4* cab, void* y,
-                   const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip);
+void launch_fact32_chan(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc, const float2* G, int L,
+                        const float* S, const float* H, int sign, const void* x, float2* Z, const float4* cab,
+                        void* y, const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip);
+cudaError_t fact_sub_prepare(int max_items);   // dynamic shared-memory limits (once per device)
+void launch_fact32_sub(cudaStream_t st, const OpView& A, const RadPack* rl, int nrl, const FactSub* subs, int nsub,
+                       int max_items, const int* item_off, const float4* item_coef, const float* Gh, int L,
+                       const float* ST, const float* HT, int sign, const void* x, float2* Z, void* y,
+                       const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip, int* err);
 
 // learned-guess network forward on the fifth-generation tensor cores (tcgen05, TMEM accumulators)
 size_t guess_forward_tc05_smem();

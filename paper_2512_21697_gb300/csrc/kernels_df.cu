@@ -28,7 +28,7 @@ __global__ void k_split_vec(int64_t n, const double2* __restrict__ x, float4* __
 }
 
 // G[l][n][e] = sum_c s[l][c] M[l][c][n][e] in double, stored split (a few MB per step)
-__global__ void k_field_combine_df(PulseView P, int block_elems, const double* s, float2* G)
+__global__ void k_field_combine_df(PulseView P, int block_elems, const double* s, float2* G, float* Gh)
 {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int ln = blockIdx.y;
@@ -36,7 +36,9 @@ __global__ void k_field_combine_df(PulseView P, int block_elems, const double* s
     int l = ln / 4, n = ln % 4;
     double v = 0;
     for (int c = 0; c < 3; c++) v += s[l * 3 + c] * P.M[(((int64_t)l * 3 + c) * 4 + n) * block_elems + e];
-    G[(int64_t)ln * block_elems + e] = df_split(v);
+    const float2 g = df_split(v);
+    G[(int64_t)ln * block_elems + e] = g;
+    if (Gh) Gh[(int64_t)ln * block_elems + e] = g.x;   // the hi words alone, for the factorised apply
 }
 
 // K[key][e] = sum_n m_n G^n_l[e] and its block transpose KT[key][r][d][t][u] = K[key][r'][2h-d][u][t]

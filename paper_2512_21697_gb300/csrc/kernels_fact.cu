@@ -11,17 +11,30 @@
 // per-pair work is a short combination with the angular coefficients.  For the transposed use of
 // a pair (rows of b from x_a), W_ab^T x_a = sum_l cA_l (U'_l^a + kb V'_l^a) + cB_l (U_l^a + kb V_l^a).
 //
-// Two passes per radial tile of FTR rows: k_fact_radial32 (block = a chunk of up to FCOL channels
-// of one kappa, one multipole) forms the four products at the tile's rows, the bands built on the
-// fly from G and shared by the chunk's channels; k_fact_angular32 (block = channel) combines its
-// partners' products, adds the diagonal block and runs the BiCGSTAB epilogues.  The products of a
-// tile (about 53 MB at the production size) stay in L2 between the two passes.
+// Two passes per radial tile of FTR rows, the products of a tile (about 53 MB at the production
+// size) staying in L2 between them.  Two forms:
+//  - per-channel (mode 2): k_fact_radial32 (block = a chunk of up to FCOL channels of one kappa, one
+//    multipole; a thread per row) forms the four products, the bands built on the fly from G and
+//    shared by the chunk's channels; k_fact_angular32 (block = channel) reads each partner's products
+//    from L2 and combines them.  Every (partner, multipole) product is read once per output channel
+//    that uses it (about 12 GB of L2 reads per apply at the production size).
+//  - subgroup (mode 1): k_fact_radial32L puts up to FLANE channels of one kappa on the lanes of a
+//    warp, each lane holding its channel's vector window in registers and the band entries read
+//    as shared-memory broadcasts (eight FMAs per 16-byte load); k_fact_mu32 (block = FSG output
+//    channels of one mu) streams the union of their (partner, multipole) products once and applies
+//    each to all FSG outputs from registers.  The partners of a channel all have mu +- 1, so the
+//    outputs of one mu share them; ordered by the parity of the orbital l and |kappa|, about half of
+//    the FSG coefficient sets of an item are nonzero at the production size and each product is read
+//    about 3.5 times per apply instead of 30.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <mutex>
 
 #include "device.h"
 #include "kernels.h"
+#include "mbar.cuh"
 
 namespace dg {
 
@@ -189,7 +202,7 @@ __global__ void __launch_bounds__(2 * FTR) k_fact_angular32(OpView A, const floa
         block_reduce_store(dsum, nsum, part_dot, part_nrm, (int64_t)tile * gridDim.x + blockIdx.x);
 }
 
-void launch_fact32(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc, const float2* G, int L,
+void launch_fact32_chan(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc, const float2* G, int L,
                    const float* S, const float* H, int sign, const void* x, float2* Z, const float4* cab, void* y,
                    const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip)
 {
@@ -199,6 +212,349 @@ void launch_fact32(cudaStream_t st, const OpView& A, const RadChunk* rc, int nrc
         k_fact_angular32<<<A.nch, 2 * FTR, 0, st>>>(A, S, H, sign, (const float2*)x, Z, L, cab, (float2*)y,
                                                      (const float2*)bsub, (const float2*)dv, pdot, pnrm, tile,
                                                      skip);
+    }
+}
+
+
+// ---- subgroup form ---------------------------------------------------------------------------
+
+namespace {
+constexpr int RSL = 4;                        // radial slots per thread (radial pass)
+constexpr int RWARP = 8;                      // warps per radial block: RWARP x RSL slots
+constexpr int RSLOTS = RWARP * RSL;           // slots per radial block (half a tile)
+constexpr int GROWS = RSLOTS + 2 * HF;        // rows of G (and of the vectors) the block's slots reach
+constexpr int XW = GROWS + 1;                 // staged vector window stride (float4): conflict-free lanes
+constexpr int OW = RSLOTS + 1;                // staged output stride (float4)
+static_assert(FTR % RSLOTS == 0, "radial blocks tile the radial tile");
+// dynamic shared memory of the radial pass, float4 entries: G^n rows [4][GROWS][BDF], later the
+// vector windows [FLANE][XW] and then the outputs [FLANE][OW] in the same space; the combined bands
+// of the block's two kappas [2][4][RSLOTS][BDF]
+constexpr int RAD_G = 4 * GROWS * BDF, RAD_E = 4 * RSLOTS * BDF, RAD_X = FLANE * XW;
+constexpr int RAD_GX = RAD_G > RAD_X ? RAD_G : RAD_X;
+static_assert(FLANE * OW <= RAD_X, "the output staging fits in the vector staging");
+// the second kappa's bands start one float4 past a 128-byte boundary, so that the two broadcast
+// addresses of a warp holding two chunks fall in different banks
+constexpr int RAD_E1 = RAD_E + 1;
+constexpr size_t RAD_SMEM = (size_t)(RAD_GX + RAD_E1 + RAD_E) * sizeof(float4);
+
+constexpr int FSPLIT = 4;                     // consumer groups of the angular pass, one item each per stage
+constexpr int NRS = 6;                        // its bulk-copy ring stages, FSPLIT items per stage
+constexpr int ITEM_F4 = 4 * FTR + FSG;        // float4 per item: its products, its coefficients
+constexpr uint32_t ITEM_ZB = 4 * FTR * sizeof(float4), ITEM_CB = FSG * sizeof(float4);
+constexpr size_t MU_RING = (size_t)NRS * FSPLIT * ITEM_F4 * sizeof(float4);
+static_assert(FSG % FSPLIT == 0, "outputs split evenly over the consumer groups");
+static_assert((size_t)FSPLIT * FSG * FTR * sizeof(float4) <= MU_RING, "the reduction fits in the ring");
+}  // namespace
+
+// U, V, U', V' at the RSLOTS slots of block (pack, l, part) of the tile.  A pack is one or two kappa
+// chunks whose channels together fill at most the FLANE lanes of a warp.  The block stages, with
+// asynchronous copies all in flight at once, the hi words of the four G^n bands of multipole l at the
+// rows its slots reach, and forms the four combined bands of each chunk's kappa at its slots,
+// es[chunk][beta][slot][d]; then it stages the channels' vector windows (in the space the bands came
+// through).  Lane = channel: each thread takes RSL consecutive slots of its channel and both function
+// types, with its window in registers; the lanes of a chunk read the same band entry (a broadcast;
+// two addresses per warp when it holds two chunks), eight FMAs per 16-byte load.  The products go
+// out through shared memory so that the stores of a channel's rows are coalesced.
+__global__ void __launch_bounds__(RWARP * 32, 2) k_fact_radial32L(OpView A, const RadPack* __restrict__ rp,
+                                                                 const float* __restrict__ Gh, int L,
+                                                                 const float2* __restrict__ x, float2* __restrict__ Z,
+                                                                 int tile, const KState* skip)
+{
+    if (skip && skip->done) return;   // uniform over the grid: the solve already finished
+    extern __shared__ float4 rsm[];
+    float4* Gs = rsm;                  // [n][row][d]; later [lane][XW] windows, then [lane][OW] outputs
+    float4* xs = rsm;
+    float4* es = rsm + RAD_GX;         // [chunk][beta][slot][d], chunk stride RAD_E1
+    __shared__ int s_ch[FLANE], s_kap[FLANE];
+    const RadPack* pk = rp + blockIdx.x;
+    const int n0 = pk->c[0].count, n1c = pk->c[1].count, nl = n0 + n1c;   // lanes of chunk 0, lanes in use
+    const int l = blockIdx.y;
+    const int n1 = A.n1;
+    const int ls0 = blockIdx.z * RSLOTS;       // first slot of the block within the tile
+    const int s0 = tile * FTR + ls0;           // its global slot
+    // G^n at rows s0 - h .. s0 + RSLOTS - 1 + h (zero outside the grid): per n a contiguous range of
+    // GROWS rows, BDF float4 (one 2 x 2 block per diagonal) each
+    const float4* Gl = reinterpret_cast<const float4*>(Gh) + (int64_t)l * 4 * n1 * BDF;
+    for (int n = 0; n < 4; n++) {
+        for (int i = threadIdx.x; i < GROWS * BDF; i += blockDim.x) {
+            const int rr = s0 - HF + i / BDF;
+            const bool in = rr >= 0 && rr < n1;
+            cp_async16z(&Gs[n * GROWS * BDF + i], Gl + ((int64_t)n * n1 + (in ? rr : 0)) * BDF + i % BDF,
+                        in ? 16u : 0u);
+        }
+    }
+    if (threadIdx.x < FLANE) {
+        const int ln = threadIdx.x, k = ln < n0 ? 0 : 1;
+        s_ch[ln] = ln < nl ? A.prec_order[pk->c[k].first + ln - (k ? n0 : 0)] : 0;
+        s_kap[ln] = pk->c[k].kappa;
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    // combined bands of each chunk's kappa: U (G0 + k G2), V (G1 + k G3) at (r, d, t, u); U', V' the
+    // block transposes (G0 + k G1), (G2 + k G3) at (r + d - h, 2h - d, u, t); zero where the row or
+    // the column is outside the grid.  Thread -> (beta, slot, half of the diagonals).
+    {
+        static_assert(RWARP * 32 == 8 * RSLOTS, "one thread per (beta, slot, half)");
+        const int ls = threadIdx.x % RSLOTS, beta = (threadIdx.x / RSLOTS) & 3, dh = threadIdx.x / (4 * RSLOTS);
+        const int na = beta == 0 ? 0 : beta == 1 ? 1 : beta == 2 ? 0 : 2;
+        const int nb = beta == 0 ? 2 : beta == 1 ? 3 : beta == 2 ? 1 : 3;
+        const int r = s0 + ls;
+        for (int k = 0; k < (n1c ? 2 : 1); k++) {
+            const float kap = (float)pk->c[k].kappa;
+            for (int d = dh * 7; d < min(BDF, dh * 7 + 7); d++) {
+                const int rr = r + d - HF;
+                float4 e = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r < n1 && rr >= 0 && rr < n1) {
+                    // Gs row of slot r is ls + h; of column slot rr, ls + d
+                    const int row = beta < 2 ? ls + HF : ls + d, dd = beta < 2 ? d : 2 * HF - d;
+                    const float4 ga = Gs[(na * GROWS + row) * BDF + dd], gb = Gs[(nb * GROWS + row) * BDF + dd];
+                    e = make_float4(fmaf(kap, gb.x, ga.x), fmaf(kap, gb.y, ga.y), fmaf(kap, gb.z, ga.z),
+                                    fmaf(kap, gb.w, ga.w));
+                    if (beta >= 2) e = make_float4(e.x, e.z, e.y, e.w);   // (u, t) -> (t, u)
+                }
+                es[k * RAD_E1 + (beta * RSLOTS + ls) * BDF + d] = e;
+            }
+        }
+    }
+    __syncthreads();   // the G rows are no longer needed: their space takes the vector windows
+    // the channels' vector windows, slots s0 - h .. s0 + RSLOTS - 1 + h, both types (zero outside the
+    // grid; the unused functions are masked when the windows are read)
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    for (int i = threadIdx.x; i < nl * GROWS; i += blockDim.x) {
+        const int cc = i / GROWS, j = i - cc * GROWS, rr = s0 - HF + j;
+        const bool in = rr >= 0 && rr < n1;
+        cp_async16z(&xs[cc * XW + j], x4 + (int64_t)s_ch[cc] * n1 + (in ? rr : 0), in ? 16u : 0u);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool act = lane < nl;
+    const int kap = s_kap[lane];
+    const int sw = s0 + w * RSL;   // the thread's first slot
+    float4 xw[RSL + 2 * HF];       // the thread's window: (x0.re, x0.im, x1.re, x1.im)
+#pragma unroll
+    for (int j = 0; j < RSL + 2 * HF; j++) {
+        float4 v = act ? xs[lane * XW + w * RSL + j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int rr = sw - HF + j;
+        if (!used_f(kap, rr, 0)) { v.x = 0.f; v.y = 0.f; }   // only slot 0 can be unused
+        if (!used_f(kap, rr, 1)) { v.z = 0.f; v.w = 0.f; }
+        xw[j] = v;
+    }
+    __syncthreads();   // xs is free: it takes the outputs from here on
+    float4* Z4 = reinterpret_cast<float4*>(Z);
+    const float4* ek = es + (lane < n0 ? 0 : RAD_E1);
+#pragma unroll 1
+    for (int beta = 0; beta < 4; beta++) {
+        if (act) {
+            float4 acc[RSL];   // (row t = 0 complex, row t = 1 complex)
+#pragma unroll
+            for (int s = 0; s < RSL; s++) acc[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4* eb = ek + (beta * RSLOTS + w * RSL) * BDF;
+#pragma unroll
+            for (int s = 0; s < RSL; s++) {
+#pragma unroll
+                for (int d = 0; d < BDF; d++) {
+                    const float4 e = eb[s * BDF + d];
+                    const float4 xv = xw[s + d];
+                    acc[s].x = fmaf(e.x, xv.x, fmaf(e.y, xv.z, acc[s].x));
+                    acc[s].y = fmaf(e.x, xv.y, fmaf(e.y, xv.w, acc[s].y));
+                    acc[s].z = fmaf(e.z, xv.x, fmaf(e.w, xv.z, acc[s].z));
+                    acc[s].w = fmaf(e.z, xv.y, fmaf(e.w, xv.w, acc[s].w));
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < RSL; s++) xs[lane * OW + w * RSL + s] = acc[s];
+        }
+        __syncthreads();
+        // rows ls0 .. ls0 + RSLOTS - 1 of (channel, l, beta): RSLOTS consecutive float4 per channel
+        for (int i = threadIdx.x; i < nl * RSLOTS; i += blockDim.x) {
+            const int cc = i / RSLOTS, j = i - cc * RSLOTS;
+            Z4[(((int64_t)s_ch[cc] * L + l) * 4 + beta) * FTR + ls0 + j] = xs[cc * OW + j];
+        }
+        __syncthreads();
+    }
+}
+
+// Outputs of subgroup blockIdx.x at the tile's rows: y_a = D^sign x_a + sign sum_items coef . products,
+// then y <- bsub - y and the <dv, y>, ||y||^2 partials (slot tile * nsub + subgroup).  A producer
+// thread copies the items' products (4 KB each: four products x FTR slots, both types) and their FSG
+// coefficient sets into an NRS-deep shared-memory ring with the bulk-copy engine, FSPLIT items per
+// stage ("full" mbarrier per stage completing on the bytes, "empty" one when every consumer warp
+// has released it).  FSPLIT groups of two consumer warps take one item of each stage; a thread holds
+// one slot, both types, and the FSG outputs' sums in registers.  The groups' sums meet in shared
+// memory (over the drained ring) in a fixed order.  Every wait is bounded: on a time-out the block
+// sets *err, lets the copies it issued land, and leaves without storing.
+__global__ void __launch_bounds__(FTR * FSPLIT + 32) k_fact_mu32(OpView A, const float* __restrict__ ST,
+                                                                const float* __restrict__ HT, int sign,
+                                                                const float2* __restrict__ x,
+                                                                const float2* __restrict__ Z,
+                                                                const FactSub* __restrict__ subs,
+                                                                const int* __restrict__ item_off,
+                                                                const float4* __restrict__ item_coef,
+                                                                float2* __restrict__ y,
+                                                                const float2* __restrict__ bsub,
+                                                                const float2* __restrict__ dv, double2* part_dot,
+                                                                double* part_nrm, int tile, const KState* skip,
+                                                                int* err)
+{
+    if (skip && skip->done) return;
+    extern __shared__ float4 msm[];
+    float4* ring = msm;                                                   // [NRS][FSPLIT][ITEM_F4]
+    int* s_off = reinterpret_cast<int*>(msm + NRS * FSPLIT * ITEM_F4);    // the subgroup's item offsets
+    __shared__ uint64_t full[NRS], empty[NRS];
+    __shared__ int fail, issued;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int gfirst = subs[blockIdx.x].first, gcount = subs[blockIdx.x].count;
+    const int nstage = (gcount + FSPLIT - 1) / FSPLIT;
+    if (tid == 0) {
+        for (int q = 0; q < NRS; q++) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 2 * FSPLIT);
+        }
+        mbar_fence_init();
+        fail = 0;
+        issued = 0;
+    }
+    for (int k = tid; k < gcount; k += blockDim.x) s_off[k] = item_off[gfirst + k];
+    __syncthreads();
+    const int ls = tid % FTR, grp = tid / FTR;   // consumers: group grp (warps 2 grp, 2 grp + 1)
+    float4 acc[FSG];
+#pragma unroll
+    for (int j = 0; j < FSG; j++) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (warp == 2 * FSPLIT) {
+        if (lane == 0) {
+            const float4* Z4 = reinterpret_cast<const float4*>(Z);
+            for (int m = 0; m < nstage; m++) {
+                const int s = m % NRS;
+                // the empty barrier orders the consumers' reads of the stage before these copies
+                if (m >= NRS && !mbar_wait_poll(&empty[s], (uint32_t)((m / NRS - 1) & 1))) { fail = 1; break; }
+                const int k0 = m * FSPLIT, nk = min(FSPLIT, gcount - k0);
+                mbar_expect_tx(&full[s], (uint32_t)nk * (ITEM_ZB + ITEM_CB));
+                for (int q = 0; q < nk; q++) {
+                    float4* dst = ring + (s * FSPLIT + q) * ITEM_F4;
+                    bulk_load(dst, Z4 + (int64_t)s_off[k0 + q] * 4 * FTR, ITEM_ZB, &full[s]);
+                    bulk_load(dst + 4 * FTR, item_coef + ((int64_t)gfirst + k0 + q) * FSG, ITEM_CB, &full[s]);
+                }
+                issued = m + 1;
+            }
+        }
+    } else {
+        for (int m = 0; m < nstage; m++) {
+            const int s = m % NRS;
+            if (!mbar_wait_poll(&full[s], (uint32_t)((m / NRS) & 1))) { fail = 1; break; }
+            if (m * FSPLIT + grp < gcount) {
+                const float4* st = ring + (s * FSPLIT + grp) * ITEM_F4;
+                const float4 U = st[ls], V = st[FTR + ls], Up = st[2 * FTR + ls], Vp = st[3 * FTR + ls];
+#pragma unroll
+                for (int j = 0; j < FSG; j++) {
+                    const float4 c = st[4 * FTR + j];   // the same address in every thread: a broadcast
+                    acc[j].x = fmaf(c.x, U.x, fmaf(c.y, V.x, fmaf(c.z, Up.x, fmaf(c.w, Vp.x, acc[j].x))));
+                    acc[j].y = fmaf(c.x, U.y, fmaf(c.y, V.y, fmaf(c.z, Up.y, fmaf(c.w, Vp.y, acc[j].y))));
+                    acc[j].z = fmaf(c.x, U.z, fmaf(c.y, V.z, fmaf(c.z, Up.z, fmaf(c.w, Vp.z, acc[j].z))));
+                    acc[j].w = fmaf(c.x, U.w, fmaf(c.y, V.w, fmaf(c.z, Up.w, fmaf(c.w, Vp.w, acc[j].w))));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
+        }
+    }
+    __syncthreads();
+    if (fail) {
+        if (tid == 0) {
+            atomicExch(err, 1);
+            // copies still in flight target this block's shared memory: give the last ones issued
+            // the same time limit before the block exits
+            for (int m = max(0, issued - NRS); m < issued; m++) mbar_wait(&full[m % NRS], (uint32_t)((m / NRS) & 1));
+        }
+        return;
+    }
+    // every copy issued has been consumed: the ring takes the groups' sums, [grp][j][ls]
+    float4* red = ring;
+    if (warp < 2 * FSPLIT) {
+#pragma unroll
+        for (int j = 0; j < FSG; j++) red[(grp * FSG + j) * FTR + ls] = acc[j];
+    }
+    __syncthreads();
+    const int n1 = A.n1, r = tile * FTR + ls;
+    double2 dsum = make_double2(0, 0);
+    double nsum = 0;
+    if (warp < 2 * FSPLIT && r < n1) {
+        const float st = (float)(sign * A.tau), sg = (float)sign;
+#pragma unroll 1
+        for (int j = grp; j < FSG; j += FSPLIT) {
+            const int a = subs[blockIdx.x].out[j];
+            if (a < 0) continue;
+            float4 cs = red[j * FTR + ls];
+#pragma unroll
+            for (int q = 1; q < FSPLIT; q++) {
+                const float4 o = red[(q * FSG + j) * FTR + ls];
+                cs.x += o.x; cs.y += o.y; cs.z += o.z; cs.w += o.w;
+            }
+            const int ka = A.ch_kappa[a], ks = A.ch_kslot[a];
+            if (!used_f(ka, r, 0)) { cs.x = 0.f; cs.y = 0.f; }   // the coupling is zero at unused rows
+            if (!used_f(ka, r, 1)) { cs.z = 0.f; cs.w = 0.f; }
+            // diagonal block (S + sign i tau H0) x_a; bands with the rows innermost: diagonal d of row
+            // r is the float4 at (ks BDF + d) n1 + r
+            const float4* Sk = reinterpret_cast<const float4*>(ST) + (int64_t)ks * BDF * n1 + r;
+            const float4* Hk = reinterpret_cast<const float4*>(HT) + (int64_t)ks * BDF * n1 + r;
+            const float4* xa = reinterpret_cast<const float4*>(x) + (int64_t)a * n1;
+            float2 d0 = make_float2(0.f, 0.f), d1 = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int d = 0; d < BDF; d++) {
+                const int rr = r + d - HF;
+                if (rr < 0 || rr >= n1) continue;
+                const float4 xv = xa[rr], sv = Sk[(int64_t)d * n1], hv = Hk[(int64_t)d * n1];
+                const float h00 = st * hv.x, h01 = st * hv.y, h10 = st * hv.z, h11 = st * hv.w;
+                d0.x += sv.x * xv.x + sv.y * xv.z - (h00 * xv.y + h01 * xv.w);
+                d0.y += sv.x * xv.y + sv.y * xv.w + (h00 * xv.x + h01 * xv.z);
+                d1.x += sv.z * xv.x + sv.w * xv.z - (h10 * xv.y + h11 * xv.w);
+                d1.y += sv.z * xv.y + sv.w * xv.w + (h10 * xv.x + h11 * xv.z);
+            }
+            float4 v = make_float4(d0.x + sg * cs.x, d0.y + sg * cs.y, d1.x + sg * cs.z, d1.y + sg * cs.w);
+            const int64_t o = (int64_t)a * n1 + r;
+            if (bsub) {
+                const float4 bb = reinterpret_cast<const float4*>(bsub)[o];
+                v = make_float4(bb.x - v.x, bb.y - v.y, bb.z - v.z, bb.w - v.w);
+            }
+            reinterpret_cast<float4*>(y)[o] = v;
+            if (dv) {
+                const float4 wv = reinterpret_cast<const float4*>(dv)[o];
+                dsum.x += (double)wv.x * v.x + (double)wv.y * v.y + (double)wv.z * v.z + (double)wv.w * v.w;
+                dsum.y += (double)wv.x * v.y - (double)wv.y * v.x + (double)wv.z * v.w - (double)wv.w * v.z;
+            }
+            nsum += (double)v.x * v.x + (double)v.y * v.y + (double)v.z * v.z + (double)v.w * v.w;
+        }
+    }
+    if (part_dot || part_nrm)
+        block_reduce_store(dsum, nsum, part_dot, part_nrm, (int64_t)tile * gridDim.x + blockIdx.x);
+}
+
+// The limits only grow: an operator with fewer items per subgroup must not lower the limit that a
+// larger operator of the same process launches with.
+cudaError_t fact_sub_prepare(int max_items)
+{
+    static std::mutex mu;
+    static size_t mu_limit = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    cudaError_t e = cudaFuncSetAttribute(k_fact_radial32L, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RAD_SMEM);
+    if (e != cudaSuccess) return e;
+    mu_limit = std::max(mu_limit, MU_RING + (size_t)max_items * sizeof(int));
+    return cudaFuncSetAttribute(k_fact_mu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_limit);
+}
+
+void launch_fact32_sub(cudaStream_t st, const OpView& A, const RadPack* rl, int nrl, const FactSub* subs, int nsub,
+                       int max_items, const int* item_off, const float4* item_coef, const float* Gh, int L,
+                       const float* ST, const float* HT, int sign, const void* x, float2* Z, void* y,
+                       const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip, int* err)
+{
+    const int ntile = (A.n1 + FTR - 1) / FTR;
+    const dim3 rgrid(nrl, L, FTR / RSLOTS);
+    const size_t msmem = MU_RING + (size_t)max_items * sizeof(int);
+    for (int tile = 0; tile < ntile; tile++) {
+        k_fact_radial32L<<<rgrid, RWARP * 32, RAD_SMEM, st>>>(A, rl, Gh, L, (const float2*)x, Z, tile, skip);
+        k_fact_mu32<<<nsub, FTR * FSPLIT + 32, msmem, st>>>(A, ST, HT, sign, (const float2*)x, Z, subs, item_off,
+                                                            item_coef, (float2*)y, (const float2*)bsub,
+                                                            (const float2*)dv, pdot, pnrm, tile, skip, err);
     }
 }
 

@@ -31,6 +31,7 @@
 #include "df64.cuh"
 #include "device.h"
 #include "kernels.h"
+#include "mbar.cuh"
 
 namespace dg {
 
@@ -45,63 +46,6 @@ constexpr int ROWF = BDO * 4;    // floats per stored row of one pair
 constexpr int NOUT = TR + 2 * HO;
 static_assert(NOUT == NT, "one transposed output row per thread");
 constexpr int STAGE32 = TR * ROWF + NOUT * 4;   // floats per complex64 ring stage: coupling rows, x_b row window
-constexpr long long WAIT_CYCLES = 4000000000LL;   // ~2 s at 2 GHz: bulk-copy wait limit
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// try_wait with a suspend-time hint: a waiting warp sleeps until the phase completes (or the hint
-// runs out) instead of spinning, so warps that wait leave the issue slots to those that compute
-constexpr uint32_t SUSPEND_NS = 20000;
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity), "r"(SUSPEND_NS)
-        : "memory");
-    return ok != 0;
-}
-
-// wait for a ring stage; false after the time limit (the caller records the failure)
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit = WAIT_CYCLES)
-{
-    long long t0 = clock64();
-    while (!mbar_test(bar, parity))
-        if (clock64() - t0 > limit) return false;
-    return true;
-}
-
 }  // namespace
 
 // Self-test of the bounded wait: one block waits on an mbarrier phase that nothing completes, with

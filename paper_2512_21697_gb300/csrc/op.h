@@ -34,6 +34,7 @@ struct AsmSet {
     double* s = nullptr;
     float2 *Gdf = nullptr, *Kdf = nullptr, *KTdf = nullptr;
     float *Wh = nullptr, *Wl = nullptr;
+    float* Ghi = nullptr;   // hi words of Gdf as plain floats (factorised apply, subgroup form)
 };
 
 }  // namespace dg
@@ -75,10 +76,17 @@ struct dirac_op {
     float *Wh = nullptr, *Wl = nullptr;   // coupling hi words (also the FP32 values) and lo words
     float4* cab_df = nullptr;
     // factorised complex64 apply of the inner solve (dirac_op_set_factorised)
-    bool fact32 = false;
+    int fact32 = 0;              // 0 stored coupling, 1 subgroup form, 2 per-channel form
     dg::RadChunk* rad_chunks = nullptr;
     int nrad = 0;
+    dg::RadPack* rad_lanes = nullptr;    // subgroup form: pairs of kappa chunks sharing FLANE lanes
+    int nrad_lanes = 0;
+    dg::FactSub* fsub = nullptr;         // subgroup form: FSG outputs of one mu and their items
+    int nfsub = 0, fsub_max = 1;         // subgroups, the largest item count
+    int* fitem_off = nullptr;            // item -> partner * L + multipole
+    float4* fitem_coef = nullptr;        // item -> FSG coefficient sets (U, V, U', V')
     float2* Zf = nullptr;        // band products of one radial tile
+    float* Ghi = nullptr;        // the current buffer set's G hi words (subgroup form)
     // grouped double-float assembly (null when a group has more than ASM_MAX_NL multipoles)
     dg::AsmChunk* asm_chunks = nullptr;
     int asm_nchunks = 0;

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # (workload, precision, driver, factorised): the mixed paths use the owner/gather passes and the
 # grouped assembly; "run" is the captured graph driver
 CASES = [("tiny", 2, "step", 0), ("small", 2, "step", 0), ("tail", 2, "step", 0), ("slice", 2, "run", 0),
-         ("small", 1, "step", 0), ("tail", 1, "run", 0), ("small", 2, "step", 1), ("order5", 2, "step", 0)]
+         ("small", 1, "step", 0), ("tail", 1, "run", 0), ("small", 2, "step", 1), ("tail", 2, "run", 2),
+         ("order5", 2, "step", 0)]
 
 CHILD = r"""
 import json, sys
@@ -31,7 +32,7 @@ for name, prec, drv, fact in json.loads(sys.argv[2]):
     bas = B.Basis(cfg)
     op = B.Operator(bas, cfg, tol=1e-12, precision=prec, max_iter=1000, tol_inner=1e-5, max_outer=30)
     if fact:
-        op.set_factorised(1)
+        op.set_factorised(fact)
     psi = torch.from_numpy(W.random_state(bas.n, 11)).cuda()
     hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device="cuda")
     t = 0.25 * cfg["n_cycles"] * 2 * np.pi / cfg["omega"]
@@ -53,7 +54,7 @@ def _run_release(name, prec, drv, fact):
     bas = B.Basis(cfg)
     op = B.Operator(bas, cfg, tol=1e-12, precision=prec, max_iter=1000, tol_inner=1e-5, max_outer=30)
     if fact:
-        op.set_factorised(1)
+        op.set_factorised(fact)
     psi = torch.from_numpy(W.random_state(bas.n, 11)).cuda()
     hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device="cuda")
     t = 0.25 * cfg["n_cycles"] * 2 * np.pi / cfg["omega"]

@@ -157,12 +157,14 @@ def test_apply32_matches_oracle_slice(oracle_mod):
     print("apply32 slice: max err / bound = %.3g" % worst)
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("name", ["tiny", "small", "tail", "wide_l"])
-def test_factorised_apply32_matches_oracle(oracle_mod, name):
+def test_factorised_apply32_matches_oracle(oracle_mod, name, mode):
     # the factorised complex64 apply (coupling from the radial bands and the angular coefficients,
-    # never stored) against the oracle, normwise bar 64 (m + 4) u max (|A| |x|)
+    # never stored; mode 1 subgroup form, 2 per-channel form) against the oracle, normwise bar
+    # 64 (m + 4) u max (|A| |x|)
     c = Case32(W.WORKLOADS[name], oracle_mod, precision=2)
-    c.op.set_factorised(True)
+    c.op.set_factorised(mode)
     x = c.random(33)
     xd = c.to_dev32(x)
     x = c.from_dev(xd)
@@ -178,7 +180,7 @@ def test_factorised_apply32_matches_oracle(oracle_mod, name):
             err = np.maximum(np.abs(y.real - ref.real), np.abs(y.imag - ref.imag)).max()
             assert err <= 64 * (m + 4) * U32 * scale, (sign, t, err / scale)
             worst = max(worst, err / ((m + 4) * U32 * scale))
-    print("factorised apply32 %s: max err / ((m+4) u max|A||x|) = %.3g" % (name, worst))
+    print("factorised apply32 %s mode %d: max err / ((m+4) u max|A||x|) = %.3g" % (name, mode, worst))
 
 
 @pytest.mark.parametrize("sched", [0, 1, 2, 3])
@@ -351,6 +353,17 @@ def test_production_apply32_sampled_rows(oracle_mod):
         err = np.abs(y[rows] - ref).max()
         assert err <= (2 * m + 8) * U32 * 4 * np.abs(y).max(), (sign, err / np.abs(y).max())
         print("production apply32 sign %+d: max err / max|y| = %.3g" % (sign, err / np.abs(y).max()))
+    # the factorised apply in its subgroup form (16 radial tiles, the largest subgroups), with the
+    # factor 64 of the factorised bar above for the kappa-weighted band terms
+    op.set_factorised(1)
+    for sign in (+1, -1):
+        t = 0.43 * T
+        op.apply32(sign, t, xd, yd)
+        y = yd.cpu().numpy().astype(np.complex128)[perm]
+        ref = orc.apply_rows(t, sign, x, ch, idx)
+        err = np.abs(y[rows] - ref).max()
+        assert err <= 64 * (2 * m + 8) * U32 * 4 * np.abs(y).max(), (sign, err / np.abs(y).max())
+        print("production factorised apply32 sign %+d: max err / max|y| = %.3g" % (sign, err / np.abs(y).max()))
 
 
 def test_production_residual_sampled_rows(oracle_mod):
