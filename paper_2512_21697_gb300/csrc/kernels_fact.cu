@@ -237,13 +237,9 @@ static_assert(FLANE * OW <= RAD_X, "the output staging fits in the vector stagin
 constexpr int RAD_E1 = RAD_E + 1;
 constexpr size_t RAD_SMEM = (size_t)(RAD_GX + RAD_E1 + RAD_E) * sizeof(float4);
 
-constexpr int FSPLIT = 4;                     // consumer groups of the angular pass, one item each per stage
-constexpr int NRS = 6;                        // its bulk-copy ring stages, FSPLIT items per stage
-constexpr int ITEM_F4 = 4 * FTR + FSG;        // float4 per item: its products, its coefficients
-constexpr uint32_t ITEM_ZB = 4 * FTR * sizeof(float4), ITEM_CB = FSG * sizeof(float4);
-constexpr size_t MU_RING = (size_t)NRS * FSPLIT * ITEM_F4 * sizeof(float4);
-static_assert(FSG % FSPLIT == 0, "outputs split evenly over the consumer groups");
-static_assert((size_t)FSPLIT * FSG * FTR * sizeof(float4) <= MU_RING, "the reduction fits in the ring");
+constexpr int FSPLIT = 4;                     // threads per slot in the angular pass (items split)
+constexpr int FPIPE = 4;                      // items each thread has in flight
+static_assert(FSG % FSPLIT == 0, "outputs split evenly over the item splits");
 }  // namespace
 
 // U, V, U', V' at the RSLOTS slots of block (pack, l, part) of the tile.  A pack is one or two kappa
@@ -376,109 +372,81 @@ __global__ void __launch_bounds__(RWARP * 32, 2) k_fact_radial32L(OpView A, cons
 }
 
 // Outputs of subgroup blockIdx.x at the tile's rows: y_a = D^sign x_a + sign sum_items coef . products,
-// then y <- bsub - y and the <dv, y>, ||y||^2 partials (slot tile * nsub + subgroup).  A producer
-// thread copies the items' products (4 KB each: four products x FTR slots, both types) and their FSG
-// coefficient sets into an NRS-deep shared-memory ring with the bulk-copy engine, FSPLIT items per
-// stage ("full" mbarrier per stage completing on the bytes, "empty" one when every consumer warp
-// has released it).  FSPLIT groups of two consumer warps take one item of each stage; a thread holds
-// one slot, both types, and the FSG outputs' sums in registers.  The groups' sums meet in shared
-// memory (over the drained ring) in a fixed order.  Every wait is bounded: on a time-out the block
-// sets *err, lets the copies it issued land, and leaves without storing.
-__global__ void __launch_bounds__(FTR * FSPLIT + 32) k_fact_mu32(OpView A, const float* __restrict__ ST,
-                                                                const float* __restrict__ HT, int sign,
-                                                                const float2* __restrict__ x,
-                                                                const float2* __restrict__ Z,
-                                                                const FactSub* __restrict__ subs,
-                                                                const int* __restrict__ item_off,
-                                                                const float4* __restrict__ item_coef,
-                                                                float2* __restrict__ y,
-                                                                const float2* __restrict__ bsub,
-                                                                const float2* __restrict__ dv, double2* part_dot,
-                                                                double* part_nrm, int tile, const KState* skip,
-                                                                int* err)
+// then y <- bsub - y and the <dv, y>, ||y||^2 partials (slot tile * nsub + subgroup).  The block first
+// copies its items' coefficient sets (FSG float4 each) and offsets into shared memory.  Thread
+// (split grp, slot ls) takes items grp, grp + FSPLIT, ... with FPIPE of them in flight: the four
+// products of an item at its slot (both types, 64 bytes) are loaded FPIPE items ahead of their use,
+// so each thread keeps 256 bytes of loads outstanding.  The splits' sums meet in shared memory in a
+// fixed order.
+__global__ void __launch_bounds__(FTR * FSPLIT, 2) k_fact_mu32(OpView A, const float* __restrict__ ST,
+                                                              const float* __restrict__ HT, int sign,
+                                                              const float2* __restrict__ x,
+                                                              const float2* __restrict__ Z,
+                                                              const FactSub* __restrict__ subs,
+                                                              const int* __restrict__ item_off,
+                                                              const float4* __restrict__ item_coef,
+                                                              float2* __restrict__ y,
+                                                              const float2* __restrict__ bsub,
+                                                              const float2* __restrict__ dv, double2* part_dot,
+                                                              double* part_nrm, int tile, const KState* skip)
 {
     if (skip && skip->done) return;
     extern __shared__ float4 msm[];
-    float4* ring = msm;                                                   // [NRS][FSPLIT][ITEM_F4]
-    int* s_off = reinterpret_cast<int*>(msm + NRS * FSPLIT * ITEM_F4);    // the subgroup's item offsets
-    __shared__ uint64_t full[NRS], empty[NRS];
-    __shared__ int fail, issued;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ float4 red[FSPLIT * FSG * FTR];
+    const int tid = threadIdx.x;
     const int gfirst = subs[blockIdx.x].first, gcount = subs[blockIdx.x].count;
-    const int nstage = (gcount + FSPLIT - 1) / FSPLIT;
-    if (tid == 0) {
-        for (int q = 0; q < NRS; q++) {
-            mbar_init(&full[q], 1);
-            mbar_init(&empty[q], 2 * FSPLIT);
-        }
-        mbar_fence_init();
-        fail = 0;
-        issued = 0;
-    }
+    float4* s_coef = msm;                                           // [item][FSG]
+    int* s_off = reinterpret_cast<int*>(msm + (size_t)gcount * FSG);  // [item]
+    for (int k = tid; k < gcount * FSG; k += blockDim.x) cp_async16z(&s_coef[k], item_coef + (int64_t)gfirst * FSG + k, 16u);
     for (int k = tid; k < gcount; k += blockDim.x) s_off[k] = item_off[gfirst + k];
+    cp_async_wait_all();
     __syncthreads();
-    const int ls = tid % FTR, grp = tid / FTR;   // consumers: group grp (warps 2 grp, 2 grp + 1)
+    const int ls = tid % FTR, grp = tid / FTR;
     float4 acc[FSG];
 #pragma unroll
     for (int j = 0; j < FSG; j++) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (warp == 2 * FSPLIT) {
-        if (lane == 0) {
-            const float4* Z4 = reinterpret_cast<const float4*>(Z);
-            for (int m = 0; m < nstage; m++) {
-                const int s = m % NRS;
-                // the empty barrier orders the consumers' reads of the stage before these copies
-                if (m >= NRS && !mbar_wait_poll(&empty[s], (uint32_t)((m / NRS - 1) & 1))) { fail = 1; break; }
-                const int k0 = m * FSPLIT, nk = min(FSPLIT, gcount - k0);
-                mbar_expect_tx(&full[s], (uint32_t)nk * (ITEM_ZB + ITEM_CB));
-                for (int q = 0; q < nk; q++) {
-                    float4* dst = ring + (s * FSPLIT + q) * ITEM_F4;
-                    bulk_load(dst, Z4 + (int64_t)s_off[k0 + q] * 4 * FTR, ITEM_ZB, &full[s]);
-                    bulk_load(dst + 4 * FTR, item_coef + ((int64_t)gfirst + k0 + q) * FSG, ITEM_CB, &full[s]);
-                }
-                issued = m + 1;
-            }
+    const float4* Zt = reinterpret_cast<const float4*>(Z) + ls;
+    float4 B[FPIPE][4];   // the products of the items in flight: (U, V, U', V') at the thread's slot
+#pragma unroll
+    for (int q = 0; q < FPIPE; q++) {
+        const int k = grp + q * FSPLIT;
+        if (k < gcount) {
+            const float4* z = Zt + (int64_t)s_off[k] * 4 * FTR;
+#pragma unroll
+            for (int b = 0; b < 4; b++) B[q][b] = __ldcg(z + b * FTR);
         }
-    } else {
-        for (int m = 0; m < nstage; m++) {
-            const int s = m % NRS;
-            if (!mbar_wait_poll(&full[s], (uint32_t)((m / NRS) & 1))) { fail = 1; break; }
-            if (m * FSPLIT + grp < gcount) {
-                const float4* st = ring + (s * FSPLIT + grp) * ITEM_F4;
-                const float4 U = st[ls], V = st[FTR + ls], Up = st[2 * FTR + ls], Vp = st[3 * FTR + ls];
+    }
+    for (int k0 = grp; k0 < gcount; k0 += FPIPE * FSPLIT) {
+#pragma unroll
+        for (int q = 0; q < FPIPE; q++) {
+            const int k = k0 + q * FSPLIT;
+            if (k < gcount) {
+                const float4 U = B[q][0], V = B[q][1], Up = B[q][2], Vp = B[q][3];
+                const int kn = k + FPIPE * FSPLIT;   // refill the slot with the item FPIPE rounds ahead
+                if (kn < gcount) {
+                    const float4* z = Zt + (int64_t)s_off[kn] * 4 * FTR;
+#pragma unroll
+                    for (int b = 0; b < 4; b++) B[q][b] = __ldcg(z + b * FTR);
+                }
+                const float4* cf = s_coef + (int64_t)k * FSG;
 #pragma unroll
                 for (int j = 0; j < FSG; j++) {
-                    const float4 c = st[4 * FTR + j];   // the same address in every thread: a broadcast
+                    const float4 c = cf[j];   // the same address in every thread: a broadcast
                     acc[j].x = fmaf(c.x, U.x, fmaf(c.y, V.x, fmaf(c.z, Up.x, fmaf(c.w, Vp.x, acc[j].x))));
                     acc[j].y = fmaf(c.x, U.y, fmaf(c.y, V.y, fmaf(c.z, Up.y, fmaf(c.w, Vp.y, acc[j].y))));
                     acc[j].z = fmaf(c.x, U.z, fmaf(c.y, V.z, fmaf(c.z, Up.z, fmaf(c.w, Vp.z, acc[j].z))));
                     acc[j].w = fmaf(c.x, U.w, fmaf(c.y, V.w, fmaf(c.z, Up.w, fmaf(c.w, Vp.w, acc[j].w))));
                 }
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&empty[s]);   // this warp is done with stage s
         }
     }
-    __syncthreads();
-    if (fail) {
-        if (tid == 0) {
-            atomicExch(err, 1);
-            // copies still in flight target this block's shared memory: give the last ones issued
-            // the same time limit before the block exits
-            for (int m = max(0, issued - NRS); m < issued; m++) mbar_wait(&full[m % NRS], (uint32_t)((m / NRS) & 1));
-        }
-        return;
-    }
-    // every copy issued has been consumed: the ring takes the groups' sums, [grp][j][ls]
-    float4* red = ring;
-    if (warp < 2 * FSPLIT) {
 #pragma unroll
-        for (int j = 0; j < FSG; j++) red[(grp * FSG + j) * FTR + ls] = acc[j];
-    }
+    for (int j = 0; j < FSG; j++) red[(grp * FSG + j) * FTR + ls] = acc[j];
     __syncthreads();
     const int n1 = A.n1, r = tile * FTR + ls;
     double2 dsum = make_double2(0, 0);
     double nsum = 0;
-    if (warp < 2 * FSPLIT && r < n1) {
+    if (r < n1) {
         const float st = (float)(sign * A.tau), sg = (float)sign;
 #pragma unroll 1
         for (int j = grp; j < FSG; j += FSPLIT) {
@@ -529,6 +497,9 @@ __global__ void __launch_bounds__(FTR * FSPLIT + 32) k_fact_mu32(OpView A, const
         block_reduce_store(dsum, nsum, part_dot, part_nrm, (int64_t)tile * gridDim.x + blockIdx.x);
 }
 
+// dynamic shared memory of the angular pass for a subgroup of n items: coefficient sets and offsets
+static size_t mu_smem(int n) { return (size_t)n * (FSG * sizeof(float4) + sizeof(int)); }
+
 // The limits only grow: an operator with fewer items per subgroup must not lower the limit that a
 // larger operator of the same process launches with.
 cudaError_t fact_sub_prepare(int max_items)
@@ -538,7 +509,7 @@ cudaError_t fact_sub_prepare(int max_items)
     std::lock_guard<std::mutex> lock(mu);
     cudaError_t e = cudaFuncSetAttribute(k_fact_radial32L, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RAD_SMEM);
     if (e != cudaSuccess) return e;
-    mu_limit = std::max(mu_limit, MU_RING + (size_t)max_items * sizeof(int));
+    mu_limit = std::max(mu_limit, mu_smem(max_items));
     return cudaFuncSetAttribute(k_fact_mu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_limit);
 }
 
@@ -549,12 +520,12 @@ void launch_fact32_sub(cudaStream_t st, const OpView& A, const RadPack* rl, int 
 {
     const int ntile = (A.n1 + FTR - 1) / FTR;
     const dim3 rgrid(nrl, L, FTR / RSLOTS);
-    const size_t msmem = MU_RING + (size_t)max_items * sizeof(int);
+    const size_t msmem = mu_smem(max_items);
     for (int tile = 0; tile < ntile; tile++) {
         k_fact_radial32L<<<rgrid, RWARP * 32, RAD_SMEM, st>>>(A, rl, Gh, L, (const float2*)x, Z, tile, skip);
-        k_fact_mu32<<<nsub, FTR * FSPLIT + 32, msmem, st>>>(A, ST, HT, sign, (const float2*)x, Z, subs, item_off,
-                                                            item_coef, (float2*)y, (const float2*)bsub,
-                                                            (const float2*)dv, pdot, pnrm, tile, skip, err);
+        k_fact_mu32<<<nsub, FTR * FSPLIT, msmem, st>>>(A, ST, HT, sign, (const float2*)x, Z, subs, item_off,
+                                                       item_coef, (float2*)y, (const float2*)bsub, (const float2*)dv,
+                                                       pdot, pnrm, tile, skip);
     }
 }
 
