@@ -144,7 +144,7 @@ void k_apply_launch(dirac_op* op, const Krylov& K, int sign, const void* x, void
     else if (op->fact32 == 1)
         launch_fact32_sub(op->st, op->ov, op->rad_lanes, op->nrad_lanes, op->fsub, op->nfsub, op->fsub_max,
                           op->fitem_off, op->fitem_coef, op->Ghi, op->pv.L, op->S32T, op->H32T, sign, x, op->Zf, y, bsub, dv,
-                          pdot, pnrm, skip, op->dev_err);
+                          pdot, pnrm, skip);
     else if (op->fact32 == 2)
         launch_fact32_chan(op->st, op->ov, op->rad_chunks, op->nrad, op->Gdf, op->pv.L, (const float*)K.S,
                            (const float*)K.H, sign, x, op->Zf, op->cab_df, y, bsub, dv, pdot, pnrm, skip);
@@ -1385,7 +1385,8 @@ extern "C" dirac_status dirac_op_set_factorised(dirac_op* op, int enable)
         op->Ghi = op->aset[op->acur].Ghi;
     }
     if (enable && !op->Zf) {
-        dirac_status e = dev_alloc(op, &op->Zf, (size_t)op->ov.nch * op->pv.L * 4 * FTR * 2);
+        // products of two radial tiles (the subgroup form forms tile t + 1 while it combines tile t)
+        dirac_status e = dev_alloc(op, &op->Zf, (size_t)2 * op->ov.nch * op->pv.L * 4 * FTR * 2);
         if (e) return e;
     }
     op->fact32 = enable;

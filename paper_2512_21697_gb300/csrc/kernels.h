@@ -158,7 +158,7 @@ cudaError_t fact_sub_prepare(int max_items);   // dynamic shared-memory limits (
 void launch_fact32_sub(cudaStream_t st, const OpView& A, const RadPack* rl, int nrl, const FactSub* subs, int nsub,
                        int max_items, const int* item_off, const float4* item_coef, const float* Gh, int L,
                        const float* ST, const float* HT, int sign, const void* x, float2* Z, void* y,
-                       const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip, int* err);
+                       const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip);
 
 // learned-guess network forward on the fifth-generation tensor cores (tcgen05, TMEM accumulators)
 size_t guess_forward_tc05_smem();

@@ -251,22 +251,18 @@ static_assert(FSG % FSPLIT == 0, "outputs split evenly over the item splits");
 // types, with its window in registers; the lanes of a chunk read the same band entry (a broadcast;
 // two addresses per warp when it holds two chunks), eight FMAs per 16-byte load.  The products go
 // out through shared memory so that the stores of a channel's rows are coalesced.
-__global__ void __launch_bounds__(RWARP * 32, 2) k_fact_radial32L(OpView A, const RadPack* __restrict__ rp,
-                                                                 const float* __restrict__ Gh, int L,
-                                                                 const float2* __restrict__ x, float2* __restrict__ Z,
-                                                                 int tile, const KState* skip)
+__device__ __forceinline__ void fact_radial_block(const OpView& A, const RadPack* __restrict__ rp,
+                                                  const float* __restrict__ Gh, int L, const float2* __restrict__ x,
+                                                  float2* __restrict__ Z, int tile, int pack, int l, int part,
+                                                  float4* rsm, int* s_ch, int* s_kap)
 {
-    if (skip && skip->done) return;   // uniform over the grid: the solve already finished
-    extern __shared__ float4 rsm[];
     float4* Gs = rsm;                  // [n][row][d]; later [lane][XW] windows, then [lane][OW] outputs
     float4* xs = rsm;
     float4* es = rsm + RAD_GX;         // [chunk][beta][slot][d], chunk stride RAD_E1
-    __shared__ int s_ch[FLANE], s_kap[FLANE];
-    const RadPack* pk = rp + blockIdx.x;
+    const RadPack* pk = rp + pack;
     const int n0 = pk->c[0].count, n1c = pk->c[1].count, nl = n0 + n1c;   // lanes of chunk 0, lanes in use
-    const int l = blockIdx.y;
     const int n1 = A.n1;
-    const int ls0 = blockIdx.z * RSLOTS;       // first slot of the block within the tile
+    const int ls0 = part * RSLOTS;             // first slot of the block within the tile
     const int s0 = tile * FTR + ls0;           // its global slot
     // G^n at rows s0 - h .. s0 + RSLOTS - 1 + h (zero outside the grid): per n a contiguous range of
     // GROWS rows, BDF float4 (one 2 x 2 block per diagonal) each
@@ -371,32 +367,26 @@ __global__ void __launch_bounds__(RWARP * 32, 2) k_fact_radial32L(OpView A, cons
     }
 }
 
-// Outputs of subgroup blockIdx.x at the tile's rows: y_a = D^sign x_a + sign sum_items coef . products,
+// Outputs of subgroup sub at the tile's rows: y_a = D^sign x_a + sign sum_items coef . products,
 // then y <- bsub - y and the <dv, y>, ||y||^2 partials (slot tile * nsub + subgroup).  The block first
 // copies its items' coefficient sets (FSG float4 each) and offsets into shared memory.  Thread
 // (split grp, slot ls) takes items grp, grp + FSPLIT, ... with FPIPE of them in flight: the four
 // products of an item at its slot (both types, 64 bytes) are loaded FPIPE items ahead of their use,
 // so each thread keeps 256 bytes of loads outstanding.  The splits' sums meet in shared memory in a
 // fixed order.
-__global__ void __launch_bounds__(FTR * FSPLIT, 2) k_fact_mu32(OpView A, const float* __restrict__ ST,
-                                                              const float* __restrict__ HT, int sign,
-                                                              const float2* __restrict__ x,
-                                                              const float2* __restrict__ Z,
-                                                              const FactSub* __restrict__ subs,
-                                                              const int* __restrict__ item_off,
-                                                              const float4* __restrict__ item_coef,
-                                                              float2* __restrict__ y,
-                                                              const float2* __restrict__ bsub,
-                                                              const float2* __restrict__ dv, double2* part_dot,
-                                                              double* part_nrm, int tile, const KState* skip)
+__device__ __forceinline__ void fact_mu_block(const OpView& A, const float* __restrict__ ST,
+                                              const float* __restrict__ HT, int sign, const float2* __restrict__ x,
+                                              const float2* __restrict__ Z, const FactSub* __restrict__ subs,
+                                              const int* __restrict__ item_off, const float4* __restrict__ item_coef,
+                                              float2* __restrict__ y, const float2* __restrict__ bsub,
+                                              const float2* __restrict__ dv, double2* part_dot, double* part_nrm,
+                                              int tile, int sub, int nsub, float4* msm)
 {
-    if (skip && skip->done) return;
-    extern __shared__ float4 msm[];
-    __shared__ float4 red[FSPLIT * FSG * FTR];
+    float4* red = msm;                                              // [split][FSG][FTR]
     const int tid = threadIdx.x;
-    const int gfirst = subs[blockIdx.x].first, gcount = subs[blockIdx.x].count;
-    float4* s_coef = msm;                                           // [item][FSG]
-    int* s_off = reinterpret_cast<int*>(msm + (size_t)gcount * FSG);  // [item]
+    const int gfirst = subs[sub].first, gcount = subs[sub].count;
+    float4* s_coef = msm + FSPLIT * FSG * FTR;                      // [item][FSG]
+    int* s_off = reinterpret_cast<int*>(s_coef + (size_t)gcount * FSG);  // [item]
     for (int k = tid; k < gcount * FSG; k += blockDim.x) cp_async16z(&s_coef[k], item_coef + (int64_t)gfirst * FSG + k, 16u);
     for (int k = tid; k < gcount; k += blockDim.x) s_off[k] = item_off[gfirst + k];
     cp_async_wait_all();
@@ -450,7 +440,7 @@ __global__ void __launch_bounds__(FTR * FSPLIT, 2) k_fact_mu32(OpView A, const f
         const float st = (float)(sign * A.tau), sg = (float)sign;
 #pragma unroll 1
         for (int j = grp; j < FSG; j += FSPLIT) {
-            const int a = subs[blockIdx.x].out[j];
+            const int a = subs[sub].out[j];
             if (a < 0) continue;
             float4 cs = red[j * FTR + ls];
 #pragma unroll
@@ -494,38 +484,80 @@ __global__ void __launch_bounds__(FTR * FSPLIT, 2) k_fact_mu32(OpView A, const f
         }
     }
     if (part_dot || part_nrm)
-        block_reduce_store(dsum, nsum, part_dot, part_nrm, (int64_t)tile * gridDim.x + blockIdx.x);
+        block_reduce_store(dsum, nsum, part_dot, part_nrm, (int64_t)tile * nsub + sub);
 }
 
-// dynamic shared memory of the angular pass for a subgroup of n items: coefficient sets and offsets
-static size_t mu_smem(int n) { return (size_t)n * (FSG * sizeof(float4) + sizeof(int)); }
+// One launch per radial tile t = -1 .. ntile - 1: blocks 0 .. nsub_t - 1 run the angular pass of tile
+// t (products in Z[t mod 2]), the others the radial pass of tile t + 1 (into Z[(t + 1) mod 2]).  The
+// two passes are latency-bound with little issue pressure, so the SMs interleave them; the launch
+// boundary orders each tile's products before their readers, and the products of tile t - 1 (read
+// in launch t - 1) before they are overwritten by launch t.  Angular blocks come first (the longer
+// ones, heaviest subgroups first).
+__global__ void __launch_bounds__(RWARP * 32, 2) k_fact_tile32(OpView A, const RadPack* __restrict__ rp, int nrp,
+                                                              const FactSub* __restrict__ subs, int nsub, int nsub_t,
+                                                              const int* __restrict__ item_off,
+                                                              const float4* __restrict__ item_coef,
+                                                              const float* __restrict__ Gh, int L,
+                                                              const float* __restrict__ ST, const float* __restrict__ HT,
+                                                              int sign, const float2* __restrict__ x,
+                                                              const float2* __restrict__ Za, float2* __restrict__ Zr,
+                                                              float2* __restrict__ y, const float2* __restrict__ bsub,
+                                                              const float2* __restrict__ dv, double2* part_dot,
+                                                              double* part_nrm, int tile, const KState* skip)
+{
+    static_assert(RWARP * 32 == FTR * FSPLIT, "both passes run 256-thread blocks");
+    if (skip && skip->done) return;   // uniform over the grid: the solve already finished
+    extern __shared__ float4 fsm[];
+    __shared__ int s_ch[FLANE], s_kap[FLANE];
+    const int b = blockIdx.x;
+    if (b < nsub_t) {
+        fact_mu_block(A, ST, HT, sign, x, Za, subs, item_off, item_coef, y, bsub, dv, part_dot, part_nrm, tile, b,
+                      nsub, fsm);
+    } else {
+        const int rb = b - nsub_t;   // (pack, l, part) with part fastest
+        const int part = rb % (FTR / RSLOTS), l = (rb / (FTR / RSLOTS)) % L, pack = rb / ((FTR / RSLOTS) * L);
+        if (pack < nrp) fact_radial_block(A, rp, Gh, L, x, Zr, tile + 1, pack, l, part, fsm, s_ch, s_kap);
+    }
+}
 
-// The limits only grow: an operator with fewer items per subgroup must not lower the limit that a
+// dynamic shared memory of the merged pass: the larger of the radial pass's staging and the angular
+// pass's reduction, coefficient sets and offsets (subgroups of at most n items)
+static size_t tile_smem(int n)
+{
+    const size_t mu = (size_t)FSPLIT * FSG * FTR * sizeof(float4) + (size_t)n * (FSG * sizeof(float4) + sizeof(int));
+    return std::max(RAD_SMEM, mu);
+}
+
+// The limit only grows: an operator with fewer items per subgroup must not lower the limit that a
 // larger operator of the same process launches with.
 cudaError_t fact_sub_prepare(int max_items)
 {
     static std::mutex mu;
-    static size_t mu_limit = 0;
+    static size_t limit = 0;
     std::lock_guard<std::mutex> lock(mu);
-    cudaError_t e = cudaFuncSetAttribute(k_fact_radial32L, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RAD_SMEM);
-    if (e != cudaSuccess) return e;
-    mu_limit = std::max(mu_limit, mu_smem(max_items));
-    return cudaFuncSetAttribute(k_fact_mu32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mu_limit);
+    limit = std::max(limit, tile_smem(max_items));
+    return cudaFuncSetAttribute(k_fact_tile32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
 }
 
+// Z holds two tiles' products (2 x channels x multipoles x 4 x FTR x 2 complex64)
 void launch_fact32_sub(cudaStream_t st, const OpView& A, const RadPack* rl, int nrl, const FactSub* subs, int nsub,
                        int max_items, const int* item_off, const float4* item_coef, const float* Gh, int L,
                        const float* ST, const float* HT, int sign, const void* x, float2* Z, void* y,
-                       const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip, int* err)
+                       const void* bsub, const void* dv, double2* pdot, double* pnrm, const KState* skip)
 {
     const int ntile = (A.n1 + FTR - 1) / FTR;
-    const dim3 rgrid(nrl, L, FTR / RSLOTS);
-    const size_t msmem = mu_smem(max_items);
-    for (int tile = 0; tile < ntile; tile++) {
-        k_fact_radial32L<<<rgrid, RWARP * 32, RAD_SMEM, st>>>(A, rl, Gh, L, (const float2*)x, Z, tile, skip);
-        k_fact_mu32<<<nsub, FTR * FSPLIT, msmem, st>>>(A, ST, HT, sign, (const float2*)x, Z, subs, item_off,
-                                                       item_coef, (float2*)y, (const float2*)bsub, (const float2*)dv,
-                                                       pdot, pnrm, tile, skip);
+    const int nrad = nrl * L * (FTR / RSLOTS);
+    const size_t zhalf = (size_t)A.nch * L * 4 * FTR * 2;   // float2 per tile buffer
+    const size_t smem = tile_smem(max_items);
+    for (int t = -1; t < ntile; t++) {
+        const int nsub_t = t >= 0 ? nsub : 0;
+        const int nrad_t = t + 1 < ntile ? nrad : 0;
+        float2* Za = Z + (size_t)((t + 2) % 2) * zhalf;
+        float2* Zr = Z + (size_t)((t + 1) % 2) * zhalf;
+        k_fact_tile32<<<nsub_t + nrad_t, RWARP * 32, smem, st>>>(A, rl, nrl, subs, nsub, nsub_t, item_off, item_coef,
+                                                                 Gh, L, ST, HT, sign, (const float2*)x, Za, Zr,
+                                                                 (float2*)y, (const float2*)bsub, (const float2*)dv,
+                                                                 pdot, pnrm, t, skip);
     }
 }
 
