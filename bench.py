@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--batch-kmax", type=int, default=20, help="|kappa| limit of the batch instances")
     ap.add_argument("--learned", action="store_true",
                     help="train the learned initial guess on production trajectories, then time guess=2 vs guess=1")
-    ap.add_argument("--factorised", type=int, nargs="?", const=1, default=0,
-                    help="factorised complex64 apply in the inner solve (coupling never stored): "
-                         "1 subgroup form (default when given), 2 per-channel form")
+    ap.add_argument("--factorised", type=int, nargs="?", const=1, default=1,
+                    help="complex64 apply of the inner solve in precision 2: 1 factorised, subgroup form "
+                         "(default: radial band products x angular coefficients, coupling values not read), "
+                         "2 factorised, per-channel form, 0 the stored coupling values (owner/gather passes)")
     ap.add_argument("--spectrum", action="store_true",
                     help="also time the photoelectron spectrum dP/dE of the final state (window (0, 2] a.u.)")
     ap.add_argument("--overlap", action="store_true",
@@ -162,7 +163,7 @@ DF_OPS_PER_FMA_OFF = 6              # ... in the fixed-binade form (df_fma_off),
 OFFSET_TOL = 1e-11                  # the library picks the fixed-binade form at tolerances >= this
 
 
-def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
+def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak, fact=1):
     """Roofline of one operator-apply launch group, timed live by the library's event timers.
 
     kind 'f64': FP64 apply (FP64 ALU bound), 'f32': complex64 owner/gather apply (HBM bound),
@@ -170,7 +171,7 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
     The owner pass's coupling products take DF_OPS_PER_FMA_OFF operations at tolerances >= 1e-11
     (the library's automatic choice), DF_OPS_PER_FMA below; the gather's diagonal blocks always ten."""
     cops = DF_OPS_PER_FMA_OFF if cfg["tol"] >= OFFSET_TOL else DF_OPS_PER_FMA
-    coup, flops, bytes_ = operator_counts(bas, cfg, "df" if kind == "df_owner" else kind)
+    coup, flops, bytes_ = operator_counts(bas, cfg, {"df_owner": "df", "fact32": "f32"}.get(kind, kind))
     t = ms / cnt / 1000.0
     gbs = bytes_ / t / 1e9
     traffic, tnote = None, None
@@ -187,6 +188,28 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
         out.update({"kernel": "k_apply<double> (FP64 operator apply)", "flops_per_apply": flops, "bound": "alu",
                     "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tf / FP64_PEAK_TFLOPS,
                     "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz"})
+    elif kind == "fact32":
+        # factorised complex64 apply: useful FMAs only (the radial band products of every channel and
+        # multipole, the angular combination of each directed pair term, the diagonal blocks); it
+        # reads no coupling values, so its HBM bytes are the vectors' and it is timed against the
+        # FP32 FMA rate (one FMA per lane per clock)
+        n1, bd = cfg["N"] + 1, 2 * cfg["order"] - 1
+        L = cfg["l_max"] + 1
+        fma_rad = bas.nch * L * n1 * 4 * 2 * bd * 2 * 2
+        fma_ang = 2 * bas.nterms * n1 * 2 * 8
+        fma_diag = bas.nch * n1 * 2 * bd * 2 * 4
+        fma = fma_rad + fma_ang + fma_diag
+        out["bytes_per_apply"] = (8 + 8) * bas.n
+        out["gbs"] = out["bytes_per_apply"] / t / 1e9
+        tf = 2 * fma / t / 1e12
+        peak = 2 * FP32_LANE_OPS / 1e3
+        out.update({"kernel": ("k_fact_tile32 (factorised complex64 inner-solve apply, subgroup form: radial pass "
+                               "of tile t+1 beside the angular pass of tile t)" if fact == 1 else
+                               "k_fact_radial32 + k_fact_angular32 (factorised complex64 inner-solve apply, "
+                               "per-channel form)"),
+                    "fma_per_apply": {"radial": fma_rad, "angular": fma_ang, "diagonal": fma_diag},
+                    "bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                    "peak_source": "derived FP32 FMA rate: 152 SMs x 128 lanes x 2 flop x 2.07 GHz"})
     elif kind == "f32":
         out.update({"kernel": "k_apply_own32 + k_apply_gather32 (complex64 inner-solve apply)",
                     "flops_per_apply": flops, "bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
@@ -224,7 +247,7 @@ def roofline_of(bas, cfg, phase, kind, ms, cnt, hbm_peak):
     return out
 
 
-def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
+def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak, factorised=0):
     """The dominant kernel's roofline, plus the complex64 SpMV's when it ran.  In precision 2 the
     dominant kernel is the residual's owner pass, timed on its own (its phase lies inside 'apply');
     the whole residual pass (split, owner, gather) is reported beside it."""
@@ -232,8 +255,8 @@ def roofline(bas, cfg, phase_ms, phase_n, precision, hbm_peak):
     if phase_n.get("apply", 0):
         cands.append(("apply", "df" if precision == 2 else "f64", phase_ms["apply"], phase_n["apply"]))
     if phase_n.get("apply32", 0):
-        cands.append(("apply32", "f32", phase_ms["apply32"], phase_n["apply32"]))
-    outs = {c[0]: roofline_of(bas, cfg, c[0], c[1], c[2], c[3], hbm_peak) for c in cands}
+        cands.append(("apply32", "fact32" if factorised else "f32", phase_ms["apply32"], phase_n["apply32"]))
+    outs = {c[0]: roofline_of(bas, cfg, c[0], c[1], c[2], c[3], hbm_peak, factorised) for c in cands}
     dom = max(cands, key=lambda c: c[2])[0]
     if dom == "apply" and precision == 2 and phase_n.get("owner", 0):
         whole = outs["apply"]
@@ -260,6 +283,16 @@ def replica_rate(steps, ms, world):
     return sps, sps * world
 
 
+# complex64 apply of the inner solve for every precision-2 operator the bench builds (--factorised)
+INNER_FACT = 1
+
+
+def inner_apply(op, precision):
+    """Put a precision-2 operator on the inner-solve apply chosen by --factorised."""
+    if precision == 2 and INNER_FACT:
+        op.set_factorised(INNER_FACT)
+
+
 def window_run(B, torch, bas, cfg, psi0_h, t0, warmup, steps, stream, dev, precision, guess=1, net=None,
                host_loop=False):
     """W warm-up steps (they fill the history and capture the graph) then K timed steps from psi0 at
@@ -268,6 +301,7 @@ def window_run(B, torch, bas, cfg, psi0_h, t0, warmup, steps, stream, dev, preci
     import numpy as np
     op = B.Operator(bas, cfg, stream=stream, tol=cfg["tol"], precision=precision, max_iter=1000, tol_inner=1e-5,
                     max_outer=20, guess=guess)
+    inner_apply(op, precision)
     if net is not None:
         B.set_guess(op, net)
     with torch.cuda.stream(stream):
@@ -572,6 +606,7 @@ def _batch_ops(B, torch, cfgs, bases, dev, precision, guess):
             break
         op = B.Operator(bas, cfg, stream=torch.cuda.Stream(), tol=cfg["tol"], precision=precision, max_iter=1000,
                         tol_inner=1e-5, max_outer=20, guess=guess)
+        inner_apply(op, precision)
         biggest = max(biggest, op.device_bytes())
         ops.append(op)
         used.append((cfg, bas))
@@ -738,7 +773,9 @@ def spectrum_measure(op, bas, psi, e_hi=2.0, n_grid=2001, reps=5):
 
 
 def main():
+    global INNER_FACT
     args = parse()
+    INNER_FACT = args.factorised
     if args.impl == "reference":
         reference_arm(args)
         return
@@ -781,8 +818,7 @@ def main():
                     tol_inner=1e-5, max_outer=20)
     if args.precision == 2 and args.overlap:
         op.set_overlap(True)   # next step's assembly overlaps the current solve (same arithmetic)
-    if args.precision == 2 and args.factorised:
-        op.set_factorised(args.factorised)
+    inner_apply(op, args.precision)
     with torch.cuda.stream(stream):
         psi = torch.from_numpy(psi0_h).to(dev)
         hist = torch.zeros(2 * bas.n, dtype=torch.complex128, device=dev)
@@ -859,7 +895,8 @@ def main():
     e2e_sps = e2e_steps / (ee0.elapsed_time(ee1) / 1000.0) * world
 
     peak_bw, peak_src = hbm_peak()
-    roof, roof32 = roofline(bas, cfg, phase_ms, phase_n, args.precision, peak_bw)
+    roof, roof32 = roofline(bas, cfg, phase_ms, phase_n, args.precision, peak_bw,
+                            args.factorised if args.precision == 2 else 0)
     for r in (roof, roof32):
         if r and r["bound"] == "hbm":
             r["peak_source"] = "%s copy bandwidth %.1f GB/s" % ("measured" if peak_src == "measured" else
@@ -901,7 +938,7 @@ def main():
                       "note": "dirac_step on the same op, the next K steps: the graph driver replaces these "
                               "launches and the per-step status read-back by one graph launch per call"},
         "phase_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "spmv_gbs": (roof32 or roof)["gbs"],
+        "spmv_gbs": (roof32 if roof32 and roof32.get("unit") == "GB/s" else roof)["gbs"],
         "roofline": roof,
         "e2e": {"value": e2e_sps, "unit": "steps/s", "h2d_bytes_per_step": bas.n * 16,
                 "d2h_bytes_per_step": bas.n * 16},
@@ -912,7 +949,7 @@ def main():
     if spec:
         line["spectrum"] = spec
     if roof32 and roof32 is not roof:
-        line["roofline_spmv32"] = roof32
+        line["roofline_apply32" if roof32.get("bound") == "alu" else "roofline_spmv32"] = roof32
     if args.precision != 0 and not args.no_fp64_compare:
         # plain FP64 on the same window and driver: the baseline of speedup_vs_fp64, and the per-result
         # errors of the mixed state against it (same start state, same W + K steps)

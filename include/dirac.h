@@ -93,6 +93,9 @@ int dirac_basis_nchannels(const dirac_basis* basis);
 dirac_status dirac_basis_channels(const dirac_basis* basis, int* kappa, int* two_mu);
 /* number of coupled unordered channel pairs (a < b) */
 int64_t dirac_basis_npairs(const dirac_basis* basis);
+/* number of (pair, multipole l) terms of the coupling, Sec. 2.2 Eq. fullH: the multipoles with a
+ * nonzero angular coefficient (Eq. Htheta) summed over the pairs; -1 for a NULL basis */
+int64_t dirac_basis_nterms(const dirac_basis* basis);
 /* Host copies of setup data for parity checks.  Radial blocks of one kappa as dense
  * (2(N+1))^2 row-major matrices in library order (slot-major, type-minor). */
 dirac_status dirac_basis_radial(const dirac_basis* basis, int kappa, double* S, double* H0);
@@ -243,8 +246,9 @@ dirac_status dirac_profile_read(dirac_op* op, double* ms, int64_t* count, int64_
  * up the array's device address (cudaGetSymbolAddress, with the op's device current), so this call
  * does no set-up; the address is kept for the life of the process, so the library must not be used
  * across a cudaDeviceReset.  It supports systems with channels x ceil((N+1)/128) <=
- * DIRAC_STATIC_MAX_PARTIALS and returns DIRAC_E_ARG beyond that, DIRAC_E_ARG for n_out outside 1..3
- * and DIRAC_E_STATE if the current device is not the op's.  All calls share the one array, which
+ * DIRAC_STATIC_MAX_PARTIALS and returns DIRAC_E_ARG beyond that, DIRAC_E_ARG for n_out outside 1..3,
+ * DIRAC_E_STATE if the current device is not the op's, and DIRAC_E_STATE, with nothing enqueued, if
+ * the op's stream is being captured into a CUDA graph (the call synchronises that stream).  All calls share the one array, which
  * keeps the last call's contents (every slot a call reads is written earlier in the same call):
  * calls whose work overlaps on the GPU (other streams, other host threads on the same device) race
  * on it and must be serialised by the caller.  It calls no cudaMalloc, cudaFree or other allocating

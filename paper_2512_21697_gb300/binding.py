@@ -50,6 +50,7 @@ SIGNATURES = {
     "dirac_basis_nchannels": (C.c_int, [_VP]),
     "dirac_basis_channels": (C.c_int, [_VP, _IP, _IP]),
     "dirac_basis_npairs": (C.c_int64, [_VP]),
+    "dirac_basis_nterms": (C.c_int64, [_VP]),
     "dirac_basis_radial": (C.c_int, [_VP, C.c_int, _DP, _DP]),
     "dirac_basis_coupling": (C.c_int, [_VP, C.POINTER(dirac_pulse), C.c_int, C.c_int, C.c_double, _DP]),
     "dirac_angular": (C.c_double, [C.c_int] * 5),
@@ -192,6 +193,7 @@ class Basis:
         _check(L.dirac_basis_channels(h, _ip(k), _ip(m)), "dirac_basis_channels")
         self.kappa, self.two_mu = k, m
         self.npairs = L.dirac_basis_npairs(h)
+        self.nterms = L.dirac_basis_nterms(h)
         del n_guess
 
     def initial_state(self):

@@ -1741,6 +1741,14 @@ extern "C" dirac_status dirac_observables_static(dirac_op* op, const void* psi_d
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev != op->device) { set_error("dirac_observables_static: current device differs from the op's"); return DIRAC_E_STATE; }
+    // the call copies its sums to the host and synchronises the op's stream, which a stream capture
+    // does not allow: refuse before anything is enqueued, so the caller's capture stays valid
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(op->st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        set_error("dirac_observables_static: the op's stream is being captured (the call synchronises it)");
+        return DIRAC_E_STATE;
+    }
     double2* scratch = nullptr;
     dirac_status e = obs_scratch_address(dev, &scratch);
     if (e) return e;

@@ -649,6 +649,7 @@ extern "C" int64_t dirac_basis_dim(const dirac_basis* b) { return b ? b->b.n() :
 extern "C" int dirac_basis_nchannels(const dirac_basis* b) { return b ? b->b.nch : -1; }
 
 extern "C" int64_t dirac_basis_npairs(const dirac_basis* b) { return b ? (int64_t)b->b.pa.size() : -1; }
+extern "C" int64_t dirac_basis_nterms(const dirac_basis* b) { return b ? (int64_t)b->b.pterm.size() : -1; }
 
 extern "C" dirac_status dirac_basis_channels(const dirac_basis* b, int* kappa, int* two_mu)
 {

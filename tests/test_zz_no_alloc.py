@@ -94,3 +94,28 @@ def test_static_scratch_size_limit():
     assert b"static scratch" in lib.dirac_last_error()
     ref = op.observables(psi)
     assert abs(ref["norm"] - 1) < 1e-10
+
+
+def test_static_scratch_refuses_a_capturing_stream():
+    # the call reads its sums back and synchronises the op's stream, which a stream capture does not
+    # allow: on a capturing stream it returns DIRAC_E_STATE before enqueueing anything, the capture
+    # stays valid, and the op works again once the capture has ended
+    import torch
+    lib = B.lib()
+    cfg = W.TINY
+    bas = B.Basis(cfg)
+    s = torch.cuda.Stream()
+    op = B.Operator(bas, cfg, stream=s)
+    psi = torch.from_numpy(_masked_random(bas, 5)).cuda()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        st, _ = _static(lib, op, psi)
+    assert st == B.DIRAC_E_STATE, lib.dirac_last_error()
+    assert b"captured" in lib.dirac_last_error()
+    torch.cuda.synchronize()
+    st, out = _static(lib, op, psi)
+    assert st == B.DIRAC_OK, lib.dirac_last_error()
+    ref = op.observables(psi)
+    for i, k in enumerate(("norm", "energy", "p_ground")):
+        assert abs(out[i] - ref[k]) <= 1e-12 * max(1.0, abs(ref[k])), (k, out[i], ref[k])
