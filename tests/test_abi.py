@@ -124,6 +124,24 @@ def test_angular_coefficients_two_routes(oracle_mod, libdirac):
         assert abs(a - b) < 1e-13 * max(1.0, abs(b)), (k1, t1, k2, t2, l, a, b)
 
 
+def test_term_count_matches_oracle_angular(pair, oracle_mod):
+    # dirac_basis_nterms: the (pair, l) terms with a nonzero angular coefficient (Eq. fullH with
+    # Eq. Htheta), counted here from the oracle's quadrature of the spinors; every term couples
+    # mu to mu +- 1 (x polarisation), which the factorised apply's grouping by mu relies on
+    cfg, bas, _ = pair
+    n = 0
+    for a in range(bas.nch):
+        for b in range(a + 1, bas.nch):
+            ka, ta, kb, tb = int(bas.kappa[a]), int(bas.two_mu[a]), int(bas.kappa[b]), int(bas.two_mu[b])
+            for l in range(cfg["l_max"] + 1):
+                c1 = oracle_mod.angular(ka, ta, -kb, tb, l)
+                c2 = oracle_mod.angular(-ka, ta, kb, tb, l)
+                if abs(c1) > 1e-10 or abs(c2) > 1e-10:
+                    assert abs(ta - tb) == 2, (ka, ta, kb, tb, l)
+                    n += 1
+    assert bas.nterms == n
+
+
 def test_coupling_blocks_match_oracle(pair):
     cfg, bas, orc = pair
     ea, eb = orc.edges()
