@@ -18,14 +18,17 @@
 //    shared by the chunk's channels; k_fact_angular32 (block = channel) reads each partner's products
 //    from L2 and combines them.  Every (partner, multipole) product is read once per output channel
 //    that uses it (about 12 GB of L2 reads per apply at the production size).
-//  - subgroup (mode 1): k_fact_radial32L puts up to FLANE channels of one kappa on the lanes of a
-//    warp, each lane holding its channel's vector window in registers and the band entries read
-//    as shared-memory broadcasts (eight FMAs per 16-byte load); k_fact_mu32 (block = FSG output
-//    channels of one mu) streams the union of their (partner, multipole) products once and applies
-//    each to all FSG outputs from registers.  The partners of a channel all have mu +- 1, so the
-//    outputs of one mu share them; ordered by the parity of the orbital l and |kappa|, about half of
-//    the FSG coefficient sets of an item are nonzero at the production size and each product is read
-//    about 3.5 times per apply instead of 30.
+//  - subgroup (mode 1), one launch of k_fact_tile32 per tile: its radial blocks put up to FLANE
+//    channels of one or two kappas on the lanes of a warp, each lane holding its channel's vector
+//    window in registers and the band entries read as shared-memory broadcasts (eight FMAs per
+//    16-byte load); its angular blocks (FSG output channels of one mu) load the union of their
+//    (partner, multipole) products once and apply each to all FSG outputs from registers.  The
+//    partners of a channel all have mu +- 1, so the outputs of one mu share them; ordered by the
+//    parity of the orbital l and |kappa|, about half of the FSG coefficient sets of an item are
+//    nonzero at the production size and each product is read about 3.5 times per apply instead of
+//    30.  Launch t runs the angular blocks of tile t beside the radial blocks of tile t + 1 (two
+//    product buffers): both kinds wait on memory far more than they compute, so the SMs interleave
+//    them.
 #include <cuda_runtime.h>
 
 #include <algorithm>

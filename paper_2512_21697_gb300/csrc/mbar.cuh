@@ -1,5 +1,6 @@
-// mbar.cuh -- shared-memory mbarriers and the bulk-copy engine (cp.async.bulk), with bounded waits:
-// the ring buffers of the owner/gather passes and of the factorised apply's angular pass.
+// mbar.cuh -- shared-memory mbarriers and the bulk-copy engine (cp.async.bulk), with bounded waits
+// (the ring buffers of the owner/gather passes), and the asynchronous copies with which the
+// factorised apply stages its tables.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -88,13 +89,8 @@ __device__ __forceinline__ bool mbar_wait_poll(uint64_t* bar, uint32_t parity, l
     return true;
 }
 
-// asynchronous global -> shared copies (cp.async): 4 bytes, and 16 bytes with zero fill when
-// src_bytes is 0; completion by cp_async_wait_all
-__device__ __forceinline__ void cp_async4(void* dst, const void* src)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
+// asynchronous global -> shared copy (cp.async) of 16 bytes, zero fill when src_bytes is 0;
+// completion by cp_async_wait_all
 __device__ __forceinline__ void cp_async16z(void* dst, const void* src, uint32_t src_bytes)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(src_bytes)
