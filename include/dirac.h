@@ -337,12 +337,18 @@ dirac_status dirac_op_set_residual_mode(dirac_op* op, int mode);
 dirac_status dirac_op_set_schedule(dirac_op* op, int complex64, int sched);
 int dirac_op_get_schedule(const dirac_op* op, int complex64);   /* -1 for a NULL op */
 
-/* Factorised complex64 apply for the inner solve (precision 2, order-7 splines): the coupling is
- * applied from the time-dependent radial bands and the angular coefficients (four band products
- * per channel and multipole, combined per pair) instead of the stored coupling values.  Same
- * operator (Eq. fullH); FP32 rounding differs, within the inner tolerance.  Allocates the
- * products of one radial tile (channels x multipoles x 4 x 64 x 2 complex64) on first use.
- * DIRAC_E_ARG for other precisions or spline orders. */
+/* Factorised complex64 apply for the inner solve (precision 2, order-7 splines; Sec. 2.2 Eq. fullH):
+ * the coupling is applied from the time-dependent radial bands and the angular coefficients (four
+ * band products per channel and multipole, combined per pair) instead of the stored coupling
+ * values.  Same operator; FP32 rounding differs, within the inner tolerance.  enable: 0 the stored
+ * coupling (the default), 1 the subgroup form (products combined per 8 outputs of one mu, the
+ * radial pass of the next tile beside the angular pass of the current one: the faster form at the
+ * production size), 2 the per-channel form.  The first switch to a form builds its tables on the
+ * host and allocates the products of two radial tiles (2 x channels x multipoles x 4 x 64 x 2
+ * complex64) and, for form 1, the FP32 hi words of the radial bands (written by every later
+ * assembly) and the subgroup item tables.  DIRAC_E_ARG for other precisions, spline orders or
+ * modes; DIRAC_E_CUDA if the subgroup form's shared-memory need exceeds the device's limit.  The
+ * input and output vectors of an apply must not alias. */
 dirac_status dirac_op_set_factorised(dirac_op* op, int enable);
 
 /* Self-test of the bounded waits of the owner passes (their bulk-copy rings): one block waits
